@@ -1,0 +1,180 @@
+"""Shift-and-invert Krylov--Schur solve of the linearised QEP (oracle).
+
+Plain FP64 restatement, test infrastructure only.
+
+* Linearisation, Eq. (Linearization): A = [[0, I], [-K, -C]], B = diag(I, M),
+  eigenvector [u; lambda u].
+* Operator, Eq. (BlockOperatorVector): r = L(s)^{-1} B v with
+      r_u = -Q(s)^{-1} (s M v_u + C v_u + M v_l),   r_l = s r_u + v_u.
+* B-inner product, Section 4.2.1: <x, y>_B = x_u^T y_u + x_l^T M y_l.
+* Arnoldi recurrence, Algorithm 1 / Algorithm 2: h = V^T B r, z = r - V h,
+  h_{j+1,j} = ||z||_B; classical Gram--Schmidt applied twice (CGS2).
+* Rayleigh--Ritz, Eq. (ArnoldiRitz): Ritz values theta of the projected
+  matrix; lambda = s + 1/theta (Section 4.1.1, theta = 1/(lambda - s)).
+* Restart: Krylov--Schur (Section 4.1.3; the paper omits the details, this is
+  Stewart's scheme): real Schur form of the projected matrix, wanted Ritz
+  values moved to the top, the first k Schur vectors kept.
+
+Readings where the paper is silent:
+* wanted set = the neig Ritz values nearest s; for equal distances Im > 0
+  first (conjugate pairs tie exactly for a real shift);
+* k = neig + (m - neig)//2, plus one when that would split a conjugate pair;
+* a Ritz pair is converged when |h_{m+1,m} y_m| / |theta| <= tol (y unit);
+* the QEP eigenvector is the upper block x = V_u y, scaled to unit 2-norm with
+  its largest-modulus entry real and positive (lowest index on ties);
+* the reported accuracy is the normwise backward error
+  eta = ||Q(lambda) x|| / ((|lambda|^2 ||M|| + |lambda| ||C|| + ||K||) ||x||)
+  with max-row-sum norms for the matrices.
+"""
+import numpy as np
+import scipy.linalg as sla
+from scipy.linalg import lapack
+
+
+def apply_operator(v, s, M, C, solve):
+    """Eq. (BlockOperatorVector)."""
+    N = M.shape[0]
+    vu, vl = v[:N], v[N:]
+    ru = -solve(s * (M @ vu) + C @ vu + M @ vl)
+    return np.concatenate([ru, s * ru + vu])
+
+
+def b_apply(x, M):
+    """B x = [x_u; M x_l]."""
+    N = M.shape[0]
+    return np.concatenate([x[:N], M @ x[N:]])
+
+
+def b_norm(x, M):
+    return float(np.sqrt(x @ b_apply(x, M)))
+
+
+def wanted_order(lam, s):
+    """Indices of lam sorted by |lam - s|, Im > 0 first on ties."""
+    key_d = np.abs(lam - s)
+    key_i = np.where(lam.imag > 0, 0, np.where(lam.imag == 0, 1, 2))
+    return np.lexsort((key_i, key_d))
+
+
+def normalise_vector(x):
+    """Unit 2-norm, largest-modulus entry real positive (lowest index on ties)."""
+    x = x / np.linalg.norm(x)
+    a = np.abs(x)
+    i = int(np.flatnonzero(a == a.max())[0])
+    return x * (np.conj(x[i]) / a[i])
+
+
+def backward_error(lam, x, K, C, M):
+    nK = abs(K).sum(axis=1).max()
+    nC = abs(C).sum(axis=1).max()
+    nM = abs(M).sum(axis=1).max()
+    r = K @ x + lam * (C @ x) + lam * lam * (M @ x)
+    den = (abs(lam) ** 2 * nM + abs(lam) * nC + nK) * np.linalg.norm(x)
+    return float(np.linalg.norm(r) / den)
+
+
+class EigsResult:
+    def __init__(self, lam, X, eta, n_conv, n_restarts, n_apply, n_vv):
+        self.lam, self.X, self.eta = lam, X, eta
+        self.n_conv, self.n_restarts, self.n_apply = n_conv, n_restarts, n_apply
+        self.n_vv = n_vv
+
+
+def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000):
+    """Algorithm 2 with CGS2 and Krylov--Schur restarts.
+
+    solve(b) must return Q(s)^{-1} b (the factorised shifted pencil).
+    v1: start vector of length 2N (original DOF order).
+    """
+    N = M.shape[0]
+    if not (0 < neig < m <= 2 * N):
+        raise ValueError("need 0 < neig < m <= 2N")
+    V = np.zeros((2 * N, m + 1))
+    H = np.zeros((m + 1, m))
+    V[:, 0] = v1 / b_norm(v1, M)
+    k = 0
+    n_apply = 0
+    n_vv = 0
+    for it in range(max_restarts + 1):
+        for j in range(k, m):
+            r = apply_operator(V[:, j], s, M, C, solve)
+            n_apply += 1
+            for _ in range(2):                      # CGS2
+                h = V[:, :j + 1].T @ b_apply(r, M)
+                r = r - V[:, :j + 1] @ h
+                H[:j + 1, j] += h
+                n_vv += 2 * (j + 1)
+            nr = b_norm(r, M)
+            H[j + 1, j] = nr
+            V[:, j + 1] = r / nr
+        Hm = H[:m, :m]
+        beta = H[m, m - 1]
+        theta, Y = np.linalg.eig(Hm)          # Ritz pairs, unit columns
+        lam = s + 1.0 / theta
+        order = wanted_order(lam, s)
+        est = np.abs(beta * Y[m - 1, :]) / np.abs(theta)
+        want = order[:neig]
+        conv = est[want] <= tol
+        if conv.all() or it == max_restarts:
+            break
+        T, Z = sla.schur(Hm, output='real')
+        wr, wi = _schur_eigs(T)
+        order = wanted_order(s + 1.0 / (wr + 1j * wi), s)
+        kk = neig + (m - neig) // 2
+        sel_idx = set(order[:kk].tolist())
+        # keep conjugate partners together
+        pos = 0
+        while pos < m:
+            if pos + 1 < m and T[pos + 1, pos] != 0.0:
+                if pos in sel_idx or pos + 1 in sel_idx:
+                    sel_idx |= {pos, pos + 1}
+                pos += 2
+            else:
+                pos += 1
+        select = np.zeros(m, dtype=np.int32)
+        select[list(sel_idx)] = 1
+        T2, Z2, info = _trsen(select, T, Z)
+        k = int(select.sum())
+        V[:, :k] = V[:, :m] @ Z2[:, :k]
+        V[:, k] = V[:, m]
+        Hn = np.zeros((m + 1, m))
+        Hn[:k, :k] = T2[:k, :k]
+        Hn[k, :k] = beta * Z2[m - 1, :k]
+        H = Hn
+    lam_w = lam[want]
+    X = []
+    eta = []
+    for t, i in enumerate(want):
+        x = normalise_vector(V[:N, :m] @ Y[:, i])
+        X.append(x)
+        eta.append(backward_error(lam_w[t], x, K, C, M))
+    return EigsResult(lam_w, np.array(X), np.array(eta), int(conv.sum()), it,
+                      n_apply, n_vv)
+
+
+def _schur_eigs(T):
+    m = T.shape[0]
+    wr = np.zeros(m)
+    wi = np.zeros(m)
+    pos = 0
+    while pos < m:
+        if pos + 1 < m and T[pos + 1, pos] != 0.0:
+            a, b, c, d = T[pos, pos], T[pos, pos + 1], T[pos + 1, pos], T[pos + 1, pos + 1]
+            ev = np.linalg.eigvals(np.array([[a, b], [c, d]]))
+            ev = ev[np.argsort(-ev.imag)]
+            wr[pos], wi[pos] = ev[0].real, ev[0].imag
+            wr[pos + 1], wi[pos + 1] = ev[1].real, ev[1].imag
+            pos += 2
+        else:
+            wr[pos] = T[pos, pos]
+            pos += 1
+    return wr, wi
+
+
+def _trsen(select, T, Z):
+    out = lapack.dtrsen(select, T, Z, job='N')
+    T2, Z2 = out[0], out[1]
+    info = out[-1]
+    if info != 0:
+        raise ArithmeticError(f"dtrsen failed: {info}")
+    return T2, Z2, info

@@ -1,0 +1,367 @@
+"""Pins of the FP64 CPU oracle against facts it does not compute itself.
+
+Each test ties one oracle function to something fixed outside it: numbers
+the paper prints (tests/golden), a library routine that is an independent
+definition (scipy's B-splines, LAPACK's dense QZ / symmetric eigensolver),
+a closed form, an invariant or brute force on a tiny case.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.interpolate as si
+import scipy.linalg as sla
+
+from oracle import bspline, pattern
+from oracle.assemble import assemble
+from oracle.nd import symbolic, nd_boxes
+from oracle.multifrontal import factorize, PivotError
+from oracle import qep
+from oracle.adjoint import damping_gradient, element_quadratic_forms
+from paper_2112_14064_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- B-splines
+@pytest.mark.parametrize("ne,p,block", [(8, 2, 4), (8, 3, 4), (12, 4, 4), (6, 3, 0)])
+def test_basis_matches_scipy_bspline(ne, p, block):
+    """Cox--de Boor values and derivatives == scipy's independent B-splines."""
+    kn = bspline.knot_vector(ne, p, block)
+    t = np.array([float(k) for k in kn])
+    xs = np.random.default_rng(0).uniform(0, 1, 25)
+    nf = bspline.n_functions(kn, p)
+    spl = si.BSpline(t, np.eye(nf), p, extrapolate=False)
+    dspl = spl.derivative()
+    for x in xs:
+        v, d = bspline.basis_and_derivative(kn, p, x)
+        np.testing.assert_allclose(v, spl(x), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(d, dspl(x), rtol=1e-12, atol=1e-10)
+        assert v.sum() == pytest.approx(1.0, abs=1e-14)   # partition of unity
+
+
+def test_fig4_pattern_counts():
+    """Knot multiplicities + support coupling reproduce Fig. 4's printed N, nnz."""
+    for space, ne, p, block, N, nnz in _golden("fig4_pattern.txt"):
+        assert pattern.hcurl_counts(int(ne), int(p), int(block)) == (int(N), int(nnz)), space
+
+
+def test_riga_dof_counts_closed_form():
+    """n = ne + p - 2 + (nb - 1)(p - 1) DOFs per direction after Dirichlet."""
+    for ne, p, b in [(16, 2, 4), (256, 3, 16), (64, 3, 16), (512, 4, 32), (32, 5, 8)]:
+        s = bspline.Space1D(ne, p, b)
+        assert s.n == ne + p - 2 + (ne // b - 1) * (p - 1)
+        assert len(s.c0_dofs) == ne // b - 1
+    assert bspline.Space1D(256, 3, 0).n == 257
+
+
+def test_maxwell_printed_value():
+    """The analytic formula pi^2 (i^2 + j^2) gives the printed 10442.04."""
+    (i, j, val, dec), = _golden("maxwell_mode.txt")
+    assert round(np.pi ** 2 * (int(i) ** 2 + int(j) ** 2), int(dec)) == float(val)
+
+
+# ---------------------------------------------------------------- assembly
+def _scipy_1d(ne, p, block):
+    """1-D mass and stiffness matrices from scipy B-splines and a Gauss rule
+    with 2p+2 points per element (both exact for these piecewise
+    polynomials), Dirichlet functions dropped."""
+    kn = bspline.knot_vector(ne, p, block)
+    t = np.array([float(k) for k in kn])
+    nf = len(t) - p - 1
+    g, w = np.polynomial.legendre.leggauss(2 * p + 2)
+    xs = np.concatenate([(e + (g + 1) / 2) / ne for e in range(ne)])
+    ws = np.concatenate([w / (2 * ne)] * ne)
+    spl = si.BSpline(t, np.eye(nf), p, extrapolate=False)
+    B = spl(xs).T
+    D = spl.derivative()(xs).T
+    M1 = (B * ws) @ B.T
+    K1 = (D * ws) @ D.T
+    return M1[1:-1, 1:-1], K1[1:-1, 1:-1]
+
+
+@pytest.mark.parametrize("ne,p,block", [(8, 2, 4), (8, 3, 4), (8, 3, 0), (10, 4, 5)])
+def test_assembly_tensor_structure(ne, p, block):
+    """With constant damping c: M = M1 (x) M1, K = M1 (x) K1 + K1 (x) M1,
+    C = c M, where M1, K1 come from scipy's B-splines (DOF i + n j)."""
+    c = 0.7
+    A = assemble(ne, p, block, np.full(ne * ne, c))
+    M1, K1 = _scipy_1d(ne, p, block)
+    np.testing.assert_allclose(A.M.toarray(), np.kron(M1, M1), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(A.K.toarray(), np.kron(M1, K1) + np.kron(K1, M1),
+                               rtol=0, atol=1e-12)
+    np.testing.assert_allclose(A.C.toarray(), c * A.M.toarray(), rtol=1e-14, atol=1e-17)
+    nnz = pattern.h1_counts(ne, p, block)[1]
+    assert A.K.nnz == nnz
+
+
+def test_damping_single_element():
+    """sigma_e = indicator of one element: C is that element's mass matrix,
+    the product of the 1-D element mass matrices."""
+    ne, p, b = 8, 3, 4
+    e0x, e0y = 3, 5
+    s = np.zeros(ne * ne)
+    s[e0x + ne * e0y] = 1.0
+    A = assemble(ne, p, b, s)
+    kn = bspline.knot_vector(ne, p, b)
+    t = np.array([float(k) for k in kn])
+    nf = len(t) - p - 1
+    g, w = np.polynomial.legendre.leggauss(2 * p + 2)
+
+    spl = si.BSpline(t, np.eye(nf), p, extrapolate=False)
+
+    def m1(e):
+        xs = (e + (g + 1) / 2) / ne
+        B = spl(xs).T
+        return ((B * (w / (2 * ne))) @ B.T)[1:-1, 1:-1]
+
+    np.testing.assert_allclose(A.C.toarray(), np.kron(m1(e0y), m1(e0x)), atol=1e-16)
+
+
+def test_undamped_limit_converges_to_laplacian():
+    """sigma_e = 0: -lambda^2 = mu_h -> pi^2 (m^2 + n^2) at order ~2p."""
+    p = 2
+    exact = np.pi ** 2 * np.array(sorted(m * m + n * n for m in range(1, 5)
+                                         for n in range(1, 5)))[:6]
+    errs = []
+    for ne in (8, 16):
+        A = assemble(ne, p, 4, np.zeros(ne * ne))
+        mu = sla.eigh(A.K.toarray(), A.M.toarray(), eigvals_only=True)[:6]
+        errs.append(np.abs(mu - exact) / exact)
+    order = np.log2(errs[0] / errs[1])
+    assert np.all(errs[1] < 1e-3)
+    assert np.all(order > 2 * p - 0.6), order
+
+
+# ---------------------------------------------------------------- symbolic
+def _brute_symbolic(A, sym):
+    """Column structures of L by dense boolean elimination."""
+    N = A.N
+    P = (A.K.toarray() != 0)[np.ix_(sym.perm, sym.perm)]
+    S = P.copy()
+    for j in range(N):
+        rows = np.flatnonzero(S[j + 1:, j]) + j + 1
+        S[np.ix_(rows, rows)] = True
+    return S
+
+
+@pytest.mark.parametrize("ne,p,block", [(16, 2, 4), (8, 3, 4), (10, 2, 0)])
+def test_symbolic_against_brute_force(ne, p, block):
+    A = assemble(ne, p, block, np.ones(ne * ne))
+    sym = symbolic(A.n1, A.space.c0_dofs, p, A.indptr, A.indices, use_c0=block > 0)
+    N = A.N
+    assert sorted(sym.perm.tolist()) == list(range(N))
+    S = _brute_symbolic(A, sym)
+    for s in range(sym.nsuper):
+        a, e = sym.sptr[s], sym.sptr[s + 1]
+        exact = np.flatnonzero(S[e:, a:e].any(axis=1)) + e
+        np.testing.assert_array_equal(sym.struct(s), exact)
+        if sym.parent[s] >= 0:
+            assert sym.parent[s] > s
+            pa = sym.parent[s]
+            assert sym.sptr[pa] <= sym.struct(s)[0] < sym.sptr[pa + 1]
+        # every struct entry belongs to an ancestor's pivots
+        anc = set()
+        q = sym.parent[s]
+        while q >= 0:
+            anc |= set(range(sym.sptr[q], sym.sptr[q + 1]))
+            q = sym.parent[q]
+        assert set(sym.struct(s).tolist()) <= anc
+
+
+def test_separators_separate():
+    """No matrix entry couples the two children of a dissection cut."""
+    ne, p, b = 16, 3, 8
+    A = assemble(ne, p, b, np.ones(ne * ne))
+    n = A.n1
+    boxes = nd_boxes(n, A.space.c0_dofs, p)
+    Kd = A.K.toarray() != 0
+    # within a macroelement the p-wide cut separates; the C^0 line too
+    for (x0, x1, y0, y1) in boxes:
+        if x1 - x0 in (1, p) and y1 - y0 > p:
+            lo = [xx + n * yy for yy in range(y0, y1) for xx in range(max(0, x0 - 3 * p), x0)]
+            hi = [xx + n * yy for yy in range(y0, y1) for xx in range(x1, min(n, x1 + 3 * p))]
+            if lo and hi:
+                assert not Kd[np.ix_(lo, hi)].any()
+
+
+# ---------------------------------------------------------------- factor
+@pytest.mark.parametrize("ne,p,block", [(16, 2, 4), (8, 3, 4), (8, 3, 0)])
+def test_ldlt_reconstructs_Q(ne, p, block):
+    sig = workloads.sigma_e(dict(ne=ne, sigma_law="uniform", lo=0.1, hi=1.0, seed=1))
+    A = assemble(ne, p, block, sig)
+    sym = symbolic(A.n1, A.space.c0_dofs, p, A.indptr, A.indices, use_c0=block > 0)
+    Q = A.Q(20.0)
+    F = factorize(sym, Q)
+    N = A.N
+    L = np.zeros((N, N))
+    for s in range(sym.nsuper):
+        a, e = sym.sptr[s], sym.sptr[s + 1]
+        idx = np.concatenate([np.arange(a, e), sym.struct(s)])
+        L[np.ix_(idx, np.arange(a, e))] = F.L[s]
+    Qp = Q.toarray()[np.ix_(sym.perm, sym.perm)]
+    R = L @ np.diag(F.D) @ L.T - Qp
+    assert np.abs(R).max() / np.abs(Qp).max() < 1e-14
+    b = np.random.default_rng(2).standard_normal(N)
+    x = F.solve(b)
+    np.testing.assert_allclose(x, np.linalg.solve(Q.toarray(), b), rtol=1e-11, atol=0)
+
+
+def test_non_positive_pivot_is_reported():
+    """A shifted matrix that is not positive definite stops the oracle."""
+    A = assemble(8, 2, 4, np.ones(64))
+    sym = symbolic(A.n1, A.space.c0_dofs, 2, A.indptr, A.indices)
+    with pytest.raises(PivotError):
+        factorize(sym, -1.0 * A.K)
+
+
+# ---------------------------------------------------------------- operator
+def test_block_operator_solves_linearised_pencil():
+    """Eq. (BlockOperatorVector): L(s) r = B v with the dense 2N pencil."""
+    ne, p, b, s = 16, 2, 4, 20.0
+    cfg = workloads.CONFIGS["tiny"]
+    A = assemble(ne, p, b, workloads.sigma_e(cfg))
+    sym = symbolic(A.n1, A.space.c0_dofs, p, A.indptr, A.indices)
+    F = factorize(sym, A.Q(s))
+    N = A.N
+    v = workloads.start_vector(3, 2 * N)
+    r = qep.apply_operator(v, s, A.M, A.C, F.solve)
+    K, C, M = A.K.toarray(), A.C.toarray(), A.M.toarray()
+    I, Z = np.eye(N), np.zeros((N, N))
+    Amat = np.block([[Z, I], [-K, -C]])
+    Bmat = np.block([[I, Z], [Z, M]])
+    Ls = Amat - s * Bmat
+    res = Ls @ r - Bmat @ v
+    assert np.linalg.norm(res) / np.linalg.norm(Bmat @ v) < 1e-13
+
+
+# ---------------------------------------------------------------- eigs
+def _dense_nearest(A, s, neig):
+    N = A.N
+    K, C, M = A.K.toarray(), A.C.toarray(), A.M.toarray()
+    I, Z = np.eye(N), np.zeros((N, N))
+    w = sla.eig(np.block([[Z, I], [-K, -C]]), np.block([[I, Z], [Z, M]]), right=False)
+    return w[qep.wanted_order(w, s)][:neig]
+
+
+def _solve_tiny(cfg_over=None, s=None, neig=None, m=None):
+    cfg = dict(workloads.CONFIGS["tiny"])
+    if cfg_over:
+        cfg.update(cfg_over)
+    A = assemble(cfg["ne"], cfg["p"], cfg["block"], workloads.sigma_e(cfg))
+    sym = symbolic(A.n1, A.space.c0_dofs, cfg["p"], A.indptr, A.indices)
+    s = cfg["shift"] if s is None else s
+    F = factorize(sym, A.Q(s))
+    r = qep.eigs(A.K, A.C, A.M, s, neig or cfg["neig"], m or cfg["m"], F.solve,
+                 workloads.start_vector(1, 2 * A.N))
+    return A, r
+
+
+def _match(ref, got):
+    """Largest relative distance from each computed value to the reference
+    multiset (exact repeats are compared as multisets)."""
+    return max(np.min(np.abs(ref - g)) / abs(g) for g in got)
+
+
+def test_eigs_match_dense_qz():
+    """P-1: nearest eigenvalues of the 2N pencil by LAPACK's QZ."""
+    A, r = _solve_tiny()
+    assert r.n_conv == 10
+    ref = _dense_nearest(A, 20.0, 10)
+    assert _match(ref, r.lam) < 1e-10
+    assert _match(r.lam, ref) < 1e-10
+    assert np.all(r.eta < 1e-12)
+
+
+def test_proportional_damping_closed_form():
+    """P-2: C = cM gives lambda = (-c +- sqrt(c^2 - 4 mu)) / 2 for each mu of
+    K x = mu M x (LAPACK's symmetric-definite solver)."""
+    c = 0.4
+    A, r = _solve_tiny({"sigma_law": "constant", "value": c})
+    mu = sla.eigh(A.K.toarray(), A.M.toarray(), eigvals_only=True)
+    disc = np.sqrt((c * c - 4 * mu).astype(complex))
+    lam_all = np.concatenate([(-c + disc) / 2, (-c - disc) / 2])
+    assert r.n_conv == 10
+    assert _match(lam_all, r.lam) < 1e-10
+
+
+def test_undamped_eigs_are_imaginary():
+    """sigma_e = 0: lambda = +- i sqrt(mu_h)."""
+    A, r = _solve_tiny({"sigma_law": "constant", "value": 0.0})
+    mu = sla.eigh(A.K.toarray(), A.M.toarray(), eigvals_only=True)
+    lam_all = np.concatenate([1j * np.sqrt(mu), -1j * np.sqrt(mu)])
+    assert _match(lam_all, r.lam) < 1e-10
+    assert np.max(np.abs(r.lam.real)) < 1e-8
+
+
+def test_backward_error_detects_wrong_eigenvalue():
+    A, r = _solve_tiny()
+    lam, x = r.lam[0], r.X[0]
+    assert qep.backward_error(lam, x, A.K, A.C, A.M) < 1e-12
+    assert qep.backward_error(lam * (1 + 1e-6), x, A.K, A.C, A.M) > 1e-9
+
+
+def test_eigenvector_normalisation():
+    A, r = _solve_tiny()
+    for x in r.X:
+        assert np.linalg.norm(x) == pytest.approx(1.0, abs=1e-14)
+        i = np.argmax(np.abs(x))
+        assert abs(x[i].imag) < 1e-15 and x[i].real > 0
+
+
+# ---------------------------------------------------------------- gradient
+def test_gradient_sum_rule_proportional():
+    """P-2: with C = cM, sum_e dlambda/dsigma_e = -lambda / (2 lambda + c),
+    from differentiating lambda^2 + c lambda + mu = 0 in c."""
+    c = 0.4
+    A, r = _solve_tiny({"sigma_law": "constant", "value": c})
+    cfg = workloads.CONFIGS["tiny"]
+    G = damping_gradient(cfg["ne"], cfg["p"], cfg["block"], r.lam[:4], r.X[:4], A.C, A.M)
+    for lam, g in zip(r.lam[:4], G):
+        assert g.sum() == pytest.approx(-lam / (2 * lam + c), rel=1e-9)
+
+
+def test_element_forms_sum_to_mass_form():
+    """sum_e x_e^T M_e x_e = x^T M x (the element forms partition M)."""
+    cfg = workloads.CONFIGS["tiny"]
+    A = assemble(cfg["ne"], cfg["p"], cfg["block"], np.ones(cfg["ne"] ** 2))
+    x = np.random.default_rng(4).standard_normal(A.N) + 1j * np.random.default_rng(5).standard_normal(A.N)
+    q = element_quadratic_forms(cfg["ne"], cfg["p"], cfg["block"], x)
+    assert q.sum() == pytest.approx(x @ (A.M @ x), rel=1e-13)
+
+
+def test_gradient_central_differences():
+    """P-8: analytic dlambda/dsigma_e vs central differences of the dense-QZ
+    eigenvalue tracked by nearest match.  The step is 1e-4: the gradients are
+    ~1e-5 while QZ's eigenvalues carry ~1e-13 absolute rounding, so a 1e-6
+    step would leave ~1e-3 relative noise; at 1e-4 the O(h^2) truncation
+    and the rounding are both below 1e-6 relative."""
+    ne, p, b, s = 8, 2, 4, 20.0
+    cfg = dict(ne=ne, sigma_law="uniform", lo=0.1, hi=1.0, seed=11)
+    sig = workloads.sigma_e(cfg)
+    A = assemble(ne, p, b, sig)
+    sym = symbolic(A.n1, A.space.c0_dofs, p, A.indptr, A.indices)
+    F = factorize(sym, A.Q(s))
+    r = qep.eigs(A.K, A.C, A.M, s, 4, 20, F.solve, workloads.start_vector(1, 2 * A.N))
+    G = damping_gradient(ne, p, b, r.lam, r.X, A.C, A.M)
+    h = 1e-4
+    for e in (0, 9, 27, 63):
+        fd = []
+        for sgn in (+1, -1):
+            s2 = sig.copy()
+            s2[e] += sgn * h
+            A2 = assemble(ne, p, b, s2)
+            w = _dense_nearest(A2, s, 8)
+            fd.append([w[np.argmin(np.abs(w - l))] for l in r.lam])
+        fd = (np.array(fd[0]) - np.array(fd[1])) / (2 * h)
+        # atol: ~1e-13 QZ rounding / (2h) = 5e-10, with a factor 4 margin
+        np.testing.assert_allclose(G[:, e], fd, rtol=1e-5, atol=2e-9)
