@@ -1,0 +1,223 @@
+/*
+ * rigaqep — shift-and-invert solver for quadratic eigenvalue problems from
+ * refined isogeometric (rIGA) discretisations, on one GB300 GPU (sm_103a).
+ *
+ * Problem (paper, Eq. QuadEig, Section 4.2):  (K + lambda C + lambda^2 M) u = 0
+ * with K the Laplacian stiffness, M the mass matrix and C = sum_e sigma_e M_e
+ * (per-element damping) of degree-p tensor-product B-splines on the unit
+ * square, homogeneous Dirichlet boundary.  rIGA repeats the knots on every
+ * block-th element line p times (C^0 separators, Section 3.3); block = 0 is
+ * maximum-continuity IGA (Section 3.2).
+ *
+ * Pipeline, in call order (Algorithm 2 of the paper):
+ *   rigaqep_assemble  Gauss-quadrature K, M, C in CSR           (Section 3)
+ *   rigaqep_analyze   separator nested dissection + symbolic    (Section 3.3)
+ *   rigaqep_factor    multifrontal LDL^T of Q(s)=s^2M+sC+K      (Alg. 2, "Factorize Q(s)")
+ *   rigaqep_solve     forward/backward substitution with the factors (Section 4.2.2)
+ *   rigaqep_eigs      Krylov-Schur on the linearised pencil     (Eqs. Linearization,
+ *                     BlockOperatorVector; Algorithms 1 and 2; Section 4.1.3)
+ *   rigaqep_grad_damping  d lambda / d sigma_e                   (no counterpart in the paper)
+ *
+ * Conventions for every entry point:
+ *  - Return value: RIGAQEP_OK or an error code; nothing is thrown across the
+ *    ABI and the process is never terminated.  rigaqep_last_error() gives a
+ *    message for the calling thread's last failure.
+ *  - DOF numbering: dof = i + n*j (xi index i fastest), n DOFs per direction
+ *    after removing the Dirichlet functions.  Element numbering e = ex + ne*ey.
+ *  - Pointers marked "device" must be CUDA device memory of the current
+ *    device; "host" pointers are ordinary host memory.  Caller buffers are
+ *    borrowed for the duration of the call only.  All device work runs on the
+ *    stream given to rigaqep_assemble; calls that return host values
+ *    synchronise that stream.
+ *  - The handle owns every internal device buffer (CSR, factors, Krylov
+ *    basis) and frees them in rigaqep_destroy.
+ *  - Out-of-order calls (e.g. solve before factor) return RIGAQEP_ERR_STATE.
+ */
+#ifndef RIGAQEP_H
+#define RIGAQEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rigaqep_problem rigaqep_problem;
+typedef struct rigaqep_symbolic rigaqep_symbolic;
+
+typedef enum {
+  RIGAQEP_OK = 0,
+  RIGAQEP_ERR_ARG = 1,             /* invalid argument (sizes, NULL, ranges) */
+  RIGAQEP_ERR_STATE = 2,           /* call out of order */
+  RIGAQEP_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+  RIGAQEP_ERR_OOM = 4,             /* device or host allocation failed */
+  RIGAQEP_ERR_PIVOT = 5,           /* non-positive pivot in LDL^T (Q(s) not SPD) */
+  RIGAQEP_ERR_REFINEMENT = 6,      /* reserved: iterative refinement stagnated */
+  RIGAQEP_ERR_NO_CONVERGENCE = 7,  /* max_restarts reached; partial results returned */
+  RIGAQEP_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
+  RIGAQEP_ERR_INTERNAL = 9         /* a device-side consistency check failed */
+} rigaqep_status;
+
+/* Mesh and discretisation.  ne_x = ne_y = ne (square meshes only), p >= 2,
+ * block = 0 (IGA) or a divisor of ne (rIGA C^0 lines every block elements),
+ * n_quad = Gauss points per direction (0 selects p+1, exact for M_e, K_e),
+ * leaf_min = largest box extent left undissected inside a macroelement
+ * (0 selects 8). */
+typedef struct {
+  int32_t ne_x, ne_y, p, block_x, block_y, n_quad, leaf_min;
+} rigaqep_mesh_desc;
+
+typedef enum { RIGAQEP_FP64 = 0 } rigaqep_precision;
+
+/* Krylov-Schur options.  krylov_dim = m (neig < m <= 96), max_restarts
+ * (0 selects 1000), tol = Ritz-estimate tolerance |h_{m+1,m} y_m|/|theta|
+ * (0 selects 1e-10), seed = start-vector seed used when no start vector is
+ * given (v1[i] = splitmix64(seed+i)/2^64 - 0.5 over the 2N entries).
+ *
+ * shift_mode selects where the spectral transformation is placed:
+ *  RIGAQEP_SHIFT_AT_TARGET (0): the shift is the target sigma itself, as in
+ *    the paper (Section 4.1.1, Algorithm 2); the neig Ritz pairs nearest
+ *    sigma are converged and returned.
+ *  RIGAQEP_SHIFT_IN_REGION (1): Q(shift) is factorised at opts->shift (a real
+ *    shift inside the spectrum region; Q(shift) must be SPD, shift = 0 gives
+ *    Q = K), the ncand pairs nearest the shift are converged, and the neig of
+ *    them nearest the target sigma are returned.  The selection is certified
+ *    (info.certified = 1) when no other eigenvalue can be nearer the target:
+ *    every eigenvalue not converged lies at least r from the shift (r = the
+ *    largest candidate distance), complex eigenvalues have
+ *    Re lambda in [-max sigma_e / 2, -min sigma_e / 2] (Rayleigh quotients of
+ *    the QEP with K, M SPD and C = sum sigma_e M_e, sigma_e >= 0) and real
+ *    ones are <= 0, which bounds their distance to the target from below. */
+enum { RIGAQEP_SHIFT_AT_TARGET = 0, RIGAQEP_SHIFT_IN_REGION = 1 };
+typedef struct {
+  int32_t krylov_dim;
+  int32_t max_restarts;
+  double tol;
+  uint64_t seed;
+  int32_t precision;
+  int32_t shift_mode;
+  double shift;
+  int32_t ncand;         /* pairs converged around the shift (0 selects neig) */
+} rigaqep_eigs_opts;
+
+/* Sizes and counters of a handle (host struct filled by rigaqep_get_info). */
+typedef struct {
+  int64_t n1;            /* DOFs per direction */
+  int64_t N;             /* total DOFs */
+  int64_t nnz;           /* entries of the shared K/M/C pattern */
+  int64_t nsuper;        /* supernodes (= fronts) */
+  int64_t nlevels;       /* assembly-tree levels */
+  int64_t nnz_L;         /* supernodal factor entries, dense pivot blocks */
+  int64_t factor_flops;  /* sum_j (c_j^2 + 2 c_j), c_j = off-diagonals of column j */
+  int64_t max_front;     /* largest front order k+u */
+  int64_t n_apply;       /* operator applications (FB solves) of the last eigs */
+  int64_t n_restarts;    /* Krylov-Schur restarts of the last eigs */
+  int64_t n_spmv;        /* sparse matrix-vector products of the last eigs */
+  int64_t n_vv;          /* length-N vector-vector products of the last eigs */
+  int64_t n_qr_sweeps;   /* Francis QR sweeps of the Ritz steps of the last eigs */
+  double norm_K, norm_M, norm_C;  /* max-row-sum norms */
+  double factor_ms;      /* device time of the last rigaqep_factor */
+  double eigs_ms;        /* device time of the last rigaqep_eigs */
+  double fb_ms;          /* device time of its FB solves (CUDA events around each) */
+  int64_t certified;     /* 1: the returned pairs are provably the neig nearest the target */
+  double cert_margin;    /* lower bound on the distance of any other eigenvalue to the
+                            target, minus the largest returned distance (>= 0 when certified) */
+  int64_t n_launches;    /* kernels launched by the last eigs (including its factorisation) */
+} rigaqep_info;
+
+/* Create a handle and assemble K, M, C (original DOF order, one CSR
+ * pattern, FP64).  sigma_e: ne*ne coefficients, element ex + ne*ey, host
+ * memory if sigma_on_device == 0, else device memory.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns all
+ * device memory of the problem; on failure *out is NULL.
+ * Defined by: Section 3.1 (tensor-product B-splines, Cox-de Boor), Section
+ * 3.3 (rIGA knots), Section 2 forms a, b, c in their scalar H^1 analogue. */
+rigaqep_status rigaqep_assemble(const rigaqep_mesh_desc* mesh, const double* sigma_e,
+                                int32_t sigma_on_device, void* cuda_stream,
+                                rigaqep_problem** out);
+
+/* Integer symbolic phase: canonical separator nested dissection, supernodes,
+ * assembly tree, update structures, extend-add maps and level sets, then the
+ * ND-ordered device CSR.  Bit-exact and deterministic.
+ * Defined by: Section 3.3 (separators coincide with the solver's partitions)
+ * and Section 5.1 (multifrontal solver with nested-dissection ordering). */
+rigaqep_status rigaqep_analyze(rigaqep_problem* prob);
+
+/* Numeric multifrontal LDL^T of Q(sigma) = sigma^2 M + sigma C + K, fronts
+ * batched per tree level.  Requires analyze.  A non-positive pivot returns
+ * RIGAQEP_ERR_PIVOT (Q(sigma) is SPD for real sigma > 0).
+ * Defined by: Algorithm 2 ("Factorize Q(s)"), Section 4.2.1. */
+rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t precision);
+
+/* x = Q(sigma)^{-1} b for nrhs right-hand sides (device, original DOF order,
+ * column-major N x nrhs; b and x may alias; both may be NULL when nrhs = 0).
+ * transpose = 1 solves with Q^T, which equals Q (K, M, C symmetric): the
+ * same factors and path.
+ * Defined by: Section 4.2.2 (forward/backward elimination). */
+rigaqep_status rigaqep_solve(rigaqep_problem* prob, const double* b, double* x,
+                             int32_t nrhs, int32_t transpose);
+
+/* neig eigenpairs of the QEP nearest the real target sigma by shift-and-invert
+ * Krylov-Schur on the linearised 2N pencil (factors Q at the shift chosen by
+ * opts->shift_mode if it is not factorised there already).
+ * v1: optional device start vector of 2N entries (original order; NULL =
+ * splitmix64 from opts->seed).  Outputs (device): lambda 2*neig doubles
+ * (re, im) ordered by |lambda - sigma| with Im > 0 first on ties; X N*neig
+ * complex (interleaved re, im; column k = eigenvector k, original order, unit
+ * 2-norm, largest-modulus entry real positive); eta neig backward errors
+ * ||Q(lambda)x|| / ((|lambda|^2||M|| + |lambda|||C|| + ||K||)||x||).
+ * *n_converged (host) = wanted pairs whose Ritz estimate met tol.
+ * Returns RIGAQEP_ERR_NO_CONVERGENCE (with outputs filled) if max_restarts
+ * is reached first.
+ * Defined by: Eqs. (Linearization), (BlockOperatorVector), Algorithm 1
+ * (Arnoldi, B-inner product), Algorithm 2, Eq. (ArnoldiRitz), Section 4.1.3. */
+rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
+                            const rigaqep_eigs_opts* opts, const double* v1,
+                            double* lambda, double* X, double* eta,
+                            int32_t* n_converged);
+
+/* G[k, e] = d lambda_k / d sigma_e = -lambda_k x_e^T M_e x_e / x^T(2 lambda_k M + C) x
+ * (unconjugated: the left eigenvector of the symmetric QEP is x itself).
+ * lambda (2*neig) and X (N*neig complex) as returned by rigaqep_eigs (device);
+ * G: device, neig x ne^2 complex, row-major (re, im interleaved).
+ * The paper has no sensitivity analysis; this is first-order perturbation
+ * theory of a simple eigenvalue of Eq. (QuadEig). */
+rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig,
+                                    const double* lambda, const double* X, double* G);
+
+/* Copy the original-order CSR (rowptr N+1, col nnz int32; K, M, C nnz
+ * doubles) to host buffers; any pointer may be NULL to skip it. */
+rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, int32_t* col,
+                                  double* K, double* M, double* C);
+
+/* Copy the symbolic phase to host buffers (any may be NULL): perm[N]
+ * (perm[new] = old dof), sptr[nsuper+1], parent[nsuper] (-1 = root),
+ * upd_ptr[nsuper+1], upd_idx[upd_ptr[nsuper]] (new indices, ascending),
+ * level[nsuper]. */
+rigaqep_status rigaqep_export_symbolic(const rigaqep_problem* prob, int32_t* perm, int32_t* sptr,
+                                       int32_t* parent, int32_t* upd_ptr, int32_t* upd_idx,
+                                       int32_t* level);
+
+/* Sizes and counters (host struct). */
+rigaqep_status rigaqep_get_info(const rigaqep_problem* prob, rigaqep_info* info);
+
+/* Host-only planning (no CUDA call, usable without a GPU): the same CSR
+ * pattern and symbolic phase as assemble + analyze.  sizes[0..5] =
+ * {N, nnz, nsuper, n_upd, nlevels, n1}. */
+rigaqep_status rigaqep_symbolic_create(const rigaqep_mesh_desc* mesh, rigaqep_symbolic** out);
+rigaqep_status rigaqep_symbolic_sizes(const rigaqep_symbolic* sym, int64_t* sizes);
+rigaqep_status rigaqep_symbolic_export(const rigaqep_symbolic* sym, int32_t* perm, int32_t* sptr,
+                                       int32_t* parent, int32_t* upd_ptr, int32_t* upd_idx,
+                                       int32_t* level, int32_t* rowptr, int32_t* col);
+void rigaqep_symbolic_destroy(rigaqep_symbolic* sym);
+
+/* Thread-local message of the calling thread's last failed call ("" if none). */
+const char* rigaqep_last_error(void);
+
+/* Free the handle and every device buffer it owns (NULL is a no-op). */
+void rigaqep_destroy(rigaqep_problem* prob);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIGAQEP_H */

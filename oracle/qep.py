@@ -25,6 +25,18 @@ Readings where the paper is silent:
 * the reported accuracy is the normwise backward error
   eta = ||Q(lambda) x|| / ((|lambda|^2 ||M|| + |lambda| ||C|| + ||K||) ||x||)
   with max-row-sum norms for the matrices.
+
+Target/shift split (the paper places its single shift inside the spectrum
+region of interest, Section 4.1.4): with a target t different from the shift
+s, the ncand pairs nearest s are converged and the neig of them nearest t are
+returned.  The choice is certified when no unconverged eigenvalue can be
+nearer t: every eigenvalue outside the candidates is at least r from s (r the
+largest candidate distance); for K, M SPD and C = sum sigma_e M_e with
+sigma_e >= 0, x^H(lambda^2 M + lambda C + K)x = 0 gives complex eigenvalues
+Re lambda = -x^H C x / (2 x^H M x) <= -min(sigma_e)/2 and real ones <= 0, so
+for 0 <= s <= t
+  complex: |lambda - t|^2 >= r^2 + (t - s)(t + s + min sigma_e),
+  real:    |lambda - t|   >= (t - s) + r.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -80,15 +92,19 @@ class EigsResult:
         self.n_vv = n_vv
 
 
-def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000):
+def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=None,
+         ncand=None, sigma_min=None):
     """Algorithm 2 with CGS2 and Krylov--Schur restarts.
 
     solve(b) must return Q(s)^{-1} b (the factorised shifted pencil).
     v1: start vector of length 2N (original DOF order).
+    target/ncand/sigma_min: the target/shift split described above (target
+    None: the shift is the target and ncand = neig).
     """
     N = M.shape[0]
-    if not (0 < neig < m <= 2 * N):
-        raise ValueError("need 0 < neig < m <= 2N")
+    ncand = neig if ncand is None else ncand
+    if not (0 < neig <= ncand < m <= 2 * N):
+        raise ValueError("need 0 < neig <= ncand < m <= 2N")
     V = np.zeros((2 * N, m + 1))
     H = np.zeros((m + 1, m))
     V[:, 0] = v1 / b_norm(v1, M)
@@ -113,14 +129,14 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000):
         lam = s + 1.0 / theta
         order = wanted_order(lam, s)
         est = np.abs(beta * Y[m - 1, :]) / np.abs(theta)
-        want = order[:neig]
+        want = order[:ncand]
         conv = est[want] <= tol
         if conv.all() or it == max_restarts:
             break
         T, Z = sla.schur(Hm, output='real')
         wr, wi = _schur_eigs(T)
         order = wanted_order(s + 1.0 / (wr + 1j * wi), s)
-        kk = neig + (m - neig) // 2
+        kk = ncand + (m - ncand) // 2
         sel_idx = set(order[:kk].tolist())
         # keep conjugate partners together
         pos = 0
@@ -141,15 +157,34 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000):
         Hn[:k, :k] = T2[:k, :k]
         Hn[k, :k] = beta * Z2[m - 1, :k]
         H = Hn
-    lam_w = lam[want]
+    cand = want
+    lam_c = lam[cand]
+    certified = bool(conv.all())
+    if target is None:
+        chosen = np.arange(neig)
+    else:
+        chosen = wanted_order(lam_c, target)[:neig]
+        dmax = np.abs(lam_c[chosen] - target).max()
+        r = np.abs(lam_c - s).max()
+        ok = (certified and s >= 0 and target >= s and sigma_min is not None
+              and sigma_min >= 0)
+        if ok:
+            bound = min(np.sqrt(r * r + (target - s) * (target + s + sigma_min)),
+                        (target - s) + r)
+            certified = bool(bound >= dmax * (1 + 1e-12))
+        else:
+            certified = False
     X = []
     eta = []
-    for t, i in enumerate(want):
+    lam_w = lam_c[chosen]
+    for t, i in enumerate(np.asarray(cand)[chosen]):
         x = normalise_vector(V[:N, :m] @ Y[:, i])
         X.append(x)
         eta.append(backward_error(lam_w[t], x, K, C, M))
-    return EigsResult(lam_w, np.array(X), np.array(eta), int(conv.sum()), it,
-                      n_apply, n_vv)
+    res = EigsResult(lam_w, np.array(X), np.array(eta), int(conv[chosen].sum()), it,
+                     n_apply, n_vv)
+    res.certified = certified
+    return res
 
 
 def _schur_eigs(T):

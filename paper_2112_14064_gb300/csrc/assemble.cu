@@ -1,0 +1,249 @@
+// Element-batched Gauss-quadrature assembly of K, M and C (FP64).
+//
+// Space: tensor-product B-splines on the unit square (paper Section 3.1),
+// identity geometric map, rIGA or IGA knots (Sections 3.2-3.3).  For a
+// tensor-product function pair on an axis-aligned element the 2-D Gauss sum
+// factorises exactly into 1-D sums:
+//   int_e B_a B_b      = mx_e(ax,bx) * my_e(ay,by)
+//   int_e grad.grad    = kx_e * my_e + mx_e * ky_e
+// with mx_e(a,b) = sum_q w_q N_a(x_q) N_b(x_q), kx_e with derivatives.
+// Step 1 computes those 1-D element integrals for every element and local
+// pair (one thread each, Cox-de Boor evaluated at the Gauss points); step 2
+// forms each CSR entry by summing over the elements shared by its two
+// functions (one thread per row, no atomics, deterministic):
+//   M_ij = sum_e mx my,  K_ij = sum_e (kx my + mx ky),  C_ij = sum_e sigma_e mx my.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rq {
+namespace {
+
+struct Tables {
+  const int* knots;      // numerators over ne
+  const int* first_fn;   // first full function of element ex
+  const int* elo;        // element range of DOF d
+  const int* ehi;
+  const double* gx;      // Gauss points on [-1, 1]
+  const double* gw;      // Gauss weights
+  int ne, p, nq, n1;
+};
+
+// Values and first derivatives of the p+1 B-splines that do not vanish on
+// knot span s (full functions s-p .. s) at x.  Cox-de Boor (paper Eqs.
+// BasisFunBi0/BasisFunBip) on the triangular table of non-zero functions:
+// degree q keeps functions s-q..s; every denominator t_{i+q}-t_i or
+// t_{i+q+1}-t_{i+1} that is used spans the non-empty span s, so none is zero.
+__device__ void basis_on_span(const int* knots, double inv_ne, int s, int p, double x,
+                              double* N, double* dN) {
+  double prev[kMaxP + 1], cur[kMaxP + 1];
+  prev[0] = 1.0;
+  auto t = [&](int i) { return (double)knots[i] * inv_ne; };
+  for (int q = 1; q <= p; ++q) {
+    for (int r = 0; r <= q; ++r) {
+      int i = s - q + r;
+      double v = 0.0;
+      if (r >= 1) v += (x - t(i)) / (t(i + q) - t(i)) * prev[r - 1];
+      if (r <= q - 1) v += (t(i + q + 1) - x) / (t(i + q + 1) - t(i + 1)) * prev[r];
+      cur[r] = v;
+    }
+    if (q == p) {
+      for (int r = 0; r <= p; ++r) {
+        int i = s - p + r;
+        double d = 0.0;
+        if (r >= 1) d += p / (t(i + p) - t(i)) * prev[r - 1];
+        if (r <= p - 1) d -= p / (t(i + p + 1) - t(i + 1)) * prev[r];
+        N[r] = cur[r];
+        dN[r] = d;
+      }
+      return;
+    }
+    for (int r = 0; r <= q; ++r) prev[r] = cur[r];
+  }
+}
+
+// m1[ex][a][b], k1[ex][a][b]: 1-D element mass/stiffness integrals.
+__global__ void k_element_1d(Tables T, double* m1, double* k1) {
+  int np1 = T.p + 1;
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)T.ne * np1 * np1;
+  if (tid >= total) return;
+  int b = tid % np1;
+  int a = (tid / np1) % np1;
+  int ex = tid / (np1 * np1);
+  double inv_ne = 1.0 / T.ne;
+  int s = T.first_fn[ex] + T.p;
+  double N[kMaxP + 1], dN[kMaxP + 1];
+  double mm = 0.0, kk = 0.0;
+  for (int q = 0; q < T.nq; ++q) {
+    double x = (ex + 0.5 * (T.gx[q] + 1.0)) * inv_ne;
+    double w = T.gw[q] * 0.5 * inv_ne;
+    basis_on_span(T.knots, inv_ne, s, T.p, x, N, dN);
+    mm += w * N[a] * N[b];
+    kk += w * dN[a] * dN[b];
+  }
+  m1[tid] = mm;
+  k1[tid] = kk;
+}
+
+__global__ void k_assemble_rows(Tables T, const int32_t* rowptr, const int32_t* col,
+                                const double* m1, const double* k1, const double* sig,
+                                double* K, double* M, double* C) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t Nn = (int64_t)T.n1 * T.n1;
+  if (r >= Nn) return;
+  int n1 = T.n1, np1 = T.p + 1;
+  int ix = r % n1, iy = r / n1;
+  for (int32_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+    int c = col[q];
+    int jx = c % n1, jy = c / n1;
+    int ex0 = max(T.elo[ix], T.elo[jx]), ex1 = min(T.ehi[ix], T.ehi[jx]);
+    int ey0 = max(T.elo[iy], T.elo[jy]), ey1 = min(T.ehi[iy], T.ehi[jy]);
+    double sm = 0.0, sk = 0.0, sc = 0.0;
+    for (int ey = ey0; ey < ey1; ++ey) {
+      int f0 = T.first_fn[ey];
+      int ay = iy + 1 - f0, by = jy + 1 - f0;
+      double my = m1[((int64_t)ey * np1 + ay) * np1 + by];
+      double ky = k1[((int64_t)ey * np1 + ay) * np1 + by];
+      for (int ex = ex0; ex < ex1; ++ex) {
+        int g0 = T.first_fn[ex];
+        int ax = ix + 1 - g0, bx = jx + 1 - g0;
+        double mx = m1[((int64_t)ex * np1 + ax) * np1 + bx];
+        double kx = k1[((int64_t)ex * np1 + ax) * np1 + bx];
+        double mxy = mx * my;
+        sm += mxy;
+        sk += kx * my + mx * ky;
+        sc += sig[ex + (int64_t)T.ne * ey] * mxy;
+      }
+    }
+    K[q] = sk;
+    M[q] = sm;
+    C[q] = sc;
+  }
+}
+
+__global__ void k_permute(const int64_t* map, const double* a, const double* b, const double* c,
+                          double* an, double* bn, double* cn, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = map[i];
+  an[i] = a[o];
+  bn[i] = b[o];
+  cn[i] = c[o];
+}
+
+// max-row-sum norms; non-negative doubles order like their bit patterns
+__global__ void k_row_norms(const int32_t* rowptr, const double* K, const double* M,
+                            const double* C, int64_t N, unsigned long long* out) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  if (r < N) {
+    for (int32_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+      s[0] += fabs(K[q]);
+      s[1] += fabs(M[q]);
+      s[2] += fabs(C[q]);
+    }
+  }
+  for (int t = 0; t < 3; ++t) {
+    double v = s[t];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + t, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// Gauss-Legendre nodes and weights by Newton's method on P_n (host).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = pk;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+}  // namespace
+
+void launch_assemble(Problem& P) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  std::vector<double> gx, gw;
+  gauss_legendre(L.nq, gx, gw);
+  DBuf<int> knots, elo, ehi;
+  DBuf<double> dgx, dgw;
+  DBuf<int>& first_fn = P.first_fn;
+  DBuf<double>& m1 = P.m1;
+  DBuf<double>& k1 = P.k1;
+  knots.upload(L.sp.knots, s);
+  first_fn.upload(L.sp.first_fn, s);
+  elo.upload(L.sp.elo, s);
+  ehi.upload(L.sp.ehi, s);
+  dgx.upload(gx, s);
+  dgw.upload(gw, s);
+  int np1 = L.p + 1;
+  int64_t ntab = (int64_t)L.ne * np1 * np1;
+  m1.alloc(ntab);
+  k1.alloc(ntab);
+  Tables T{knots.p, first_fn.p, elo.p, ehi.p, dgx.p, dgw.p, L.ne, L.p, L.nq, L.n1};
+  k_element_1d<<<(unsigned)((ntab + 255) / 256), 256, 0, s>>>(T, m1.p, k1.p);
+  RQ_CUDA(cudaGetLastError());
+  P.K.alloc(L.nnz);
+  P.M.alloc(L.nnz);
+  P.C.alloc(L.nnz);
+  k_assemble_rows<<<(unsigned)((L.N + 127) / 128), 128, 0, s>>>(T, P.rowptr.p, P.col.p, m1.p, k1.p,
+                                                                 P.sigma_e.p, P.K.p, P.M.p, P.C.p);
+  RQ_CUDA(cudaGetLastError());
+  RQ_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+}
+
+void launch_norms(Problem& P) {
+  DBuf<unsigned long long> out;
+  out.alloc(3);
+  RQ_CUDA(cudaMemsetAsync(out.p, 0, 3 * sizeof(unsigned long long), P.stream));
+  int64_t N = P.plan.N;
+  k_row_norms<<<(unsigned)((N + 255) / 256), 256, 0, P.stream>>>(P.rowptr.p, P.K.p, P.M.p, P.C.p, N,
+                                                                  out.p);
+  RQ_CUDA(cudaGetLastError());
+  unsigned long long h[3];
+  RQ_CUDA(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, P.stream));
+  RQ_CUDA(cudaStreamSynchronize(P.stream));
+  double d[3];
+  for (int t = 0; t < 3; ++t) std::memcpy(&d[t], &h[t], sizeof(double));
+  P.info.norm_K = d[0];
+  P.info.norm_M = d[1];
+  P.info.norm_C = d[2];
+}
+
+void launch_permute_values(Problem& P) {
+  int64_t n = P.plan.nnz;
+  P.Kn.alloc(n);
+  P.Mn.alloc(n);
+  P.Cn.alloc(n);
+  k_permute<<<(unsigned)((n + 255) / 256), 256, 0, P.stream>>>(P.slot_map.p, P.K.p, P.M.p, P.C.p,
+                                                               P.Kn.p, P.Mn.p, P.Cn.p, n);
+  RQ_CUDA(cudaGetLastError());
+}
+
+}  // namespace rq

@@ -1,0 +1,367 @@
+// C-ABI of rigaqep: argument checks, state machine and error mapping.
+// Every entry point catches all C++ exceptions and returns a status code.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+rigaqep_status guard(F&& f) {
+  try {
+    f();
+    return RIGAQEP_OK;
+  } catch (const rq::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::invalid_argument& e) {
+    g_last_error = e.what();
+    return RIGAQEP_ERR_ARG;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return RIGAQEP_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return RIGAQEP_ERR_INTERNAL;
+  } catch (...) {
+    g_last_error = "unknown failure";
+    return RIGAQEP_ERR_INTERNAL;
+  }
+}
+
+void need(bool cond, rigaqep_status code, const char* msg) {
+  if (!cond) throw rq::Error(code, msg);
+}
+
+void check_mesh(const rigaqep_mesh_desc* m) {
+  need(m != nullptr, RIGAQEP_ERR_ARG, "mesh descriptor is NULL");
+  need(m->ne_x == m->ne_y && m->ne_x >= 2, RIGAQEP_ERR_ARG, "only square meshes ne_x == ne_y >= 2");
+  need(m->block_x == m->block_y, RIGAQEP_ERR_ARG, "block_x must equal block_y");
+  need(m->p >= 2 && m->p <= rq::kMaxP, RIGAQEP_ERR_ARG, "p must be in [2, 8]");
+  need(m->block_x >= 0 && (m->block_x == 0 || m->ne_x % m->block_x == 0), RIGAQEP_ERR_ARG,
+       "block must be 0 or divide ne");
+  need(m->n_quad >= 0 && m->n_quad <= 10, RIGAQEP_ERR_ARG, "n_quad must be in [0, 10]");
+  need(m->leaf_min >= 0, RIGAQEP_ERR_ARG, "leaf_min must be >= 0");
+}
+
+template <class T>
+void copy_out(T* dst, const std::vector<T>& src) {
+  if (dst && !src.empty()) std::memcpy(dst, src.data(), src.size() * sizeof(T));
+}
+
+}  // namespace
+
+namespace rq {
+Problem::~Problem() {
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+}
+}  // namespace rq
+
+struct rigaqep_symbolic {
+  rq::Plan plan;
+};
+
+extern "C" {
+
+rigaqep_status rigaqep_assemble(const rigaqep_mesh_desc* mesh, const double* sigma_e,
+                                int32_t sigma_on_device, void* cuda_stream,
+                                rigaqep_problem** out) {
+  return guard([&] {
+    need(out != nullptr, RIGAQEP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    check_mesh(mesh);
+    need(sigma_e != nullptr, RIGAQEP_ERR_ARG, "sigma_e is NULL");
+    rigaqep_problem* h = new rigaqep_problem();
+    try {
+      rq::Problem& P = h->impl;
+      P.stream = (cudaStream_t)cuda_stream;
+      P.plan.build_pattern(mesh->ne_x, mesh->p, mesh->block_x, mesh->n_quad, mesh->leaf_min);
+      RQ_CUDA(cudaEventCreate(&P.ev0));
+      RQ_CUDA(cudaEventCreate(&P.ev1));
+      P.rowptr.upload(P.plan.rowptr, P.stream);
+      P.col.upload(P.plan.col, P.stream);
+      int64_t ne2 = (int64_t)P.plan.ne * P.plan.ne;
+      P.sigma_e.alloc(ne2);
+      RQ_CUDA(cudaMemcpyAsync(P.sigma_e.p, sigma_e, sizeof(double) * ne2,
+                              sigma_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              P.stream));
+      std::vector<double> hs(ne2);
+      RQ_CUDA(cudaMemcpyAsync(hs.data(), P.sigma_e.p, sizeof(double) * ne2, cudaMemcpyDeviceToHost,
+                              P.stream));
+      RQ_CUDA(cudaStreamSynchronize(P.stream));
+      P.sigma_min = *std::min_element(hs.begin(), hs.end());
+      P.sigma_max = *std::max_element(hs.begin(), hs.end());
+      P.status.alloc(1);
+      RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
+      rq::launch_assemble(P);
+      rq::launch_norms(P);
+      P.info.n1 = P.plan.n1;
+      P.info.N = P.plan.N;
+      P.info.nnz = P.plan.nnz;
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    rq::Problem& P = prob->impl;
+    rq::Plan& L = P.plan;
+    cudaStream_t s = P.stream;
+    L.build_symbolic();
+    P.perm.upload(L.perm, s);
+    P.iperm.upload(L.iperm, s);
+    P.sptr.upload(L.sptr, s);
+    P.upd_ptr.upload(L.upd_ptr, s);
+    P.upd_idx.upload(L.upd_idx, s);
+    P.relmap.upload(L.relmap, s);
+    P.child_ptr.upload(L.child_ptr, s);
+    P.child_idx.upload(L.child_idx, s);
+    P.lvl_nodes.upload(L.lvl_nodes, s);
+    P.loff.upload(L.loff, s);
+    P.uoff.upload(L.uoff, s);
+    P.rowptr_n.upload(L.rowptr_n, s);
+    P.col_n.upload(L.col_n, s);
+    P.fpos.upload(L.fpos, s);
+    P.slot_map.upload(L.slot_map, s);
+    rq::launch_permute_values(P);
+    P.lvl_maxF.assign(L.nlevels, 0);
+    P.lvl_maxK.assign(L.nlevels, 0);
+    for (int sn = 0; sn < L.nsuper; ++sn) {
+      int k = L.sptr[sn + 1] - L.sptr[sn], u = L.upd_ptr[sn + 1] - L.upd_ptr[sn];
+      int lv = L.level[sn];
+      P.lvl_maxF[lv] = std::max(P.lvl_maxF[lv], k + u);
+      P.lvl_maxK[lv] = std::max(P.lvl_maxK[lv], k);
+    }
+    P.Lval.alloc(L.l_total);
+    P.Uval.alloc(L.u_total);
+    P.Dinv.alloc(L.N);
+    P.yvec.alloc(L.upd_idx.size());
+    P.xwork.alloc(L.N);
+    // fronts larger than the default 48 KB of dynamic shared memory
+    size_t smax = sizeof(double) * (size_t)L.max_front;
+    need(smax <= 200 * 1024, RIGAQEP_ERR_ARG, "front too large for one CTA");
+    rq::factor_configure(smax);
+    rq::fb_plan(P);
+    RQ_CUDA(cudaStreamSynchronize(s));
+    P.info.nsuper = L.nsuper;
+    P.info.nlevels = L.nlevels;
+    P.info.nnz_L = L.nnz_L;
+    P.info.factor_flops = L.flops;
+    P.info.max_front = L.max_front;
+    P.analyzed = true;
+    P.factored = false;
+  });
+}
+
+rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t precision) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    rq::Problem& P = prob->impl;
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_factor");
+    need(precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG, "only RIGAQEP_FP64 is available");
+    need(sigma == sigma, RIGAQEP_ERR_ARG, "sigma is NaN");
+    P.factored = false;
+    RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
+    RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
+    rq::launch_factor(P, sigma);
+    RQ_CUDA(cudaEventRecord(P.ev1, P.stream));
+    rq::DevStatus st;
+    RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
+    RQ_CUDA(cudaStreamSynchronize(P.stream));
+    float ms = 0.f;
+    RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+    P.info.factor_ms = ms;
+    if (st.pivot_fail)
+      throw rq::Error(RIGAQEP_ERR_PIVOT, "non-positive pivot in supernode " +
+                                             std::to_string(st.pivot_fail - 1) +
+                                             ": Q(sigma) is not positive definite");
+    P.factored = true;
+    P.fact_sigma = sigma;
+  });
+}
+
+rigaqep_status rigaqep_solve(rigaqep_problem* prob, const double* b, double* x, int32_t nrhs,
+                             int32_t transpose) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    need(nrhs >= 0, RIGAQEP_ERR_ARG, "nrhs must be >= 0");
+    need(nrhs == 0 || (b != nullptr && x != nullptr), RIGAQEP_ERR_ARG, "NULL argument");
+    need(transpose == 0 || transpose == 1, RIGAQEP_ERR_ARG, "transpose must be 0 or 1");
+    rq::Problem& P = prob->impl;
+    need(P.factored, RIGAQEP_ERR_STATE, "rigaqep_factor must run before rigaqep_solve");
+    int64_t N = P.plan.N;
+    // Q is symmetric, so the transposed solve uses the same factors and path.
+    for (int c = 0; c < nrhs; ++c) {
+      rq::launch_gather(P.perm.p, b + N * c, P.xwork.p, N, (int32_t)N, 1, P.stream);
+      rq::launch_fb(P, P.xwork.p, P.fact_sigma, nullptr, nullptr, nullptr);
+      rq::launch_scatter(P.perm.p, P.xwork.p, x + N * c, N, P.stream);
+    }
+    RQ_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
+                            const rigaqep_eigs_opts* opts, const double* v1, double* lambda,
+                            double* X, double* eta, int32_t* n_converged) {
+  rigaqep_status st = RIGAQEP_OK;
+  rigaqep_status g = guard([&] {
+    need(prob != nullptr && lambda != nullptr && X != nullptr && eta != nullptr &&
+             n_converged != nullptr,
+         RIGAQEP_ERR_ARG, "NULL argument");
+    rq::Problem& P = prob->impl;
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_eigs");
+    rq::EigsParams E;
+    E.neig = neig;
+    E.target = sigma;
+    E.in_region = opts && opts->shift_mode == RIGAQEP_SHIFT_IN_REGION;
+    need(!opts || opts->shift_mode == RIGAQEP_SHIFT_AT_TARGET || E.in_region, RIGAQEP_ERR_ARG,
+         "unknown shift_mode");
+    E.shift = E.in_region ? opts->shift : sigma;
+    E.ncand = (E.in_region && opts->ncand > 0) ? opts->ncand : neig;
+    E.m = opts && opts->krylov_dim > 0 ? opts->krylov_dim : std::min(rq::kMaxKrylov, 2 * E.ncand + 20);
+    E.max_restarts = opts && opts->max_restarts > 0 ? opts->max_restarts : 1000;
+    E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
+    E.seed = opts ? opts->seed : 1;
+    need(!opts || opts->precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG, "only RIGAQEP_FP64 is available");
+    need(neig >= 1 && neig <= E.ncand, RIGAQEP_ERR_ARG, "need 1 <= neig <= ncand");
+    need(E.ncand < E.m && E.m <= rq::kMaxKrylov, RIGAQEP_ERR_ARG, "need ncand < krylov_dim <= 96");
+    need(E.m <= 2 * P.plan.N, RIGAQEP_ERR_ARG, "krylov_dim exceeds 2N");
+    need(sigma > 0.0, RIGAQEP_ERR_ARG, "the target must be real and positive");
+    need(!E.in_region || E.shift == E.shift, RIGAQEP_ERR_ARG, "shift is NaN");
+    P.launches = 0;
+    if (!P.factored || P.fact_sigma != E.shift) {
+      rigaqep_status fs = rigaqep_factor(prob, E.shift, RIGAQEP_FP64);
+      if (fs != RIGAQEP_OK) throw rq::Error(fs, g_last_error);
+      P.launches = 2 * P.plan.nlevels;
+    }
+    int nconv = 0;
+    rq::eigs_run(P, E, v1, lambda, X, eta, &nconv);
+    *n_converged = nconv;
+    if (nconv < neig) {
+      g_last_error = "Krylov-Schur reached max_restarts before all wanted pairs converged";
+      st = RIGAQEP_ERR_NO_CONVERGENCE;
+    }
+  });
+  return g != RIGAQEP_OK ? g : st;
+}
+
+rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig, const double* lambda,
+                                    const double* X, double* G) {
+  return guard([&] {
+    need(prob != nullptr && lambda != nullptr && X != nullptr && G != nullptr, RIGAQEP_ERR_ARG,
+         "NULL argument");
+    need(neig >= 1, RIGAQEP_ERR_ARG, "neig must be >= 1");
+    rq::Problem& P = prob->impl;
+    need(neig <= 64, RIGAQEP_ERR_ARG, "neig must be <= 64");
+    rq::grad_run(P, neig, lambda, X, G);
+  });
+}
+
+rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, int32_t* col,
+                                  double* K, double* M, double* C) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    const rq::Problem& P = prob->impl;
+    copy_out(rowptr, P.plan.rowptr);
+    copy_out(col, P.plan.col);
+    size_t nb = sizeof(double) * P.plan.nnz;
+    if (K) RQ_CUDA(cudaMemcpyAsync(K, P.K.p, nb, cudaMemcpyDeviceToHost, P.stream));
+    if (M) RQ_CUDA(cudaMemcpyAsync(M, P.M.p, nb, cudaMemcpyDeviceToHost, P.stream));
+    if (C) RQ_CUDA(cudaMemcpyAsync(C, P.C.p, nb, cudaMemcpyDeviceToHost, P.stream));
+    RQ_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+rigaqep_status rigaqep_export_symbolic(const rigaqep_problem* prob, int32_t* perm, int32_t* sptr,
+                                       int32_t* parent, int32_t* upd_ptr, int32_t* upd_idx,
+                                       int32_t* level) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    const rq::Problem& P = prob->impl;
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze has not run");
+    const rq::Plan& L = P.plan;
+    copy_out(perm, L.perm);
+    copy_out(sptr, L.sptr);
+    copy_out(parent, L.parent);
+    copy_out(upd_ptr, L.upd_ptr);
+    copy_out(upd_idx, L.upd_idx);
+    copy_out(level, L.level);
+  });
+}
+
+rigaqep_status rigaqep_get_info(const rigaqep_problem* prob, rigaqep_info* info) {
+  return guard([&] {
+    need(prob != nullptr && info != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    *info = prob->impl.info;
+  });
+}
+
+rigaqep_status rigaqep_symbolic_create(const rigaqep_mesh_desc* mesh, rigaqep_symbolic** out) {
+  return guard([&] {
+    need(out != nullptr, RIGAQEP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    check_mesh(mesh);
+    rigaqep_symbolic* h = new rigaqep_symbolic();
+    try {
+      h->plan.build_pattern(mesh->ne_x, mesh->p, mesh->block_x, mesh->n_quad, mesh->leaf_min);
+      h->plan.build_symbolic();
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+  });
+}
+
+rigaqep_status rigaqep_symbolic_sizes(const rigaqep_symbolic* sym, int64_t* sizes) {
+  return guard([&] {
+    need(sym != nullptr && sizes != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    const rq::Plan& L = sym->plan;
+    sizes[0] = L.N;
+    sizes[1] = L.nnz;
+    sizes[2] = L.nsuper;
+    sizes[3] = (int64_t)L.upd_idx.size();
+    sizes[4] = L.nlevels;
+    sizes[5] = L.n1;
+  });
+}
+
+rigaqep_status rigaqep_symbolic_export(const rigaqep_symbolic* sym, int32_t* perm, int32_t* sptr,
+                                       int32_t* parent, int32_t* upd_ptr, int32_t* upd_idx,
+                                       int32_t* level, int32_t* rowptr, int32_t* col) {
+  return guard([&] {
+    need(sym != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    const rq::Plan& L = sym->plan;
+    copy_out(perm, L.perm);
+    copy_out(sptr, L.sptr);
+    copy_out(parent, L.parent);
+    copy_out(upd_ptr, L.upd_ptr);
+    copy_out(upd_idx, L.upd_idx);
+    copy_out(level, L.level);
+    copy_out(rowptr, L.rowptr);
+    copy_out(col, L.col);
+  });
+}
+
+void rigaqep_symbolic_destroy(rigaqep_symbolic* sym) { delete sym; }
+
+const char* rigaqep_last_error(void) { return g_last_error.c_str(); }
+
+void rigaqep_destroy(rigaqep_problem* prob) {
+  if (!prob) return;
+  if (prob->impl.stream) cudaStreamSynchronize(prob->impl.stream);
+  delete prob;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the CUDA translation units of rigaqep.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/rigaqep.h"
+#include "plan.h"
+
+namespace rq {
+
+constexpr int kMaxKrylov = 96;   // largest Krylov dimension m
+constexpr int kMaxP = 8;         // largest B-spline degree
+
+// Error carried through the C++ layers and mapped to a status at the ABI.
+struct Error : std::runtime_error {
+  rigaqep_status code;
+  Error(rigaqep_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define RQ_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::rq::Error(e_ == cudaErrorMemoryAllocation ? RIGAQEP_ERR_OOM : RIGAQEP_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+// Owning device buffer.
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    RQ_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    alloc(h.size());
+    if (!h.empty()) RQ_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+};
+
+// Device-side status word written by kernels instead of trapping.
+struct DevStatus {
+  int32_t pivot_fail;   // first failing supernode + 1 (0 = none)
+  int32_t ritz_fail;    // QR iteration limit reached
+  int32_t internal;     // consistency check failed
+  int32_t pad;
+};
+
+// Output of the single-CTA Ritz kernel.
+struct RitzOut {
+  int32_t n_conv;       // wanted pairs (first neig) with estimate <= tol
+  int32_t k;            // kept dimension after reordering (restart)
+  int32_t fail;         // QR did not converge
+  int32_t sweeps;       // Francis double-shift sweeps of this step
+  double beta;
+  double lam[2 * kMaxKrylov];    // wanted lambdas (re, im), first neig
+  double est[kMaxKrylov];        // Ritz estimates of the wanted pairs
+};
+
+struct Problem {
+  Plan plan;
+  cudaStream_t stream = nullptr;
+  bool analyzed = false;
+  bool factored = false;
+  double fact_sigma = 0.0;
+  rigaqep_info info{};
+
+  // original-order CSR and values
+  DBuf<int32_t> rowptr, col;
+  DBuf<double> K, M, C;
+  DBuf<double> sigma_e;
+  DBuf<double> m1, k1;          // 1-D element mass / stiffness integrals
+  DBuf<int> first_fn;           // first full function of each element
+  // ND-ordered CSR and values
+  DBuf<int32_t> rowptr_n, col_n, fpos;
+  DBuf<int64_t> slot_map;
+  DBuf<double> Kn, Mn, Cn;
+  // symbolic on device
+  DBuf<int32_t> perm, iperm, sptr, upd_ptr, upd_idx, relmap, child_ptr, child_idx, lvl_nodes;
+  DBuf<int64_t> loff, uoff;
+  // numeric factor
+  DBuf<double> Lval, Uval, Dinv;
+  DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
+  DBuf<double> xwork;           // FB work vector (N)
+  DBuf<double> zbuf, wbuf;      // FB intermediates (N)
+  DBuf<int32_t> fwd_items, bwd_items;   // FB work items (front, start, count, 0)
+  std::vector<int32_t> fwd_lvl, bwd_lvl;  // work items of each level
+  // Krylov workspace
+  DBuf<double> V, Vtmp, H, part, hvec, wvec, yop, scal, Y;
+  DBuf<RitzOut> ritz;
+  DBuf<unsigned> counter;       // last-block-done counters of the fused reductions
+  DBuf<DevStatus> status;
+  int64_t Np = 0;               // N rounded up to 32
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double sigma_min = 0.0, sigma_max = 0.0;  // extremes of the damping coefficients
+  int64_t launches = 0;         // kernel launches of the current call
+  std::vector<int32_t> h_lvl_ptr;
+  std::vector<int32_t> lvl_maxF;  // largest front order per level
+  std::vector<int32_t> lvl_maxK;
+  ~Problem();
+};
+
+// kernels / launch helpers (each .cu file)
+void launch_assemble(Problem& P);
+void launch_permute_values(Problem& P);
+void launch_norms(Problem& P);
+void launch_factor(Problem& P, double sigma);
+void factor_configure(size_t smem_max);
+void fb_plan(Problem& P);
+// FB solve of Q x = b in the ND order, in place on xn (device, length N).
+// If vu != nullptr the backward sweep writes r_u = -x to ru and
+// r_l = sigma * r_u + vu to rl instead of writing x back (the operator step).
+void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl);
+void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n, int32_t ld_in,
+                   int32_t ncol, cudaStream_t s);
+void launch_scatter(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);
+// Krylov pieces
+struct EigsParams {
+  int neig;        // pairs returned
+  int ncand;       // pairs converged around the shift
+  double target;   // selection point
+  double shift;    // spectral shift (Q factorised there)
+  bool in_region;  // selection by target among the candidates
+  int m, max_restarts;
+  double tol;
+  uint64_t seed;
+};
+void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
+              double* eta, int* n_conv);
+void grad_run(Problem& P, int neig, const double* lambda, const double* X, double* G);
+
+}  // namespace rq
+
+struct rigaqep_problem {
+  rq::Problem impl;
+};

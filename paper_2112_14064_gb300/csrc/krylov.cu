@@ -1,0 +1,758 @@
+// Shift-and-invert Krylov-Schur on the linearised QEP (FP64), device side.
+//
+// Linearisation (paper Eq. Linearization): A = [[0, I], [-K, -C]],
+// B = diag(I, M).  Operator (Eq. BlockOperatorVector):
+//   r_u = -Q(s)^{-1} (s M v_u + C v_u + M v_l),   r_l = s r_u + v_u.
+// B-inner product (Section 4.2.1): <x, y>_B = x_u^T y_u + x_l^T M y_l.
+// Arnoldi step j (Algorithms 1 and 2) with classical Gram-Schmidt applied
+// twice (CGS2): h = V^T B r, r -= V h (twice), h_{j+1,j} = ||r||_B,
+// v_{j+1} = r / h_{j+1,j}.  Ritz step and truncation: ritz.cu.
+//
+// The Krylov basis lives in the nested-dissection order of the factor, so
+// no permutation is needed per step: V is (2 Np) x (m+1), column-major,
+// column c = [v_u (Np); v_l (Np)] with Np = N rounded up to 32 (zero pad).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rq {
+
+size_t ritz_smem(int m);
+void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
+                 int kwant, int final_pass, double sigma, double tol, cudaStream_t s);
+
+namespace {
+
+constexpr int kSub = 8;  // lanes per CSR row
+
+// y_i = sum_q M_iq (s vu_q + vl_q) + C_iq vu_q  (fused s M v_u + C v_u + M v_l)
+__global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const double* Mv,
+                          const double* Cv, const double* vu, const double* vl, double s,
+                          double* y, int64_t N) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = t / kSub;
+  int sub = t % kSub;
+  double acc = 0.0;
+  if (r < N) {
+    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) {
+      int32_t c = col[q];
+      double u = vu[c];
+      acc += Mv[q] * (s * u + vl[c]) + Cv[q] * u;
+    }
+  }
+  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
+  if (r < N && sub == 0) y[r] = acc;
+}
+
+__global__ void k_spmv(const int32_t* rowptr, const int32_t* col, const double* A, const double* x,
+                       double* y, int64_t N) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = t / kSub;
+  int sub = t % kSub;
+  double acc = 0.0;
+  if (r < N) {
+    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) acc += A[q] * x[col[q]];
+  }
+  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
+  if (r < N && sub == 0) y[r] = acc;
+}
+
+// h[c] = sum_i V[i, c] x(i) over the 2 Np rows, x(i) = xa[i] (i < Np) or
+// xb[i - Np]; then H[c, j] += h[c].  Per-thread accumulators for all 64
+// columns, a butterfly transpose-reduction inside each warp (lane l ends with
+// columns 2l, 2l+1), a sum over the block's warps, and a fixed-order sum over
+// blocks by the last block to finish (counter in global memory).
+__global__ void __launch_bounds__(128) k_dots(const double* V, int64_t ld, int ncol,
+                                               const double* xa, const double* xb, int64_t Np,
+                                               double* part, unsigned* counter, double* h,
+                                               double* H, int ldh, int j, int c_off) {
+  double acc[64];
+#pragma unroll
+  for (int c = 0; c < 64; ++c) acc[c] = 0.0;
+  int64_t rows = 2 * Np;
+  // columns in warp-uniform chunks of 8 with unconditional (clamped) loads
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = i < Np ? xa[i] : xb[i - Np];
+    const double* vr = V + i;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 8) {
+      if (c0 < ncol) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = vr[ld * min(c0 + q, ncol - 1)];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[c0 + q] += (c0 + q < ncol ? v[q] : 0.0) * x;
+      }
+    }
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16, len = 64; o > 0; o >>= 1, len >>= 1) {
+    bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < len / 2; ++i) {
+      double send = up ? acc[i] : acc[i + len / 2];
+      double keep = up ? acc[i + len / 2] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  __shared__ double red[4][64];
+  __shared__ bool last;
+  red[warp][2 * lane] = acc[0];
+  red[warp][2 * lane + 1] = acc[1];
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    double sm = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
+    part[blockIdx.x * 64 + threadIdx.x] = sm;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // 128 threads: column c = tid & 63, half = tid >> 6 sums every other block
+  int c = threadIdx.x & 63, half = threadIdx.x >> 6;
+  double sm = 0.0;
+  for (int b = half; b < (int)gridDim.x; b += 2) sm += ((volatile double*)part)[b * 64 + c];
+  __syncthreads();
+  red[half][c] = sm;
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double v = red[0][threadIdx.x] + red[1][threadIdx.x];
+    h[c_off + threadIdx.x] = v;
+    H[c_off + threadIdx.x + (int64_t)ldh * j] += v;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// B-norm of z = [zu; zl]: sum zu^2 + zl . (M zl) with the SpMV fused (8 lanes
+// per row); the last block sets nrm = sqrt(sum), H[j+1, j] = nrm (if H),
+// scal = {1/nrm, nrm}.
+__global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double* Mv,
+                        const double* zu, const double* zl, int64_t N, double* part,
+                        unsigned* counter, double* H, int ldh, int j, double* scal) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = t / kSub;
+  int sub = t % kSub;
+  double acc = 0.0;
+  if (r < N) {
+    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) acc += Mv[q] * zl[col[q]];
+  }
+  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
+  double v = 0.0;
+  if (r < N && sub == 0) v = zl[r] * acc + zu[r] * zu[r];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double red[8];
+  __shared__ double r2[256];
+  __shared__ bool last;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sm += red[w];
+    part[blockIdx.x] = sm;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sm = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sm += ((volatile double*)part)[b];
+  r2[threadIdx.x] = sm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)blockDim.x; ++w) tot += r2[w];
+    double nr = sqrt(tot);
+    if (H) H[(j + 1) + (int64_t)ldh * j] = nr;
+    scal[0] = 1.0 / nr;
+    scal[1] = nr;
+    *counter = 0u;
+  }
+}
+
+// z[i] -= sum_c V[i, c] h[c] over the 2 Np rows of column z (ld stride in V)
+__global__ void k_update(const double* V, int64_t ld, int ncol, const double* h, double* z,
+                         int64_t rows) {
+  __shared__ double hs[kMaxKrylov + 1];
+  for (int t = threadIdx.x; t <= kMaxKrylov; t += blockDim.x) hs[t] = t < ncol ? h[t] : 0.0;
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  const double* vr = V + i;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = 0;
+  for (; c + 4 <= ncol; c += 4) {
+    double v0 = vr[ld * c], v1 = vr[ld * (c + 1)], v2 = vr[ld * (c + 2)], v3 = vr[ld * (c + 3)];
+    a0 += v0 * hs[c];
+    a1 += v1 * hs[c + 1];
+    a2 += v2 * hs[c + 2];
+    a3 += v3 * hs[c + 3];
+  }
+  for (; c < ncol; ++c) a0 += vr[ld * c] * hs[c];
+  z[i] -= (a0 + a1) + (a2 + a3);
+}
+
+__global__ void k_scale(double* z, const double* scal, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) z[i] *= scal[0];
+}
+
+// out[i, t] = sum_{c < m} V[i, c] Q[c, t] (restart / basis change); each
+// thread owns one row and 16 output columns t0 .. t0+15 (blockIdx.y).
+__global__ void k_basis_gemm(const double* V, int64_t ld, int m, const double* Q, int k,
+                             double* out, int64_t rows) {
+  extern __shared__ double qs[];
+  int t0 = blockIdx.y * 16;
+  int nt = min(16, k - t0);
+  for (int i = threadIdx.x; i < m * 16; i += blockDim.x) {
+    int c = i % m, q = i / m;
+    qs[i] = q < nt ? Q[c + m * (t0 + q)] : 0.0;
+  }
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  const double* vr = V + i;
+  for (int c = 0; c < m; ++c) {
+    double v = vr[ld * c];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] += v * qs[c + m * q];
+  }
+  for (int q = 0; q < nt; ++q) out[i + ld * (t0 + q)] = acc[q];
+}
+
+// start vector in the original order: splitmix64(seed + i) / 2^64 - 0.5
+__global__ void k_start_vector(uint64_t seed, double* v, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t z = seed + (uint64_t)i + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  v[i] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+}
+
+// V_u(:,0)[j] = v1[perm[j]], V_l(:,0)[j] = v1[N + perm[j]]
+__global__ void k_load_start(const double* v1, const int32_t* perm, double* V0, int64_t N,
+                             int64_t Np) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  int32_t o = perm[j];
+  V0[j] = v1[o];
+  V0[Np + j] = v1[N + o];
+}
+
+// Xn[i, t] = sum_c V_u[i, c] Y[c, t] (complex Y), scattered to the original order
+__global__ void k_eigvec(const double* V, int64_t ld, int m, const double* Y, int neig,
+                         const int32_t* perm, double* X, int64_t N) {
+  extern __shared__ double ys[];
+  for (int i = threadIdx.x; i < 2 * m * neig; i += blockDim.x) ys[i] = Y[i];
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  for (int t = 0; t < neig; ++t) {
+    double ar = 0.0, ai = 0.0;
+    for (int c = 0; c < m; ++c) {
+      double v = V[i + ld * c];
+      ar += v * ys[2 * (c + m * t)];
+      ai += v * ys[2 * (c + m * t) + 1];
+    }
+    X[2 * (o + N * t)] = ar;
+    X[2 * (o + N * t) + 1] = ai;
+  }
+}
+
+// per column: ||x||^2 and the largest |x_i| (lowest index on ties)
+__global__ void k_colstats(const double* X, int64_t N, double* stats) {
+  int t = blockIdx.x;
+  const double* x = X + 2 * N * t;
+  double s = 0.0, best = -1.0;
+  int64_t bi = 0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    double a2 = x[2 * i] * x[2 * i] + x[2 * i + 1] * x[2 * i + 1];
+    s += a2;
+    if (a2 > best) { best = a2; bi = i; }
+  }
+  __shared__ double ss[1024], sb[1024];
+  __shared__ int64_t si[1024];
+  ss[threadIdx.x] = s;
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      ss[threadIdx.x] += ss[threadIdx.x + w];
+      double b2 = sb[threadIdx.x + w];
+      int64_t i2 = si[threadIdx.x + w];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sb[threadIdx.x] = b2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    stats[4 * t] = ss[0];
+    stats[4 * t + 1] = (double)si[0];
+    stats[4 * t + 2] = x[2 * si[0]];
+    stats[4 * t + 3] = x[2 * si[0] + 1];
+  }
+}
+
+// x <- x * conj(x_imax) / (|x_imax| ||x||)
+__global__ void k_colnormalise(double* X, int64_t N, const double* stats) {
+  int t = blockIdx.y;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double* x = X + 2 * N * t;
+  double pr = stats[4 * t + 2], pi = stats[4 * t + 3];
+  double pa = hypot(pr, pi);
+  double sc = 1.0 / (pa * sqrt(stats[4 * t]));
+  // (a + ib)(pr - i pi)
+  double a = x[2 * i], b = x[2 * i + 1];
+  double nr = (a * pr + b * pi) * sc, ni = (b * pr - a * pi) * sc;
+  x[2 * i] = nr;
+  x[2 * i + 1] = ni;
+}
+
+// partial sums of ||K x + l C x + l^2 M x||^2 and ||x||^2 for column t
+__global__ void k_qres(const int32_t* rowptr, const int32_t* col, const double* K, const double* M,
+                       const double* C, const double* X, const double* lam, int64_t N,
+                       double* part) {
+  int t = blockIdx.y;
+  const double* x = X + 2 * N * t;
+  double lr = lam[2 * t], li = lam[2 * t + 1];
+  double l2r = lr * lr - li * li, l2i = 2 * lr * li;
+  double s = 0.0, sx = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double kr = 0, ki = 0, cr = 0, ci = 0, mr = 0, mi = 0;
+    for (int32_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+      double xr = x[2 * col[q]], xi = x[2 * col[q] + 1];
+      kr += K[q] * xr; ki += K[q] * xi;
+      cr += C[q] * xr; ci += C[q] * xi;
+      mr += M[q] * xr; mi += M[q] * xi;
+    }
+    double rr = kr + (lr * cr - li * ci) + (l2r * mr - l2i * mi);
+    double ri = ki + (lr * ci + li * cr) + (l2r * mi + l2i * mr);
+    s += rr * rr + ri * ri;
+    sx += x[2 * r] * x[2 * r] + x[2 * r + 1] * x[2 * r + 1];
+  }
+  __shared__ double a[256], b[256];
+  a[threadIdx.x] = s;
+  b[threadIdx.x] = sx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) { a[threadIdx.x] += a[threadIdx.x + w]; b[threadIdx.x] += b[threadIdx.x + w]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * (blockIdx.x + gridDim.x * t)] = a[0];
+    part[2 * (blockIdx.x + gridDim.x * t) + 1] = b[0];
+  }
+}
+
+__global__ void k_eta(const double* part, int nblk, const double* lam, double nK, double nM,
+                      double nC, double* eta, int neig) {
+  int t = threadIdx.x;
+  if (t >= neig) return;
+  double s = 0.0, sx = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    s += part[2 * (b + nblk * t)];
+    sx += part[2 * (b + nblk * t) + 1];
+  }
+  double al = hypot(lam[2 * t], lam[2 * t + 1]);
+  eta[t] = sqrt(s) / ((al * al * nM + al * nC + nK) * sqrt(sx));
+}
+
+__global__ void k_copy_lam(const RitzOut* out, double* lam, int neig) {
+  int t = threadIdx.x;
+  if (t < 2 * neig) lam[t] = out->lam[t];
+}
+
+// ---- damping sensitivity ----
+// partial sums of x^T (2 l M + C) x (unconjugated) for column t
+__global__ void k_gden(const int32_t* rowptr, const int32_t* col, const double* M, const double* C,
+                       const double* X, const double* lam, int64_t N, double* part) {
+  int t = blockIdx.y;
+  const double* x = X + 2 * N * t;
+  double lr = lam[2 * t], li = lam[2 * t + 1];
+  double sr = 0.0, si = 0.0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double mr = 0, mi = 0, cr = 0, ci = 0;
+    for (int32_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+      double xr = x[2 * col[q]], xi = x[2 * col[q] + 1];
+      mr += M[q] * xr; mi += M[q] * xi;
+      cr += C[q] * xr; ci += C[q] * xi;
+    }
+    // w = 2 l (Mx) + Cx ; accumulate x_r * w
+    double wr = 2 * (lr * mr - li * mi) + cr, wi = 2 * (lr * mi + li * mr) + ci;
+    double xr = x[2 * r], xi = x[2 * r + 1];
+    sr += xr * wr - xi * wi;
+    si += xr * wi + xi * wr;
+  }
+  __shared__ double a[256], b[256];
+  a[threadIdx.x] = sr;
+  b[threadIdx.x] = si;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) { a[threadIdx.x] += a[threadIdx.x + w]; b[threadIdx.x] += b[threadIdx.x + w]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * (blockIdx.x + gridDim.x * t)] = a[0];
+    part[2 * (blockIdx.x + gridDim.x * t) + 1] = b[0];
+  }
+}
+
+__global__ void k_gden_final(const double* part, int nblk, int neig, double* den) {
+  int t = threadIdx.x;
+  if (t >= neig) return;
+  double sr = 0, si = 0;
+  for (int b = 0; b < nblk; ++b) { sr += part[2 * (b + nblk * t)]; si += part[2 * (b + nblk * t) + 1]; }
+  den[2 * t] = sr;
+  den[2 * t + 1] = si;
+}
+
+// G[t, e] = -l_t q_{t,e} / den_t with q = x_e^T (mx (x) my) x_e over the
+// element's (p+1)^2 functions (Dirichlet functions carry no DOF)
+__global__ void k_grad(const double* X, const double* lam, const double* den, const double* m1,
+                       const int* first_fn, int ne, int p, int n1, int64_t N, int neig,
+                       double* G) {
+  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t ne2 = (int64_t)ne * ne;
+  if (tid >= ne2 * neig) return;
+  int t = tid / ne2;
+  int64_t e = tid % ne2;
+  int ex = e % ne, ey = e / ne;
+  int np1 = p + 1;
+  const double* x = X + 2 * N * t;
+  double xr[kMaxP + 1][kMaxP + 1], xi[kMaxP + 1][kMaxP + 1];
+  for (int a = 0; a < np1; ++a)
+    for (int b = 0; b < np1; ++b) {
+      int dx = first_fn[ex] + a - 1, dy = first_fn[ey] + b - 1;
+      if (dx >= 0 && dx < n1 && dy >= 0 && dy < n1) {
+        int64_t d = dx + (int64_t)n1 * dy;
+        xr[a][b] = x[2 * d];
+        xi[a][b] = x[2 * d + 1];
+      } else {
+        xr[a][b] = 0.0;
+        xi[a][b] = 0.0;
+      }
+    }
+  const double* mx = m1 + (int64_t)ex * np1 * np1;
+  const double* my = m1 + (int64_t)ey * np1 * np1;
+  double qr = 0.0, qi = 0.0;
+  for (int b = 0; b < np1; ++b)
+    for (int d = 0; d < np1; ++d) {
+      // W[b][d] = sum_{a,c} x[a][b] mx[a][c] x[c][d]
+      double wr = 0.0, wi = 0.0;
+      for (int a = 0; a < np1; ++a) {
+        double tr = 0.0, ti = 0.0;
+        for (int c = 0; c < np1; ++c) {
+          double mac = mx[a * np1 + c];
+          tr += mac * xr[c][d];
+          ti += mac * xi[c][d];
+        }
+        wr += xr[a][b] * tr - xi[a][b] * ti;
+        wi += xr[a][b] * ti + xi[a][b] * tr;
+      }
+      double mbd = my[b * np1 + d];
+      qr += mbd * wr;
+      qi += mbd * wi;
+    }
+  // g = -l q / den
+  double lr = lam[2 * t], li = lam[2 * t + 1];
+  double nr = -(lr * qr - li * qi), ni = -(lr * qi + li * qr);
+  double dr = den[2 * t], di = den[2 * t + 1];
+  double dd = dr * dr + di * di;
+  G[2 * (e + ne2 * t)] = (nr * dr + ni * di) / dd;
+  G[2 * (e + ne2 * t) + 1] = (ni * dr - nr * di) / dd;
+}
+
+struct Work {
+  Problem& P;
+  int m;
+  int64_t N, Np, ld;
+  int nblk;
+  cudaStream_t s;
+  double sigma;
+  int64_t n_apply = 0, n_spmv = 0, n_vv = 0;
+  // FB timing: event pairs around every FB solve of one restart cycle
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  double fb_ms = 0.0;
+  ~Work() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  void fb_events(int count) {
+    while ((int)ev.size() < 2 * count) {
+      cudaEvent_t e;
+      RQ_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+  }
+  // after a stream synchronisation: add the elapsed FB time of this cycle
+  void fb_collect() {
+    for (int i = 0; i + 1 < ev_used; i += 2) {
+      float ms = 0.f;
+      RQ_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      fb_ms += ms;
+    }
+    ev_used = 0;
+  }
+
+  double* col(int c) { return P.V.p + ld * c; }
+
+  void dots(int j, const double* xa, const double* xb) {
+    for (int c0 = 0; c0 <= j; c0 += 64) {
+      int nc = std::min(64, j + 1 - c0);
+      k_dots<<<nblk, 128, 0, s>>>(P.V.p + ld * c0, ld, nc, xa, xb, Np, P.part.p, P.counter.p,
+                                  P.hvec.p, P.H.p, m + 1, j, c0);
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
+  }
+  void spmv(const double* A, const double* x, double* y) {
+    int64_t thr = N * kSub;
+    k_spmv<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, A, x, y, N);
+    RQ_CUDA(cudaGetLastError());
+    ++n_spmv;
+    ++P.launches;
+  }
+  // B-norm of column c -> H[c, c-1] (if setH) and V[:, c] normalised
+  void normalise(int c, bool setH) {
+    double* z = col(c);
+    int64_t thr = N * kSub;
+    unsigned nb = (unsigned)((thr + 255) / 256);
+    k_bnorm<<<nb, 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, P.Mn.p, z, z + Np, N, P.part.p,
+                               P.counter.p + 1, setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p);
+    RQ_CUDA(cudaGetLastError());
+    ++n_spmv;
+    P.launches += 2;
+    k_scale<<<(unsigned)((2 * Np + 255) / 256), 256, 0, s>>>(z, P.scal.p, 2 * Np);
+    RQ_CUDA(cudaGetLastError());
+    n_vv += 2;
+  }
+  void step(int j) {
+    double* v = col(j);
+    double* r = col(j + 1);
+    int64_t thr = N * kSub;
+    k_spmv_op<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, P.Mn.p, P.Cn.p,
+                                                            v, v + Np, sigma, P.yop.p, N);
+    RQ_CUDA(cudaGetLastError());
+    n_spmv += 3;
+    RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+    launch_fb(P, P.yop.p, sigma, v, r, r + Np);
+    RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+    ++n_apply;
+    for (int pass = 0; pass < 2; ++pass) {
+      spmv(P.Mn.p, r + Np, P.wvec.p);
+      dots(j, r, P.wvec.p);
+      k_update<<<(unsigned)((2 * Np + 255) / 256), 256, 0, s>>>(P.V.p, ld, j + 1, P.hvec.p, r, 2 * Np);
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+      n_vv += 4 * (j + 1);
+    }
+    normalise(j + 1, true);
+  }
+};
+
+}  // namespace
+
+void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
+              double* eta, int* n_conv) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int m = E.m, max_restarts = E.max_restarts;
+  const int nks = E.ncand;          // pairs converged around the shift
+  const double sigma = E.shift, tol = E.tol;
+  const uint64_t seed = E.seed;
+  Work W{P, m, L.N, 0, 0, 0, s, sigma};
+  W.fb_events(m + 1);
+  W.Np = (L.N + 31) / 32 * 32;
+  W.ld = 2 * W.Np;
+  W.nblk = 2 * 152;
+  int64_t ld = W.ld, Np = W.Np, N = L.N;
+  P.V.alloc(ld * (m + 1));
+  P.Vtmp.alloc(ld * m);
+  P.H.alloc((m + 1) * m);
+  P.part.alloc(64 * (size_t)std::max(W.nblk, 4 * 1024) + (size_t)(L.N * 8 + 255) / 256);
+  P.counter.alloc(4);
+  RQ_CUDA(cudaMemsetAsync(P.counter.p, 0, 4 * sizeof(unsigned), s));
+  P.hvec.alloc(kMaxKrylov + 1);
+  P.wvec.alloc(Np);
+  P.yop.alloc(Np);
+  P.scal.alloc(4);
+  P.Y.alloc(2 * (size_t)m * kMaxKrylov);
+  P.ritz.alloc(1);
+  DBuf<double> Hn, Qb, v1buf;
+  Hn.alloc((m + 1) * m);
+  Qb.alloc((size_t)m * m);
+  RQ_CUDA(cudaMemsetAsync(P.V.p, 0, sizeof(double) * ld * (m + 1), s));
+  RQ_CUDA(cudaMemsetAsync(P.Vtmp.p, 0, sizeof(double) * ld * m, s));
+  RQ_CUDA(cudaMemsetAsync(P.H.p, 0, sizeof(double) * (m + 1) * m, s));
+  RQ_CUDA(cudaMemsetAsync(P.wvec.p, 0, sizeof(double) * Np, s));
+  RQ_CUDA(cudaEventRecord(P.ev0, s));
+
+  const double* start = v1;
+  if (!start) {
+    v1buf.alloc(2 * N);
+    k_start_vector<<<(unsigned)((2 * N + 255) / 256), 256, 0, s>>>(seed, v1buf.p, 2 * N);
+    RQ_CUDA(cudaGetLastError());
+    start = v1buf.p;
+  }
+  k_load_start<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(start, P.perm.p, P.V.p, N, Np);
+  RQ_CUDA(cudaGetLastError());
+  W.normalise(0, false);
+
+  int kwant = nks + (m - nks) / 2;
+  int k = 0;
+  RitzOut h_out{};
+  int restarts = 0;
+  int64_t qr_sweeps = 0;
+  for (int it = 0;; ++it) {
+    for (int j = k; j < m; ++j) W.step(j);
+    launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 0, sigma, tol, s);
+    ++P.launches;
+    RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
+    RQ_CUDA(cudaStreamSynchronize(s));
+    W.fb_collect();
+    if (h_out.fail) throw Error(RIGAQEP_ERR_INTERNAL, "QR iteration on the projected matrix did not converge");
+    qr_sweeps += h_out.sweeps;
+    if (h_out.n_conv >= nks || it >= max_restarts) break;
+    k = h_out.k;
+    // V[:, :k] = V[:, :m] Q ; V[:, k] = V[:, m] ; H = Hnew
+    size_t smem = sizeof(double) * (size_t)m * 16;
+    dim3 gg((unsigned)((ld + 127) / 128), (unsigned)((k + 15) / 16));
+    k_basis_gemm<<<gg, 128, smem, s>>>(P.V.p, ld, m, Qb.p, k, P.Vtmp.p, ld);
+    RQ_CUDA(cudaGetLastError());
+    ++P.launches;
+    RQ_CUDA(cudaMemcpyAsync(P.V.p, P.Vtmp.p, sizeof(double) * ld * k, cudaMemcpyDeviceToDevice, s));
+    RQ_CUDA(cudaMemcpyAsync(P.V.p + ld * k, P.V.p + ld * m, sizeof(double) * ld,
+                            cudaMemcpyDeviceToDevice, s));
+    RQ_CUDA(cudaMemcpyAsync(P.H.p, Hn.p, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToDevice, s));
+    ++restarts;
+  }
+  // final pass: eigenvectors of H for the candidate Ritz values
+  launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 1, sigma, tol, s);
+  ++P.launches;
+  RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  W.fb_collect();
+  // selection of the neig candidates nearest the target (Im > 0 first on
+  // ties), and the certificate that no other eigenvalue is nearer
+  const int neig = E.neig;
+  std::vector<int> order(nks);
+  for (int i = 0; i < nks; ++i) order[i] = i;
+  auto dist = [&](int i) { return std::hypot(h_out.lam[2 * i] - E.target, h_out.lam[2 * i + 1]); };
+  auto cls = [&](int i) { double im = h_out.lam[2 * i + 1]; return im > 0 ? 0 : (im == 0 ? 1 : 2); };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    double da = dist(a), db = dist(b);
+    if (da != db) return da < db;
+    return cls(a) < cls(b);
+  });
+  bool all_conv = true;
+  for (int i = 0; i < nks; ++i) all_conv = all_conv && (h_out.est[i] <= tol);
+  int sel_conv = 0;
+  double dmax = 0.0;
+  for (int q = 0; q < neig; ++q) {
+    sel_conv += h_out.est[order[q]] <= tol ? 1 : 0;
+    dmax = std::max(dmax, dist(order[q]));
+  }
+  double margin = -1.0;
+  bool cert = false;
+  if (!E.in_region) {
+    cert = all_conv;
+    margin = 0.0;
+  } else if (all_conv && E.shift >= 0.0 && E.target >= E.shift && P.sigma_min >= 0.0) {
+    double r = 0.0;
+    for (int i = 0; i < nks; ++i)
+      r = std::max(r, std::hypot(h_out.lam[2 * i] - E.shift, h_out.lam[2 * i + 1]));
+    double ts = E.target - E.shift;
+    double bc = std::sqrt(r * r + ts * (E.target + E.shift + P.sigma_min));
+    double br = ts + r;
+    double bound = std::min(bc, br);
+    margin = bound - dmax;
+    cert = bound >= dmax * (1.0 + 1e-12);
+  }
+  P.info.certified = cert ? 1 : 0;
+  P.info.cert_margin = margin;
+  std::vector<double> lam_sel(2 * neig);
+  DBuf<double> Ysel;
+  Ysel.alloc(2 * (size_t)m * neig);
+  for (int q = 0; q < neig; ++q) {
+    int i = order[q];
+    lam_sel[2 * q] = h_out.lam[2 * i];
+    lam_sel[2 * q + 1] = h_out.lam[2 * i + 1];
+    RQ_CUDA(cudaMemcpyAsync(Ysel.p + 2 * (size_t)m * q, P.Y.p + 2 * (size_t)m * i,
+                            sizeof(double) * 2 * m, cudaMemcpyDeviceToDevice, s));
+  }
+  RQ_CUDA(cudaMemcpyAsync(lambda, lam_sel.data(), sizeof(double) * 2 * neig, cudaMemcpyHostToDevice, s));
+  {
+    size_t smem = sizeof(double) * 2 * (size_t)m * neig;
+    RQ_CUDA(cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_eigvec<<<(unsigned)((N + 127) / 128), 128, smem, s>>>(P.V.p, ld, m, Ysel.p, neig, P.perm.p, X, N);
+    RQ_CUDA(cudaGetLastError());
+  }
+  DBuf<double> stats;
+  stats.alloc(4 * (size_t)neig);
+  k_colstats<<<neig, 1024, 0, s>>>(X, N, stats.p);
+  RQ_CUDA(cudaGetLastError());
+  dim3 g((unsigned)((N + 255) / 256), neig);
+  k_colnormalise<<<g, 256, 0, s>>>(X, N, stats.p);
+  RQ_CUDA(cudaGetLastError());
+  int qb = 2 * 152;
+  dim3 gq(qb, neig);
+  k_qres<<<gq, 256, 0, s>>>(P.rowptr.p, P.col.p, P.K.p, P.M.p, P.C.p, X, lambda, N, P.part.p);
+  RQ_CUDA(cudaGetLastError());
+  k_eta<<<1, 64, 0, s>>>(P.part.p, qb, lambda, P.info.norm_K, P.info.norm_M, P.info.norm_C, eta, neig);
+  RQ_CUDA(cudaGetLastError());
+  P.launches += 5;
+  RQ_CUDA(cudaEventRecord(P.ev1, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+  P.info.eigs_ms = ms;
+  P.info.n_apply = W.n_apply;
+  P.info.n_restarts = restarts;
+  P.info.n_spmv = W.n_spmv;
+  P.info.n_vv = W.n_vv;
+  P.info.n_qr_sweeps = qr_sweeps;
+  P.info.fb_ms = W.fb_ms;
+  P.info.n_launches = P.launches;
+  *n_conv = sel_conv;
+}
+
+void grad_run(Problem& P, int neig, const double* lambda, const double* X, double* G) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  int64_t N = L.N;
+  int nb = 2 * 152;
+  DBuf<double> part, den;
+  part.alloc(2 * (size_t)nb * neig);
+  den.alloc(2 * (size_t)neig);
+  dim3 g(nb, neig);
+  k_gden<<<g, 256, 0, s>>>(P.rowptr.p, P.col.p, P.M.p, P.C.p, X, lambda, N, part.p);
+  RQ_CUDA(cudaGetLastError());
+  k_gden_final<<<1, 64, 0, s>>>(part.p, nb, neig, den.p);
+  RQ_CUDA(cudaGetLastError());
+  int64_t tot = (int64_t)L.ne * L.ne * neig;
+  k_grad<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(X, lambda, den.p, P.m1.p, P.first_fn.p, L.ne,
+                                                       L.p, L.n1, N, neig, G);
+  RQ_CUDA(cudaGetLastError());
+  RQ_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace rq

@@ -1,0 +1,54 @@
+// Host-side integer planning: univariate spaces, CSR pattern, separator
+// nested dissection, supernodal symbolic factorisation and front maps.
+// No CUDA dependency: everything here is plain C++ on int32/int64.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace rq {
+
+struct Space1D {
+  int ne = 0, p = 0, block = 0;
+  std::vector<int> knots;   // knot numerators over ne (exact)
+  int n_full = 0;           // B-splines on the open knot vector
+  int n = 0;                // DOFs after the two Dirichlet functions are dropped
+  std::vector<int> c0;      // DOF indices of the C^0 separator functions
+  std::vector<int> elo, ehi;  // DOF d lives on elements [elo[d], ehi[d])
+  std::vector<int> first_fn;  // element ex carries full functions first_fn[ex]..+p
+  void build(int ne_, int p_, int block_);
+  bool coupled(int a, int b) const;  // DOFs a, b share an open interval
+};
+
+struct Plan {
+  // mesh
+  int ne = 0, p = 0, block = 0, nq = 0, leaf_min = 8;
+  Space1D sp;
+  int n1 = 0;
+  int64_t N = 0, nnz = 0;
+  // original-order CSR pattern (columns ascending)
+  std::vector<int32_t> rowptr, col;
+  // ordering and supernodes
+  std::vector<int32_t> perm, iperm, sptr, owner;
+  int nsuper = 0;
+  std::vector<int32_t> parent, level, upd_ptr, upd_idx;
+  int nlevels = 0;
+  std::vector<int32_t> child_ptr, child_idx;  // children of each supernode
+  // ND-ordered CSR (columns ascending) and the map to original slots
+  std::vector<int32_t> rowptr_n, col_n;
+  std::vector<int64_t> slot_map;   // slot_map[new slot] = original slot
+  std::vector<int32_t> fpos;       // front row of a new-order slot, -1 if col < row
+  // front storage layout
+  std::vector<int64_t> loff;       // factor panel of s: (k+u) x k, column-major
+  std::vector<int64_t> uoff;       // update block of s: u x u, column-major
+  std::vector<int32_t> relmap;     // for each s: struct(s) -> position in parent's front
+  int64_t l_total = 0, u_total = 0;
+  std::vector<int32_t> lvl_ptr, lvl_nodes;  // supernodes of each level, ascending
+  int64_t nnz_L = 0, flops = 0, max_front = 0;
+
+  // build the pattern only (assemble) and the symbolic phase (analyze)
+  void build_pattern(int ne_, int p_, int block_, int nq_, int leaf_min_);
+  void build_symbolic();
+};
+
+}  // namespace rq

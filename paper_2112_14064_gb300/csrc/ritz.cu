@@ -1,0 +1,634 @@
+// Rayleigh-Ritz step and Krylov-Schur truncation on the device (FP64).
+//
+// Input: the (m+1) x m projected matrix of a Krylov decomposition
+//   S V_m = V_m H_m + h_{m+1,m} v_{m+1} e_m^T   (paper Eq. Arnoldi; after a
+//   restart the leading k x k block is quasi-triangular with a spike row).
+// Ritz values theta of H_m approximate the eigenvalues of the shift-and-invert
+// operator (Eq. ArnoldiRitz); lambda = s + 1/theta (Section 4.1.1).  The
+// restart keeps the invariant subspace of the wanted Ritz values (Krylov-Schur,
+// Section 4.1.3, which the paper cites without details).
+//
+// One CTA of four warps (one per SM sub-partition, so the FP64 row and column
+// updates use all four FP64 pipes) does the whole step in shared memory:
+//   1. Householder reduction of H_m to Hessenberg form, Z accumulated;
+//   2. Francis double-shift QR to real Schur form T = Z^T H_m Z, 2x2 blocks
+//      standardised (equal diagonal for complex pairs, split when real);
+//   3. rank of every Ritz value by |lambda - s| (Im > 0 first on ties);
+//   4. eigenvectors of the wanted values by back-substitution on T, Ritz
+//      estimates |h_{m+1,m} e_m^T Z y| / (|theta| ||y||);
+//   5. restart: the wanted blocks are moved to the top of T by adjacent block
+//      swaps (each swap solves the small Sylvester equation A X - X B = C and
+//      applies the orthogonal factor of [X; -I]); the new projected matrix is
+//      [T_kk ; h_{m+1,m} Z(m,1:k)] and the kept basis is V Z(:,1:k).
+#include "internal.h"
+
+namespace rq {
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+constexpr int NT = 128;   // threads of the Ritz CTA
+
+struct RitzArgs {
+  const double* H;   // (m+1) x m, column-major, ld = m+1
+  double* Hnew;      // restart matrix, same layout
+  double* Q;         // m x k kept Schur vectors, ld = m
+  double* Y;         // final: m x neig eigenvectors of H_m (re, im interleaved)
+  RitzOut* out;
+  int m, neig, kwant, final_pass;
+  double sigma, tol;
+};
+
+struct Smem {
+  double* T;   // m x m, column-major
+  double* Z;   // m x m
+  double* v;   // Householder vector (m)
+  double* wr;  // Ritz values (Schur order)
+  double* wi;
+  int* rank;
+  int* sel;
+  double* yr;  // one eigenvector of T (re, im)
+  double* yi;
+  double* sr;  // running right-hand sides of the back-substitution
+  double* si;
+  double* red; // 4 partial sums
+};
+
+#define TT(r, c) S.T[(r) + m * (c)]
+#define ZZ(r, c) S.Z[(r) + m * (c)]
+
+// Householder reflector for x[0..n): (I - tau v v^T) x = beta e_0, v[0] = 1.
+// All threads compute it redundantly from the same data.
+__device__ void house(const double* x, int n, double* v, double& tau, double& beta) {
+  double alpha = x[0], sg = 0.0;
+  for (int i = 1; i < n; ++i) sg += x[i] * x[i];
+  v[0] = 1.0;
+  if (sg == 0.0) {
+    tau = 0.0;
+    beta = alpha;
+    for (int i = 1; i < n; ++i) v[i] = 0.0;
+    return;
+  }
+  double nr = sqrt(alpha * alpha + sg);
+  beta = alpha <= 0.0 ? nr : -nr;
+  double d = alpha - beta;
+  for (int i = 1; i < n; ++i) v[i] = x[i] / d;
+  tau = (beta - alpha) / beta;
+}
+
+// rows r0..r0+n-1 of A (ld m) <- P rows, columns c0..c1-1, threads over columns
+__device__ void apply_left(double* A, int m, const double* v, double tau, int n, int r0, int c0,
+                           int c1, int lane) {
+  if (tau == 0.0) return;
+  for (int c = c0 + lane; c < c1; c += NT) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += v[i] * A[(r0 + i) + m * c];
+    s *= tau;
+    for (int i = 0; i < n; ++i) A[(r0 + i) + m * c] -= s * v[i];
+  }
+}
+
+// columns c0..c0+n-1 of A <- cols P, rows r0..r1-1, threads over rows
+__device__ void apply_right(double* A, int m, const double* v, double tau, int n, int c0, int r0,
+                            int r1, int lane) {
+  if (tau == 0.0) return;
+  for (int r = r0 + lane; r < r1; r += NT) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += v[i] * A[r + m * (c0 + i)];
+    s *= tau;
+    for (int i = 0; i < n; ++i) A[r + m * (c0 + i)] -= s * v[i];
+  }
+}
+
+// Plane rotation G = [[c, -s], [s, c]] on rows/cols j, j+1: T <- G^T T G, Z <- Z G
+__device__ void rotate(Smem& S, int m, int j, double c, double s, int lane) {
+  __syncthreads();
+  for (int col = j + lane; col < m; col += NT) {
+    double a = TT(j, col), b = TT(j + 1, col);
+    TT(j, col) = c * a + s * b;
+    TT(j + 1, col) = -s * a + c * b;
+  }
+  __syncthreads();
+  for (int r = lane; r < m; r += NT) {
+    if (r <= j + 1) {
+      double a = TT(r, j), b = TT(r, j + 1);
+      TT(r, j) = c * a + s * b;
+      TT(r, j + 1) = -s * a + c * b;
+    }
+    double a = ZZ(r, j), b = ZZ(r, j + 1);
+    ZZ(r, j) = c * a + s * b;
+    ZZ(r, j + 1) = -s * a + c * b;
+  }
+  __syncthreads();
+}
+
+// Standardise the 2x2 diagonal block at j: split it (exact zero below the
+// diagonal) when its eigenvalues are real, else make its diagonal equal.
+// Returns true when the block stays a complex pair.
+__device__ bool standardize2(Smem& S, int m, int j, int lane) {
+  double a = TT(j, j), b = TT(j, j + 1), e = TT(j + 1, j), d = TT(j + 1, j + 1);
+  if (e == 0.0) return false;
+  double hp = 0.5 * (a - d);
+  double disc = hp * hp + b * e;
+  double c, s;
+  bool cplx;
+  if (disc >= 0.0) {
+    // eigenvector of the eigenvalue l1; g1 = (c, s) spans it
+    double rt = sqrt(disc);
+    double l1 = 0.5 * (a + d) + (hp >= 0.0 ? rt : -rt);
+    double x1 = b, y1 = l1 - a;      // from the first row
+    double x2 = l1 - d, y2 = e;      // from the second row
+    double n1 = x1 * x1 + y1 * y1, n2 = x2 * x2 + y2 * y2;
+    double x = n1 >= n2 ? x1 : x2, y = n1 >= n2 ? y1 : y2;
+    double nr = sqrt(x * x + y * y);
+    c = x / nr;
+    s = y / nr;
+    cplx = false;
+  } else {
+    // T'11 - T'22 = cos(2t)(a - d) + sin(2t)(b + e) = 0
+    double th = 0.5 * atan2(-(a - d), b + e);
+    c = cos(th);
+    s = sin(th);
+    cplx = true;
+  }
+  rotate(S, m, j, c, s, lane);
+  if (!cplx) {
+    if (lane == 0) TT(j + 1, j) = 0.0;
+  } else if (lane == 0) {
+    double avg = 0.5 * (TT(j, j) + TT(j + 1, j + 1));
+    TT(j, j) = avg;
+    TT(j + 1, j + 1) = avg;
+  }
+  __syncthreads();
+  return cplx;
+}
+
+// Swap the adjacent diagonal blocks at j (size n1) and j+n1 (size n2).
+__device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm, int lane) {
+  int n = n1 + n2;
+  double A[2][2], B[2][2], Cm[2][2];
+  for (int r = 0; r < n1; ++r)
+    for (int c = 0; c < n1; ++c) A[r][c] = TT(j + r, j + c);
+  for (int r = 0; r < n2; ++r)
+    for (int c = 0; c < n2; ++c) B[r][c] = TT(j + n1 + r, j + n1 + c);
+  for (int r = 0; r < n1; ++r)
+    for (int c = 0; c < n2; ++c) Cm[r][c] = TT(j + r, j + n1 + c);
+  // Sylvester A X - X B = C, unknown X[r][c] at index r + n1*c
+  int ns = n1 * n2;
+  double G[4][5];
+  for (int r = 0; r < n1; ++r)
+    for (int c = 0; c < n2; ++c) {
+      int row = r + n1 * c;
+      for (int r2 = 0; r2 < n1; ++r2)
+        for (int c2 = 0; c2 < n2; ++c2) {
+          int cc = r2 + n1 * c2;
+          double v = 0.0;
+          if (c == c2) v += A[r][r2];
+          if (r == r2) v -= B[c2][c];
+          G[row][cc] = v;
+        }
+      G[row][ns] = Cm[r][c];
+    }
+  double smin = fmax(kEps * tnorm, 1e-300);
+  for (int col = 0; col < ns; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < ns; ++r)
+      if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
+    if (piv != col)
+      for (int c = 0; c <= ns; ++c) {
+        double t = G[col][c];
+        G[col][c] = G[piv][c];
+        G[piv][c] = t;
+      }
+    if (fabs(G[col][col]) < smin) G[col][col] = G[col][col] >= 0.0 ? smin : -smin;
+    for (int r = col + 1; r < ns; ++r) {
+      double f = G[r][col] / G[col][col];
+      for (int c = col; c <= ns; ++c) G[r][c] -= f * G[col][c];
+    }
+  }
+  double xs[4];
+  for (int r = ns - 1; r >= 0; --r) {
+    double t = G[r][ns];
+    for (int c = r + 1; c < ns; ++c) t -= G[r][c] * xs[c];
+    xs[r] = t / G[r][r];
+  }
+  // W = [X; -I] (n x n2); Householder QR, reflectors kept in vh
+  double W[4][2];
+  for (int r = 0; r < n1; ++r)
+    for (int c = 0; c < n2; ++c) W[r][c] = xs[r + n1 * c];
+  for (int r = 0; r < n2; ++r)
+    for (int c = 0; c < n2; ++c) W[n1 + r][c] = (r == c) ? -1.0 : 0.0;
+  double vh[2][4], tau[2];
+  for (int q = 0; q < n2; ++q) {
+    double x[4];
+    for (int i = q; i < n; ++i) x[i - q] = W[i][q];
+    double beta;
+    for (int i = 0; i < 4; ++i) vh[q][i] = 0.0;
+    house(x, n - q, vh[q] + q, tau[q], beta);
+    // apply to the remaining columns of W
+    for (int c = q + 1; c < n2; ++c) {
+      double s = 0.0;
+      for (int i = q; i < n; ++i) s += vh[q][i] * W[i][c];
+      s *= tau[q];
+      for (int i = q; i < n; ++i) W[i][c] -= s * vh[q][i];
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < n2; ++q) {
+    apply_left(S.T, m, vh[q], tau[q], n, j, j, m, lane);
+    __syncthreads();
+    apply_right(S.T, m, vh[q], tau[q], n, j, 0, j + n, lane);
+    apply_right(S.Z, m, vh[q], tau[q], n, j, 0, m, lane);
+    __syncthreads();
+  }
+  if (lane == 0)
+    for (int r = j + n2; r < j + n; ++r)
+      for (int c = j; c < j + n2; ++c) TT(r, c) = 0.0;
+  __syncthreads();
+  if (n2 == 2) standardize2(S, m, j, lane);
+  if (n1 == 2) standardize2(S, m, j + n2, lane);
+}
+
+// Sum over the CTA; every thread gets the result.
+__device__ double block_sum(double v, double* red, int lane) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((lane & 31) == 0) red[lane >> 5] = v;
+  __syncthreads();
+  double s = (red[0] + red[1]) + (red[2] + red[3]);
+  __syncthreads();
+  return s;
+}
+
+__device__ double frob(Smem& S, int m, int lane) {
+  double s = 0.0;
+  for (int i = lane; i < m * m; i += NT) s += S.T[i] * S.T[i];
+  return sqrt(block_sum(s, S.red, lane));
+}
+
+// Real Schur form of the Hessenberg T by Francis double-shift steps.
+__device__ bool francis(Smem& S, int m, int lane, int& sweeps) {
+  double tn = frob(S, m, lane);
+  if (tn == 0.0) tn = 1.0;
+  int hi = m - 1, its = 0, total = 0;
+  double v[3];
+  while (hi >= 0) {
+    int l = hi;
+    while (l > 0) {
+      double sc = fabs(TT(l - 1, l - 1)) + fabs(TT(l, l));
+      if (sc == 0.0) sc = tn;
+      if (fabs(TT(l, l - 1)) <= kEps * sc) break;
+      --l;
+    }
+    __syncthreads();
+    if (l > 0 && lane == 0) TT(l, l - 1) = 0.0;
+    __syncthreads();
+    if (l == hi) { --hi; its = 0; continue; }
+    if (l == hi - 1) {
+      standardize2(S, m, hi - 1, lane);
+      hi -= 2;
+      its = 0;
+      continue;
+    }
+    if (++total > 40 * m) { sweeps = total; return false; }
+    ++its;
+    double sh, th;
+    if (its % 11 == 10) {
+      double w = fabs(TT(hi, hi - 1)) + fabs(TT(hi - 1, hi - 2));
+      double z0 = TT(hi, hi) + 0.75 * w;
+      sh = 2.0 * z0;
+      th = z0 * z0 + 0.4375 * w * w;
+    } else {
+      sh = TT(hi - 1, hi - 1) + TT(hi, hi);
+      th = TT(hi - 1, hi - 1) * TT(hi, hi) - TT(hi - 1, hi) * TT(hi, hi - 1);
+    }
+    double x = TT(l, l) * TT(l, l) + TT(l, l + 1) * TT(l + 1, l) - sh * TT(l, l) + th;
+    double y = TT(l + 1, l) * (TT(l, l) + TT(l + 1, l + 1) - sh);
+    double z = TT(l + 1, l) * TT(l + 2, l + 1);
+    for (int kq = l; kq <= hi - 2; ++kq) {
+      double xv[3] = {x, y, z}, tau, beta;
+      house(xv, 3, v, tau, beta);
+      int c0 = kq > l ? kq - 1 : l;
+      __syncthreads();
+      apply_left(S.T, m, v, tau, 3, kq, c0, m, lane);
+      __syncthreads();
+      if (kq > l && lane == 0) {
+        TT(kq + 1, kq - 1) = 0.0;
+        TT(kq + 2, kq - 1) = 0.0;
+      }
+      apply_right(S.T, m, v, tau, 3, kq, 0, min(kq + 4, hi + 1), lane);
+      apply_right(S.Z, m, v, tau, 3, kq, 0, m, lane);
+      __syncthreads();
+      x = TT(kq + 1, kq);
+      y = TT(kq + 2, kq);
+      if (kq < hi - 2) z = TT(kq + 3, kq);
+    }
+    {
+      double xv[2] = {x, y}, tau, beta;
+      house(xv, 2, v, tau, beta);
+      int kq = hi - 1;
+      __syncthreads();
+      apply_left(S.T, m, v, tau, 2, kq, kq - 1, m, lane);
+      __syncthreads();
+      if (lane == 0) TT(kq + 1, kq - 1) = 0.0;
+      apply_right(S.T, m, v, tau, 2, kq, 0, hi + 1, lane);
+      apply_right(S.Z, m, v, tau, 2, kq, 0, m, lane);
+      __syncthreads();
+    }
+  }
+  sweeps = total;
+  return true;
+}
+
+__device__ void hessenberg(Smem& S, int m, int lane) {
+  for (int c = 0; c + 2 < m; ++c) {
+    int n = m - c - 1;
+    // Householder vector of T[c+1:m, c]; computed redundantly
+    double alpha = TT(c + 1, c), sg = 0.0;
+    for (int i = 1 + lane; i < n; i += NT) sg += TT(c + 1 + i, c) * TT(c + 1 + i, c);
+    sg = block_sum(sg, S.red, lane);
+    if (sg == 0.0) continue;
+    double nr = sqrt(alpha * alpha + sg);
+    double beta = alpha <= 0.0 ? nr : -nr;
+    double d = alpha - beta;
+    double tau = (beta - alpha) / beta;
+    __syncthreads();
+    for (int i = lane; i < n; i += NT) S.v[i] = i == 0 ? 1.0 : TT(c + 1 + i, c) / d;
+    __syncthreads();
+    apply_left(S.T, m, S.v, tau, n, c + 1, c, m, lane);
+    __syncthreads();
+    apply_right(S.T, m, S.v, tau, n, c + 1, 0, m, lane);
+    apply_right(S.Z, m, S.v, tau, n, c + 1, 0, m, lane);
+    __syncthreads();
+    if (lane == 0)
+      for (int i = 1; i < n; ++i) TT(c + 1 + i, c) = 0.0;
+    __syncthreads();
+  }
+}
+
+__device__ inline void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
+  if (fabs(br) >= fabs(bi)) {
+    double r = bi / br, d = br + bi * r;
+    cr = (ar + ai * r) / d;
+    ci = (ai - ar * r) / d;
+  } else {
+    double r = br / bi, d = bi + br * r;
+    cr = (ar * r + ai) / d;
+    ci = (ai * r - ar) / d;
+  }
+}
+
+// Eigenvector y of quasi-triangular T for the eigenvalue at diagonal
+// position j (wr, wi; wi > 0 means j is the first row of its 2x2 block).
+__device__ void trevc_one(Smem& S, int m, int j, double lr, double li, double smin, int lane) {
+  bool pair = (li != 0.0);
+  int top;
+  for (int i = lane; i < m; i += NT) { S.yr[i] = 0.0; S.yi[i] = 0.0; }
+  __syncthreads();
+  if (!pair) {
+    if (lane == 0) S.yr[j] = 1.0;
+    top = j;
+  } else {
+    // (T_blk - lambda I) [y_j; y_j+1] = 0 with T_blk = [[a, b], [e, a]]
+    if (lane == 0) {
+      S.yr[j] = TT(j, j + 1);
+      S.yi[j] = 0.0;
+      S.yr[j + 1] = lr - TT(j, j);
+      S.yi[j + 1] = li;
+    }
+    top = j + 1;
+  }
+  __syncthreads();
+  for (int r = lane; r < m; r += NT) {
+    double ar = 0.0, ai = 0.0;
+    if (r < j)
+      for (int l = j; l <= top; ++l) { ar -= TT(r, l) * S.yr[l]; ai -= TT(r, l) * S.yi[l]; }
+    S.sr[r] = ar;
+    S.si[r] = ai;
+  }
+  __syncthreads();
+  int i = j - 1;
+  while (i >= 0) {
+    bool blk2 = (i >= 1 && TT(i, i - 1) != 0.0);
+    if (!blk2) {
+      double dr = TT(i, i) - lr, di = -li;
+      if (fabs(dr) + fabs(di) < smin) dr = smin;
+      double yr, yi;
+      cdiv(S.sr[i], S.si[i], dr, di, yr, yi);
+      __syncthreads();
+      if (lane == 0) { S.yr[i] = yr; S.yi[i] = yi; }
+      for (int r = lane; r < i; r += NT) {
+        S.sr[r] -= TT(r, i) * yr;
+        S.si[r] -= TT(r, i) * yi;
+      }
+      __syncthreads();
+      i -= 1;
+    } else {
+      // [[a - l, b], [c, d - l]] [y0; y1] = [s0; s1]  (complex)
+      int i0 = i - 1;
+      double ar = TT(i0, i0) - lr, ai = -li, br = TT(i0, i), cr = TT(i, i0);
+      double dr = TT(i, i) - lr, di = -li;
+      double s0r = S.sr[i0], s0i = S.si[i0], s1r = S.sr[i], s1i = S.si[i];
+      // det = (a-l)(d-l) - b c
+      double detr = ar * dr - ai * di - br * cr, deti = ar * di + ai * dr;
+      if (fabs(detr) + fabs(deti) < smin) detr = smin;
+      // y0 = (s0 (d-l) - b s1) / det ; y1 = ((a-l) s1 - c s0) / det
+      double n0r = s0r * dr - s0i * di - br * s1r, n0i = s0r * di + s0i * dr - br * s1i;
+      double n1r = ar * s1r - ai * s1i - cr * s0r, n1i = ar * s1i + ai * s1r - cr * s0i;
+      double y0r, y0i, y1r, y1i;
+      cdiv(n0r, n0i, detr, deti, y0r, y0i);
+      cdiv(n1r, n1i, detr, deti, y1r, y1i);
+      __syncthreads();
+      if (lane == 0) { S.yr[i0] = y0r; S.yi[i0] = y0i; S.yr[i] = y1r; S.yi[i] = y1i; }
+      for (int r = lane; r < i0; r += NT) {
+        S.sr[r] -= TT(r, i0) * y0r + TT(r, i) * y1r;
+        S.si[r] -= TT(r, i0) * y0i + TT(r, i) * y1i;
+      }
+      __syncthreads();
+      i -= 2;
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_ritz(RitzArgs R) {
+  extern __shared__ double sm[];
+  const int m = R.m;
+  const int lane = threadIdx.x;  // thread index in the CTA
+  Smem S;
+  S.T = sm;
+  S.Z = S.T + m * m;
+  S.v = S.Z + m * m;
+  S.wr = S.v + m;
+  S.wi = S.wr + m;
+  S.yr = S.wi + m;
+  S.yi = S.yr + m;
+  S.sr = S.yi + m;
+  S.si = S.sr + m;
+  S.red = S.si + m;
+  S.rank = (int*)(S.red + 4);
+  S.sel = S.rank + m;
+
+  for (int i = lane; i < m * m; i += NT) {
+    int r = i % m, c = i / m;
+    S.T[i] = R.H[r + (m + 1) * c];
+    S.Z[i] = (r == c) ? 1.0 : 0.0;
+  }
+  const double beta = R.H[m + (m + 1) * (m - 1)];
+  __syncthreads();
+  hessenberg(S, m, lane);
+  int sweeps = 0;
+  bool ok = francis(S, m, lane, sweeps);
+  __syncthreads();
+  // eigenvalues in Schur order
+  if (lane == 0) {
+    int pos = 0;
+    while (pos < m) {
+      if (pos + 1 < m && TT(pos + 1, pos) != 0.0) {
+        double a = TT(pos, pos), im = sqrt(fabs(TT(pos, pos + 1) * TT(pos + 1, pos)));
+        S.wr[pos] = a; S.wi[pos] = im;
+        S.wr[pos + 1] = a; S.wi[pos + 1] = -im;
+        pos += 2;
+      } else {
+        S.wr[pos] = TT(pos, pos);
+        S.wi[pos] = 0.0;
+        pos += 1;
+      }
+    }
+  }
+  __syncthreads();
+  // ranks by |lambda - s| = 1/|theta|, Im lambda > 0 first on ties
+  // (lambda - s = 1/theta, so Im lambda has the sign of -Im theta)
+  for (int i = lane; i < m; i += NT) {
+    double ti = 1.0 / hypot(S.wr[i], S.wi[i]);
+    int ci = S.wi[i] < 0.0 ? 0 : (S.wi[i] == 0.0 ? 1 : 2);
+    int rk = 0;
+    for (int q = 0; q < m; ++q) {
+      double tq = 1.0 / hypot(S.wr[q], S.wi[q]);
+      int cq = S.wi[q] < 0.0 ? 0 : (S.wi[q] == 0.0 ? 1 : 2);
+      if (tq < ti || (tq == ti && (cq < ci || (cq == ci && q < i)))) ++rk;
+    }
+    S.rank[i] = rk;
+  }
+  __syncthreads();
+  double tnorm = frob(S, m, lane);
+  double smin = fmax(kEps * tnorm, 1e-300);
+  int nconv = 0;
+  // wanted pairs: eigenvectors, estimates and (final pass) outputs
+  for (int pos = 0; pos < m; ++pos) {
+    int rk = S.rank[pos];
+    if (rk >= R.neig) continue;
+    double lr = S.wr[pos], li = S.wi[pos];
+    int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
+    double lri = lr, lii = fabs(li);
+    trevc_one(S, m, jstart, lri, lii, smin, lane);
+    // y_H = Z y ; estimate uses the last row; norm of y equals norm of Z y
+    double nrm = 0.0;
+    for (int i = lane; i < m; i += NT) nrm += S.yr[i] * S.yr[i] + S.yi[i] * S.yi[i];
+    nrm = sqrt(block_sum(nrm, S.red, lane));
+    double lastr = 0.0, lasti = 0.0;
+    for (int l = lane; l < m; l += NT) {
+      lastr += ZZ(m - 1, l) * S.yr[l];
+      lasti += ZZ(m - 1, l) * S.yi[l];
+    }
+    lastr = block_sum(lastr, S.red, lane);
+    lasti = block_sum(lasti, S.red, lane);
+    double theta = hypot(lr, li);
+    double est = fabs(beta) * hypot(lastr, lasti) / (nrm * theta);
+    if (est <= R.tol) ++nconv;
+    if (lane == 0) {
+      // lambda = s + 1/theta
+      double ir, ii;
+      cdiv(1.0, 0.0, lr, li, ir, ii);
+      R.out->lam[2 * rk] = R.sigma + ir;
+      R.out->lam[2 * rk + 1] = ii;
+      R.out->est[rk] = est;
+    }
+    if (R.final_pass) {
+      double sgn = (li < 0.0) ? -1.0 : 1.0;
+      for (int r = lane; r < m; r += NT) {
+        double ar = 0.0, ai = 0.0;
+        for (int l = 0; l < m; ++l) { ar += ZZ(r, l) * S.yr[l]; ai += ZZ(r, l) * S.yi[l]; }
+        R.Y[2 * (r + m * rk)] = ar / nrm;
+        R.Y[2 * (r + m * rk) + 1] = sgn * ai / nrm;
+      }
+    }
+    __syncthreads();
+  }
+  if (lane == 0) {
+    R.out->n_conv = nconv;
+    R.out->fail = ok ? 0 : 1;
+    R.out->beta = beta;
+    R.out->sweeps = sweeps;
+  }
+  if (R.final_pass) return;
+  // select the kwant nearest, never splitting a conjugate pair
+  for (int i = lane; i < m; i += NT) S.sel[i] = S.rank[i] < R.kwant ? 1 : 0;
+  __syncthreads();
+  if (lane == 0) {
+    int pos = 0;
+    while (pos < m) {
+      if (pos + 1 < m && TT(pos + 1, pos) != 0.0) {
+        int s = S.sel[pos] | S.sel[pos + 1];
+        S.sel[pos] = s;
+        S.sel[pos + 1] = s;
+        pos += 2;
+      } else {
+        pos += 1;
+      }
+    }
+  }
+  __syncthreads();
+  // reorder: move selected blocks to the top
+  int ks = 0, pos = 0;
+  while (pos < m) {
+    int bs = (pos + 1 < m && TT(pos + 1, pos) != 0.0) ? 2 : 1;
+    if (S.sel[pos]) {
+      int here = pos;
+      while (here > ks) {
+        int nbf = (here >= 2 && TT(here - 1, here - 2) != 0.0) ? 2 : 1;
+        int prev = here - nbf;
+        swap_blocks(S, m, prev, nbf, bs, tnorm, lane);
+        // the selected block now starts at prev; keep the flags in step
+        __syncthreads();
+        if (lane == 0) {
+          for (int i = 0; i < bs; ++i) S.sel[prev + i] = 1;
+          for (int i = 0; i < nbf; ++i) S.sel[prev + bs + i] = 0;
+        }
+        __syncthreads();
+        here = prev;
+      }
+      ks += bs;
+    }
+    pos += bs;
+  }
+  __syncthreads();
+  int k = ks;
+  for (int i = lane; i < (m + 1) * m; i += NT) {
+    int r = i % (m + 1), c = i / (m + 1);
+    double v = 0.0;
+    if (c < k) {
+      if (r < k) v = TT(r, c);
+      else if (r == k) v = beta * ZZ(m - 1, c);
+    }
+    R.Hnew[i] = v;
+  }
+  for (int i = lane; i < m * k; i += NT) R.Q[i] = S.Z[i];
+  if (lane == 0) R.out->k = k;
+}
+
+}  // namespace
+
+size_t ritz_smem(int m) {
+  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 2 * sizeof(int) * m;
+}
+
+void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
+                 int kwant, int final_pass, double sigma, double tol, cudaStream_t s) {
+  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, sigma, tol};
+  size_t smem = ritz_smem(m);
+  RQ_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_ritz<<<1, NT, smem, s>>>(R);
+  RQ_CUDA(cudaGetLastError());
+}
+
+}  // namespace rq

@@ -1,0 +1,264 @@
+"""Python binding of the rigaqep C-ABI (argument marshalling only).
+
+Every computation runs in ``_lib/librigaqep.so`` (CUDA, sm_103a); this module
+only converts arguments, holds the handle and maps status codes to
+exceptions.  PyTorch provides device buffers and the current stream.  There
+is no fallback: if the library is missing or a call fails, an exception is
+raised.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librigaqep.so")
+
+STATUS = {
+    0: "OK", 1: "ERR_ARG", 2: "ERR_STATE", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_PIVOT",
+    6: "ERR_REFINEMENT", 7: "ERR_NO_CONVERGENCE", 8: "ERR_TIMEOUT", 9: "ERR_INTERNAL",
+}
+
+# every symbol declared in include/rigaqep.h
+EXPORTS = [
+    "rigaqep_assemble", "rigaqep_analyze", "rigaqep_factor", "rigaqep_solve", "rigaqep_eigs",
+    "rigaqep_grad_damping", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
+    "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
+    "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy",
+]
+
+
+class RigaqepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("ne_x", "ne_y", "p", "block_x", "block_y", "n_quad", "leaf_min")]
+
+
+class EigsOpts(ctypes.Structure):
+    _fields_ = [("krylov_dim", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("shift_mode", ctypes.c_int32),
+                ("shift", ctypes.c_double), ("ncand", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_int64) for n in
+                 ("n1", "N", "nnz", "nsuper", "nlevels", "nnz_L", "factor_flops", "max_front",
+                  "n_apply", "n_restarts", "n_spmv", "n_vv", "n_qr_sweeps")]
+                + [(n, ctypes.c_double) for n in
+                   ("norm_K", "norm_M", "norm_C", "factor_ms", "eigs_ms", "fb_ms")]
+                + [("certified", ctypes.c_int64), ("cert_margin", ctypes.c_double),
+                   ("n_launches", ctypes.c_int64)])
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, V = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                         ctypes.c_void_p)
+    sig = {
+        "rigaqep_assemble": [ctypes.POINTER(MeshDesc), P, I32, V, ctypes.POINTER(P)],
+        "rigaqep_analyze": [P],
+        "rigaqep_factor": [P, D, I32],
+        "rigaqep_solve": [P, P, P, I32, I32],
+        "rigaqep_eigs": [P, I32, D, ctypes.POINTER(EigsOpts), P, P, P, P, ctypes.POINTER(I32)],
+        "rigaqep_grad_damping": [P, I32, P, P, P],
+        "rigaqep_export_csr": [P, P, P, P, P, P],
+        "rigaqep_export_symbolic": [P, P, P, P, P, P, P],
+        "rigaqep_get_info": [P, ctypes.POINTER(Info)],
+        "rigaqep_symbolic_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)],
+        "rigaqep_symbolic_sizes": [P, ctypes.POINTER(I64)],
+        "rigaqep_symbolic_export": [P, P, P, P, P, P, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.rigaqep_symbolic_destroy.argtypes = [P]
+    lib.rigaqep_symbolic_destroy.restype = None
+    lib.rigaqep_destroy.argtypes = [P]
+    lib.rigaqep_destroy.restype = None
+    lib.rigaqep_last_error.argtypes = []
+    lib.rigaqep_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        raise RigaqepError(code, load().rigaqep_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def mesh_desc(ne, p, block, n_quad=0, leaf_min=0):
+    return MeshDesc(ne, ne, p, block, block, n_quad, leaf_min)
+
+
+def symbolic_host(ne, p, block, n_quad=0, leaf_min=0):
+    """Pattern + symbolic phase on the host only (no CUDA call)."""
+    lib = load()
+    h = ctypes.c_void_p()
+    md = mesh_desc(ne, p, block, n_quad, leaf_min)
+    _check(lib.rigaqep_symbolic_create(ctypes.byref(md), ctypes.byref(h)))
+    try:
+        sz = (ctypes.c_int64 * 6)()
+        _check(lib.rigaqep_symbolic_sizes(h, sz))
+        N, nnz, ns, nu, nl, n1 = list(sz)
+        out = dict(perm=np.empty(N, np.int32), sptr=np.empty(ns + 1, np.int32),
+                   parent=np.empty(ns, np.int32), upd_ptr=np.empty(ns + 1, np.int32),
+                   upd_idx=np.empty(nu, np.int32), level=np.empty(ns, np.int32),
+                   rowptr=np.empty(N + 1, np.int32), col=np.empty(nnz, np.int32))
+        _check(lib.rigaqep_symbolic_export(h, *[_ptr(out[k]) for k in
+                                                ("perm", "sptr", "parent", "upd_ptr", "upd_idx",
+                                                 "level", "rowptr", "col")]))
+        out["nlevels"] = nl
+        out["n1"] = n1
+        return out
+    finally:
+        lib.rigaqep_symbolic_destroy(h)
+
+
+class Problem:
+    """One rIGA QEP on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, ne, p, block, sigma_e, n_quad=0, leaf_min=0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.ne, self.p, self.block = ne, p, block
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        if isinstance(sigma_e, np.ndarray):
+            sig = np.ascontiguousarray(sigma_e, dtype=np.float64)
+            on_dev = 0
+        else:
+            sig = sigma_e.contiguous().to(torch.float64)
+            on_dev = 1 if sig.is_cuda else 0
+        count = sig.size if isinstance(sig, np.ndarray) else sig.numel()
+        if count != ne * ne:
+            raise ValueError("sigma_e must have ne*ne entries")
+        self._h = ctypes.c_void_p()
+        md = mesh_desc(ne, p, block, n_quad, leaf_min)
+        _check(self.lib.rigaqep_assemble(ctypes.byref(md), _ptr(sig), on_dev,
+                                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(self._h)))
+        inf = self.info()
+        self.N, self.nnz, self.n1 = inf["N"], inf["nnz"], inf["n1"]
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.rigaqep_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- pipeline
+    def analyze(self):
+        _check(self.lib.rigaqep_analyze(self._h))
+        return self
+
+    def factor(self, sigma, precision=0):
+        _check(self.lib.rigaqep_factor(self._h, float(sigma), precision))
+        return self
+
+    def solve(self, b, out=None, transpose=0):
+        """x = Q(sigma)^{-1} b for a float64 CUDA tensor b of shape (N,) or (nrhs, N)."""
+        torch = self._torch
+        b = b.contiguous()
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        x = torch.empty_like(b) if out is None else out
+        _check(self.lib.rigaqep_solve(self._h, _ptr(b), _ptr(x), nrhs, transpose))
+        return x
+
+    def eigs(self, neig, sigma, m=None, tol=1e-10, max_restarts=1000, seed=1, v1=None,
+             raise_on_noconv=True, shift=None, ncand=None):
+        """Eigenpairs nearest the target sigma: (lambda (neig,) complex,
+        X (neig, N) complex, eta (neig,), n_converged, status).
+
+        shift=None places the spectral shift at sigma; a real shift selects
+        the in-region mode (ncand pairs converged around the shift, the neig
+        nearest sigma returned; see info()["certified"])."""
+        torch = self._torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nc = neig if ncand is None else ncand
+        m = m or min(96, 2 * nc + 20)
+        lam = torch.empty((neig, 2), dtype=torch.float64, device=dev)
+        X = torch.empty((neig, self.N, 2), dtype=torch.float64, device=dev)
+        eta = torch.empty(neig, dtype=torch.float64, device=dev)
+        nconv = ctypes.c_int32(0)
+        opts = EigsOpts(m, max_restarts, tol, seed, 0, 0 if shift is None else 1,
+                        0.0 if shift is None else float(shift), nc)
+        if v1 is not None:
+            v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
+        st = self.lib.rigaqep_eigs(self._h, neig, float(sigma), ctypes.byref(opts), _ptr(v1),
+                                   _ptr(lam), _ptr(X), _ptr(eta), ctypes.byref(nconv))
+        if st != 0 and not (st == 7 and not raise_on_noconv):
+            _check(st)
+        return (torch.view_as_complex(lam), torch.view_as_complex(X), eta, nconv.value, st)
+
+    def grad_damping(self, lam, X):
+        """d lambda_k / d sigma_e, complex tensor of shape (neig, ne*ne)."""
+        torch = self._torch
+        neig = lam.shape[0]
+        lam_r = torch.view_as_real(lam.contiguous()).contiguous()
+        X_r = torch.view_as_real(X.contiguous()).contiguous()
+        G = torch.empty((neig, self.ne * self.ne, 2), dtype=torch.float64, device=lam.device)
+        _check(self.lib.rigaqep_grad_damping(self._h, neig, _ptr(lam_r), _ptr(X_r), _ptr(G)))
+        return torch.view_as_complex(G)
+
+    # -- introspection
+    def info(self):
+        inf = Info()
+        _check(self.lib.rigaqep_get_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def export_csr(self):
+        N, nnz = self.N, self.nnz
+        out = dict(rowptr=np.empty(N + 1, np.int32), col=np.empty(nnz, np.int32),
+                   K=np.empty(nnz), M=np.empty(nnz), C=np.empty(nnz))
+        _check(self.lib.rigaqep_export_csr(self._h, *[_ptr(out[k]) for k in
+                                                      ("rowptr", "col", "K", "M", "C")]))
+        return out
+
+    def export_symbolic(self):
+        inf = self.info()
+        ns = inf["nsuper"]
+        out = dict(perm=np.empty(self.N, np.int32), sptr=np.empty(ns + 1, np.int32),
+                   parent=np.empty(ns, np.int32), upd_ptr=np.empty(ns + 1, np.int32),
+                   level=np.empty(ns, np.int32))
+        _check(self.lib.rigaqep_export_symbolic(self._h, _ptr(out["perm"]), _ptr(out["sptr"]),
+                                                _ptr(out["parent"]), _ptr(out["upd_ptr"]), None,
+                                                _ptr(out["level"])))
+        out["upd_idx"] = np.empty(int(out["upd_ptr"][-1]), np.int32)
+        _check(self.lib.rigaqep_export_symbolic(self._h, None, None, None, None,
+                                                _ptr(out["upd_idx"]), None))
+        return out
