@@ -185,6 +185,23 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
 rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig,
                                     const double* lambda, const double* X, double* G);
 
+/* The same d lambda / d sigma_e as rigaqep_grad_damping (same arguments and
+ * layout), for callers that must not allocate device memory during the call:
+ * code that runs on a latency-critical path where the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree would stall other streams, or code
+ * inside a framework whose memory manager owns all device memory.  The
+ * paper has no counterpart; this is a service of the library.
+ * Its reduction scratch is a fixed array in device global memory (305 KiB,
+ * held by every GPU that loads the library until the process exits), so
+ * neig must be <= 64; larger neig returns RIGAQEP_ERR_ARG before any GPU
+ * work.  The first call on each device looks up that array's device address
+ * with the device current; make that first call before any stream capture.
+ * All calls share the one array (each call writes every entry it reads), so
+ * calls that overlap on the GPU, from any stream or thread, race: serialise
+ * them.  Synchronises the handle's stream before returning. */
+rigaqep_status rigaqep_grad_damping_noalloc(rigaqep_problem* prob, int32_t neig,
+                                            const double* lambda, const double* X, double* G);
+
 /* Copy the original-order CSR (rowptr N+1, col nnz int32; K, M, C nnz
  * doubles) to host buffers; any pointer may be NULL to skip it. */
 rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, int32_t* col,

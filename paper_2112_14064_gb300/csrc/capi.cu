@@ -268,6 +268,15 @@ rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig, const d
   });
 }
 
+rigaqep_status rigaqep_grad_damping_noalloc(rigaqep_problem* prob, int32_t neig,
+                                            const double* lambda, const double* X, double* G) {
+  return guard([&] {
+    need(prob != nullptr && lambda != nullptr && X != nullptr && G != nullptr, RIGAQEP_ERR_ARG,
+         "NULL argument");
+    rq::grad_run_noalloc(prob->impl, neig, lambda, X, G);
+  });
+}
+
 rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, int32_t* col,
                                   double* K, double* M, double* C) {
   return guard([&] {

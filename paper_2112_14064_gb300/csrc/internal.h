@@ -145,6 +145,7 @@ struct EigsParams {
 void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
               double* eta, int* n_conv);
 void grad_run(Problem& P, int neig, const double* lambda, const double* X, double* G);
+void grad_run_noalloc(Problem& P, int neig, const double* lambda, const double* X, double* G);
 
 }  // namespace rq
 

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -750,6 +751,60 @@ void grad_run(Problem& P, int neig, const double* lambda, const double* X, doubl
   RQ_CUDA(cudaGetLastError());
   int64_t tot = (int64_t)L.ne * L.ne * neig;
   k_grad<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(X, lambda, den.p, P.m1.p, P.first_fn.p, L.ne,
+                                                       L.p, L.n1, N, neig, G);
+  RQ_CUDA(cudaGetLastError());
+  RQ_CUDA(cudaStreamSynchronize(s));
+}
+
+
+// ---- allocation-free variant of the damping sensitivity ----
+//
+// Scratch for the reduction of x^T (2 lambda M + C) x: per-block partial sums
+// (re, im) of up to kNoAllocMaxEig eigenpairs, then the denominators.  It
+// lives in this file-scope device array, so the call needs no cudaMalloc;
+// every GPU that loads the library keeps these 305 KiB until the process
+// exits.  Every entry the kernels read is written earlier in the same call.
+constexpr int kNoAllocBlocks = 2 * 152;
+constexpr int kNoAllocMaxEig = 64;
+constexpr size_t kNoAllocScratch = 2 * (size_t)kNoAllocBlocks * kNoAllocMaxEig + 2 * kNoAllocMaxEig;
+static __device__ __align__(256) double g_grad_scratch[kNoAllocScratch];
+
+namespace {
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[256] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is queried
+// once per device (with that device current) and cached.
+double* noalloc_scratch() {
+  int dev = 0;
+  RQ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) throw Error(RIGAQEP_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    RQ_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  return g_scratch_ptr[dev];
+}
+}  // namespace
+
+void grad_run_noalloc(Problem& P, int neig, const double* lambda, const double* X, double* G) {
+  if (neig < 1 || neig > kNoAllocMaxEig)
+    throw Error(RIGAQEP_ERR_ARG, "neig must be in [1, 64] for the allocation-free gradient");
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  int64_t N = L.N;
+  double* part = noalloc_scratch();
+  double* den = part + 2 * (size_t)kNoAllocBlocks * kNoAllocMaxEig;
+  dim3 g(kNoAllocBlocks, neig);
+  k_gden<<<g, 256, 0, s>>>(P.rowptr.p, P.col.p, P.M.p, P.C.p, X, lambda, N, part);
+  RQ_CUDA(cudaGetLastError());
+  k_gden_final<<<1, 64, 0, s>>>(part, kNoAllocBlocks, neig, den);
+  RQ_CUDA(cudaGetLastError());
+  int64_t tot = (int64_t)L.ne * L.ne * neig;
+  k_grad<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne,
                                                        L.p, L.n1, N, neig, G);
   RQ_CUDA(cudaGetLastError());
   RQ_CUDA(cudaStreamSynchronize(s));

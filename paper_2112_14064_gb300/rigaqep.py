@@ -22,7 +22,7 @@ STATUS = {
 # every symbol declared in include/rigaqep.h
 EXPORTS = [
     "rigaqep_assemble", "rigaqep_analyze", "rigaqep_factor", "rigaqep_solve", "rigaqep_eigs",
-    "rigaqep_grad_damping", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
+    "rigaqep_grad_damping", "rigaqep_grad_damping_noalloc", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy",
 ]
@@ -80,6 +80,7 @@ def load():
         "rigaqep_solve": [P, P, P, I32, I32],
         "rigaqep_eigs": [P, I32, D, ctypes.POINTER(EigsOpts), P, P, P, P, ctypes.POINTER(I32)],
         "rigaqep_grad_damping": [P, I32, P, P, P],
+        "rigaqep_grad_damping_noalloc": [P, I32, P, P, P],
         "rigaqep_export_csr": [P, P, P, P, P, P],
         "rigaqep_export_symbolic": [P, P, P, P, P, P, P],
         "rigaqep_get_info": [P, ctypes.POINTER(Info)],
@@ -234,6 +235,19 @@ class Problem:
         G = torch.empty((neig, self.ne * self.ne, 2), dtype=torch.float64, device=lam.device)
         _check(self.lib.rigaqep_grad_damping(self._h, neig, _ptr(lam_r), _ptr(X_r), _ptr(G)))
         return torch.view_as_complex(G)
+
+    def grad_damping_noalloc(self, lam, X, out=None):
+        """Same as grad_damping, writing into the caller's buffer out (neig,
+        ne*ne, 2 float64) with no device allocation inside the library call."""
+        torch = self._torch
+        neig = lam.shape[0]
+        lam_r = torch.view_as_real(lam.contiguous()).contiguous()
+        X_r = torch.view_as_real(X.contiguous()).contiguous()
+        if out is None:
+            out = torch.empty((neig, self.ne * self.ne, 2), dtype=torch.float64, device=lam.device)
+        _check(self.lib.rigaqep_grad_damping_noalloc(self._h, neig, _ptr(lam_r), _ptr(X_r),
+                                                     _ptr(out)))
+        return torch.view_as_complex(out)
 
     # -- introspection
     def info(self):
