@@ -17,18 +17,17 @@
 // looking LDL^T of the k pivot columns with the rank-1 updates applied to the
 // pivot block, to L21 and to the U block.
 //
-// The 32 x 32 diagonal blocks of each unit-lower pivot block are replaced by
-// their inverses at the end of the factorisation, so the FB solves apply them
-// as small matrix-vector products instead of 32-step substitutions.
+// Partitioned inverse: at the end of each front's factorisation the unit-lower
+// pivot block L11 is replaced by inv(L11) and L21 by W = L21 inv(L11), so a
+// front's forward elimination is one matrix-vector product with the panel
+// [inv(L11); W] and its backward elimination one transposed product with the
+// same panel; no front has a sequential substitution chain.
 //
-// FB, two launches per level and sweep.  Forward (leaves first): one CTA per
-// front gathers the right-hand side of its pivots and its children's update
-// vectors and solves the pivot block (z = L11^{-1} x_s, x_s <- D^{-1} z);
-// then the update vectors y_s -= L21 z are formed by CTAs that each own 64
-// rows of L21, so large fronts spread over many SMs.  Backward (root first):
-// CTAs that each own 32 pivot columns form w = L21^T x_struct (warps split
-// the rows, a butterfly reduction gives one column per lane), then one CTA
-// per front solves x_s <- L11^{-T} (x_s - w).
+// FB, one launch per level and sweep.  Forward (leaves first): work items of
+// 32 panel rows; each gathers its front's right-hand side and children's
+// update vectors, then forms D^{-1} inv(L11) x_s (pivot rows) or the update
+// vector y_s = children - W x_s (update rows).  Backward (root first): work
+// items of 32 pivot columns form x_s = inv(L11)^T D^{-1}z - W^T x_struct.
 #include "internal.h"
 
 namespace rq {
@@ -136,26 +135,40 @@ __global__ void k_front_factor(FrontArgs A, int lvl_begin) {
     }
     __syncthreads();
   }
-  // Replace each 32 x 32 unit-lower diagonal block of L11 by its inverse
-  // (lane j: column j by forward substitution), used by the FB solves.
-  for (int b0 = warp * 32; b0 < k; b0 += nw * 32) {
-    int nb = min(32, k - b0);
-    double col[32];
-    if (lane < nb) {
-      for (int i = 0; i < 32; ++i) col[i] = 0.0;
-      col[lane] = 1.0;
-      for (int i = lane + 1; i < nb; ++i) {
-        double acc = 0.0;
-        for (int l = lane; l < i; ++l) acc += L[(b0 + i) + F * (b0 + l)] * col[l];
-        col[i] = -acc;
+  // Partitioned inverse for the FB solves: L11 <- inv(L11) (unit lower,
+  // column j from the already inverted trailing block, last column first),
+  // then L21 <- W = L21 inv(L11) (each thread one row, columns left to right;
+  // column j only needs original columns >= j).
+  for (int j = k - 2; j >= 0; --j) {
+    // new column j (rows j+1..k-1) into shared memory, then written back
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
+      double v0 = 0.0, v1 = 0.0;
+      int c = j + 1;
+      for (; c + 1 < i; c += 2) {
+        v0 -= L[i + F * c] * L[c + F * j];
+        v1 -= L[i + F * (c + 1)] * L[(c + 1) + F * j];
       }
+      for (; c < i; ++c) v0 -= L[i + F * c] * L[c + F * j];
+      lb[i] = (v0 + v1) - L[i + F * j];      // the c = i term, inv(L11)[i, i] = 1
     }
-    __syncwarp();
-    if (lane < nb)
-      for (int i = lane + 1; i < nb; ++i) L[(b0 + i) + F * (b0 + lane)] = col[i];
-    __syncwarp();
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) L[i + F * j] = lb[i];
+    __syncthreads();
+  }
+  for (int64_t i = k + threadIdx.x; i < F; i += blockDim.x) {
+    for (int j = 0; j < k; ++j) {
+      double w0 = L[i + F * j], w1 = 0.0;   // L21[i, j] times inv(L11)[j, j] = 1
+      int c = j + 1;
+      for (; c + 1 < k; c += 2) {
+        w0 += L[i + F * c] * L[c + F * j];
+        w1 += L[i + F * (c + 1)] * L[(c + 1) + F * j];
+      }
+      for (; c < k; ++c) w0 += L[i + F * c] * L[c + F * j];
+      L[i + F * j] = w0 + w1;
+    }
   }
 }
+
 
 struct FBArgs {
   const int32_t* sptr;
@@ -164,22 +177,19 @@ struct FBArgs {
   const int32_t* relmap;
   const int32_t* child_ptr;
   const int32_t* child_idx;
-  const int32_t* lvl_nodes;
   const int64_t* loff;
   const double* Lval;
   const double* Dinv;
-  double* yvec;
-  double* zbuf;    // unscaled forward solution of the pivot rows
-  double* wbuf;    // L21^T x_struct of the pivot rows (backward)
-  const int4* fwd_items;  // (front, first row of L21, rows)
-  const int4* bwd_items;  // (front, first pivot column, columns)
+  double* yvec;    // update vectors of the forward sweep (one per supernode)
+  double* zbuf;    // forward result D^{-1} inv(L11) x of the pivot rows
+  const int4* fwd_items;  // (front, first panel row, rows <= 32, 0)
+  const int4* bwd_items;  // (front, first pivot column, columns <= 32, 0)
 };
 
 FBArgs fb_args(Problem& P) {
-  return FBArgs{P.sptr.p,  P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
-                P.child_idx.p, P.lvl_nodes.p, P.loff.p, P.Lval.p, P.Dinv.p,
-                P.yvec.p, P.zbuf.p, P.wbuf.p, (const int4*)P.fwd_items.p,
-                (const int4*)P.bwd_items.p};
+  return FBArgs{P.sptr.p, P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p, P.child_idx.p,
+                P.loff.p, P.Lval.p, P.Dinv.p, P.yvec.p, P.zbuf.p,
+                (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
 // Butterfly transpose-reduction of 32 per-lane accumulators: afterwards lane
@@ -198,20 +208,26 @@ __device__ __forceinline__ double warp_transpose_reduce(double (&acc)[32], int l
   return acc[0];
 }
 
-// Forward, pivot rows of one front per CTA: gather the right-hand side and the
-// children's update vectors, then z = L11^{-1} x_s in 32-row blocks (the
-// diagonal blocks hold their inverses), x_s <- D^{-1} z.
-__global__ void k_fb_fwd_tri(FBArgs A, int lvl_begin, double* x) {
-  extern __shared__ double xs[];
-  int s = A.lvl_nodes[lvl_begin + blockIdx.x];
+// Forward sweep, one work item = up to 32 consecutive rows of one front's
+// panel P = [inv(L11); W], W = L21 inv(L11):
+//   xg  = x_s + (children's update vectors at the pivot rows)
+//   z   = inv(L11) xg           -> zbuf = D^{-1} z   (pivot rows)
+//   y_s = (children at the update rows) - W xg      (update rows)
+// Lanes run down the rows (coalesced columns), the four warps split the
+// columns; pivot rows only use the columns up to the chunk's last row.
+__global__ void __launch_bounds__(128) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
+  extern __shared__ double xg[];
+  __shared__ double part[4][32];
+  __shared__ double yadd[32];
+  int4 it = A.fwd_items[item_begin + blockIdx.x];
+  int s = it.x, r0 = it.y, nr = it.z;
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  const double* L = A.Lval + A.loff[s];
-  double* ys = A.yvec + A.upd_ptr[s];
+  const double* P = A.Lval + A.loff[s];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < k; t += blockDim.x) xs[t] = x[a + t];
-  for (int i = threadIdx.x; i < u; i += blockDim.x) ys[i] = 0.0;
+  for (int t = threadIdx.x; t < k; t += blockDim.x) xg[t] = xin[a + t];
+  if (threadIdx.x < 32) yadd[threadIdx.x] = 0.0;
   __syncthreads();
   for (int ci = A.child_ptr[s]; ci < A.child_ptr[s + 1]; ++ci) {
     int c = A.child_idx[ci];
@@ -220,187 +236,75 @@ __global__ void k_fb_fwd_tri(FBArgs A, int lvl_begin, double* x) {
     const double* yc = A.yvec + A.upd_ptr[c];
     for (int r = threadIdx.x; r < uc; r += blockDim.x) {
       int pos = rm[r];
-      double v = yc[r];
-      if (pos < k) xs[pos] += v;
-      else ys[pos - k] += v;
+      if (pos < k) xg[pos] += yc[r];
+      else if (pos >= r0 && pos < r0 + nr) yadd[pos - r0] += yc[r];
     }
     __syncthreads();
   }
-  for (int b0 = 0; b0 < k; b0 += 32) {
-    int nb = min(32, k - b0);
-    if (warp == 0) {
-      // z_b = inv(L_bb) x_b, lane = row.  Loads are unconditional (clamped
-      // to the block) so they issue together; out-of-range terms are zeroed.
-      int rr = min(lane, nb - 1);
-      const double* row = L + (b0 + rr) + F * b0;
-      double v[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) v[c] = row[F * min(c, nb - 1)];
-      double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        a0 += (c <= lane ? v[c] : 0.0) * xs[b0 + min(c, nb - 1)];
-        a1 += (c + 1 <= lane ? v[c + 1] : 0.0) * xs[b0 + min(c + 1, nb - 1)];
-      }
-      __syncwarp();
-      if (lane < nb) xs[b0 + lane] = a0 + a1;
-    }
-    __syncthreads();
-    for (int i = b0 + nb + threadIdx.x; i < k; i += blockDim.x) {
-      const double* row = L + i + F * b0;
-      double acc = 0.0;
-      if (nb == 32) {
-        double v[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = row[F * c];
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll
-        for (int c = 0; c < 32; c += 4) {
-          a0 += v[c] * xs[b0 + c];
-          a1 += v[c + 1] * xs[b0 + c + 1];
-          a2 += v[c + 2] * xs[b0 + c + 2];
-          a3 += v[c + 3] * xs[b0 + c + 3];
-        }
-        acc = (a0 + a1) + (a2 + a3);
-      } else {
-        for (int c = 0; c < nb; ++c) acc += row[F * c] * xs[b0 + c];
-      }
-      xs[i] -= acc;
-    }
-    __syncthreads();
+  int row = r0 + min(lane, nr - 1);
+  int cend = r0 + nr <= k ? r0 + nr : k;     // triangle: columns <= last pivot row
+  int q = (cend + 3) / 4;
+  int cb = warp * q, ce = min(cend, cb + q);
+  const double* pr = P + row;
+  double s0 = 0.0, s1 = 0.0;
+  int c = cb;
+  for (; c + 1 < ce; c += 2) {
+    s0 += pr[F * c] * xg[c];
+    s1 += pr[F * (c + 1)] * xg[c + 1];
   }
-  for (int t = threadIdx.x; t < k; t += blockDim.x) {
-    A.zbuf[a + t] = xs[t];
-    x[a + t] = xs[t] * A.Dinv[a + t];
-  }
-}
-
-// Forward, update rows: y_s[r] -= L21[r, :] z_s for one block of rows.
-__global__ void k_fb_fwd_gemv(FBArgs A, int item_begin) {
-  int4 it = A.fwd_items[item_begin + blockIdx.x];
-  int s = it.x;
-  int a = A.sptr[s], k = A.sptr[s + 1] - a;
-  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
-  int64_t F = k + u;
-  const double* L = A.Lval + A.loff[s];
-  double* ys = A.yvec + A.upd_ptr[s];
-  extern __shared__ double zs[];
-  for (int t = threadIdx.x; t < k; t += blockDim.x) zs[t] = A.zbuf[a + t];
+  if (c < ce) s0 += pr[F * c] * xg[c];
+  part[warp][lane] = s0 + s1;
   __syncthreads();
-  int r = it.y + threadIdx.x;
-  if (threadIdx.x >= it.z) return;
-  const double* row = L + k + r;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  int t = 0;
-  for (; t + 8 <= k; t += 8) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q & 3] += row[F * (t + q)] * zs[t + q];
+  if (threadIdx.x < nr) {
+    int i = r0 + threadIdx.x;
+    double dot = (part[0][threadIdx.x] + part[1][threadIdx.x]) +
+                 (part[2][threadIdx.x] + part[3][threadIdx.x]);
+    if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
+    else A.yvec[A.upd_ptr[s] + (i - k)] = yadd[threadIdx.x] - dot;
   }
-  for (; t < k; ++t) acc[0] += row[F * t] * zs[t];
-  ys[r] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
-// Backward, w = L21^T x_struct for a block of <= 32 pivot columns: warps split
-// the update rows, lanes run along a column, butterfly to one column per lane.
-__global__ void k_fb_bwd_gemv(FBArgs A, int item_begin, const double* x) {
+// Backward sweep, one work item = up to 32 pivot columns c of one front:
+//   x_c = sum_{i >= c, i < k} inv(L11)[i, c] zbuf_i - sum_i W[i, c] x_struct(i)
+// i.e. x_s = inv(L11)^T (D^{-1} z - L21^T x_struct) with W = L21 inv(L11).
+// Warps split the rows, lanes run down them (coalesced), butterfly to one
+// column per lane.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
+__global__ void __launch_bounds__(256) k_fb_bwd(FBArgs A, int item_begin, double* x,
+                                                double sigma, const double* vu, double* ru,
+                                                double* rl) {
+  __shared__ double red[8][32];
   int4 it = A.bwd_items[item_begin + blockIdx.x];
   int s = it.x, c0 = it.y, nc = it.z;
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  const double* L = A.Lval + A.loff[s];
+  const double* P = A.Lval + A.loff[s] + F * c0;
   const int32_t* st = A.upd_idx + A.upd_ptr[s];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double acc[32];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-  for (int i = warp * 32 + lane; i < u; i += nw * 32) {
-    double xv = x[st[i]];
-    const double* row = L + k + i + F * c0;
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  for (int64_t i = c0 + threadIdx.x; i < F; i += blockDim.x) {
+    double g = i < k ? A.zbuf[a + i] : -x[st[i - k]];
+    const double* pr = P + i;
     double v[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) v[c] = row[F * min(c, nc - 1)];
+    for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] += v[c] * xv;
+    for (int q = 0; q < 32; ++q) acc[q] += v[q] * g;
   }
   double v = warp_transpose_reduce(acc, lane);
-  __shared__ double red[8][32];
   red[warp][lane] = v;
   __syncthreads();
   if (threadIdx.x < nc) {
     double sum = 0.0;
-    for (int w = 0; w < nw; ++w) sum += red[w][threadIdx.x];
-    A.wbuf[a + c0 + threadIdx.x] = sum;
-  }
-}
-
-// Backward, pivot rows of one front per CTA: x_s <- L11^{-T} (x_s - w), last
-// 32-block first; each block subtracts the already solved rows below it
-// (butterfly column dots) and applies the transposed inverse diagonal block.
-__global__ void k_fb_bwd_tri(FBArgs A, int lvl_begin, double* x, double sigma, const double* vu,
-                             double* ru, double* rl) {
-  extern __shared__ double xs[];
-  __shared__ double red[8][32];
-  int s = A.lvl_nodes[lvl_begin + blockIdx.x];
-  int a = A.sptr[s], k = A.sptr[s + 1] - a;
-  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
-  int64_t F = k + u;
-  const double* L = A.Lval + A.loff[s];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < k; t += blockDim.x)
-    xs[t] = x[a + t] - (u > 0 ? A.wbuf[a + t] : 0.0);
-  __syncthreads();
-  int nblk = (k + 31) / 32;
-  for (int bi = nblk - 1; bi >= 0; --bi) {
-    int b0 = bi * 32;
-    int nb = min(32, k - b0);
-    int r0 = b0 + nb;
-    if (r0 < k) {
-      double acc[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-      for (int i = r0 + warp * 32 + lane; i < k; i += nw * 32) {
-        double xv = xs[i];
-        const double* row = L + i + F * b0;
-        double v[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = row[F * min(c, nb - 1)];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] += v[c] * xv;
-      }
-      double v = warp_transpose_reduce(acc, lane);
-      red[warp][lane] = v;
-      __syncthreads();
-      if (threadIdx.x < nb) {
-        double sum = 0.0;
-        for (int w = 0; w < nw; ++w) sum += red[w][threadIdx.x];
-        xs[b0 + threadIdx.x] -= sum;
-      }
-      __syncthreads();
-    }
-    if (warp == 0) {
-      // x_b = inv(L_bb)^T x_b, lane = column (clamped unconditional loads)
-      const double* colp = L + b0 + F * (b0 + min(lane, nb - 1));
-      double v[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = colp[min(i, nb - 1)];
-      double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-      for (int i = 0; i < 32; i += 2) {
-        a0 += (i >= lane && i < nb ? v[i] : 0.0) * xs[b0 + min(i, nb - 1)];
-        a1 += (i + 1 >= lane && i + 1 < nb ? v[i + 1] : 0.0) * xs[b0 + min(i + 1, nb - 1)];
-      }
-      __syncwarp();
-      if (lane < nb) xs[b0 + lane] = a0 + a1;
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < k; t += blockDim.x) {
-    double v = xs[t];
-    x[a + t] = v;
+    for (int w = 0; w < 8; ++w) sum += red[w][threadIdx.x];
+    int cc = a + c0 + threadIdx.x;
+    x[cc] = sum;
     if (ru) {
-      ru[a + t] = -v;
-      rl[a + t] = sigma * (-v) + vu[a + t];
+      ru[cc] = -sum;
+      rl[cc] = sigma * (-sum) + vu[cc];
     }
   }
 }
@@ -421,9 +325,7 @@ void factor_configure(size_t smem_max) {
   int v = (int)smem_max;
   if (smem_max <= 48 * 1024) return;
   RQ_CUDA(cudaFuncSetAttribute(k_front_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-  RQ_CUDA(cudaFuncSetAttribute(k_fb_fwd_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-  RQ_CUDA(cudaFuncSetAttribute(k_fb_fwd_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-  RQ_CUDA(cudaFuncSetAttribute(k_fb_bwd_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  RQ_CUDA(cudaFuncSetAttribute(k_fb_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
 }
 
 void launch_factor(Problem& P, double sigma) {
@@ -451,9 +353,8 @@ void fb_plan(Problem& P) {
     for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
       int s = L.lvl_nodes[q];
       int k = L.sptr[s + 1] - L.sptr[s], u = L.upd_ptr[s + 1] - L.upd_ptr[s];
-      for (int r = 0; r < u; r += 64) fwd.insert(fwd.end(), {s, r, std::min(64, u - r), 0});
-      if (u > 0)
-        for (int c = 0; c < k; c += 32) bwd.insert(bwd.end(), {s, c, std::min(32, k - c), 0});
+      for (int r = 0; r < k + u; r += 32) fwd.insert(fwd.end(), {s, r, std::min(32, k + u - r), 0});
+      for (int c = 0; c < k; c += 32) bwd.insert(bwd.end(), {s, c, std::min(32, k - c), 0});
     }
     P.fwd_lvl[l + 1] = (int32_t)(fwd.size() / 4);
     P.bwd_lvl[l + 1] = (int32_t)(bwd.size() / 4);
@@ -461,7 +362,7 @@ void fb_plan(Problem& P) {
   P.fwd_items.upload(fwd, P.stream);
   P.bwd_items.upload(bwd, P.stream);
   P.zbuf.alloc(L.N);
-  P.wbuf.alloc(L.N);
+  P.wbuf.alloc(1);
 }
 
 void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
@@ -469,26 +370,14 @@ void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* r
   cudaStream_t s = P.stream;
   FBArgs A = fb_args(P);
   for (int l = 0; l < L.nlevels; ++l) {
-    int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
-    k_fb_fwd_tri<<<cnt, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, b, xn);
+    int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
+    k_fb_fwd<<<ic, 128, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
-    int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
-    if (ic > 0) {
-      k_fb_fwd_gemv<<<ic, 64, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, ib);
-      RQ_CUDA(cudaGetLastError());
-      ++P.launches;
-    }
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
-    int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
-    if (ic > 0) {
-      k_fb_bwd_gemv<<<ic, 256, 0, s>>>(A, ib, xn);
-      RQ_CUDA(cudaGetLastError());
-      ++P.launches;
-    }
-    k_fb_bwd_tri<<<cnt, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, b, xn, sigma, vu, ru, rl);
+    k_fb_bwd<<<ic, 256, 0, s>>>(A, ib, xn, sigma, vu, ru, rl);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }
