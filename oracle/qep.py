@@ -13,7 +13,8 @@ Plain FP64 restatement, test infrastructure only.
   matrix; lambda = s + 1/theta (Section 4.1.1, theta = 1/(lambda - s)).
 * Restart: Krylov--Schur (Section 4.1.3; the paper omits the details, this is
   Stewart's scheme): real Schur form of the projected matrix, wanted Ritz
-  values moved to the top, the first k Schur vectors kept.
+  values moved to the top, the first k Schur vectors kept; converged kept
+  Ritz values are locked (moved to the front, their spike entries dropped).
 
 Readings where the paper is silent:
 * wanted set = the neig Ritz values nearest s; for equal distances Im > 0
@@ -109,6 +110,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
     H = np.zeros((m + 1, m))
     V[:, 0] = v1 / b_norm(v1, M)
     k = 0
+    lock = 0        # leading Schur columns locked (converged, decoupled)
     n_apply = 0
     n_vv = 0
     for it in range(max_restarts + 1):
@@ -137,7 +139,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
         wr, wi = _schur_eigs(T)
         order = wanted_order(s + 1.0 / (wr + 1j * wi), s)
         kk = ncand + (m - ncand) // 2
-        sel_idx = set(order[:kk].tolist())
+        sel_idx = set(order[:kk].tolist()) | set(range(lock))
         # keep conjugate partners together
         pos = 0
         while pos < m:
@@ -151,11 +153,17 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
         select[list(sel_idx)] = 1
         T2, Z2, info = _trsen(select, T, Z)
         k = int(select.sum())
-        V[:, :k] = V[:, :m] @ Z2[:, :k]
+        # locking: converged kept Ritz values move to the front and their
+        # spike entries are dropped (decoupled from the active part)
+        conv_pos = _converged_positions(T2, theta, est, want, tol, k)
+        conv_pos[:lock] = 1
+        T3, Z3, info = _trsen(conv_pos.astype(np.int32), T2, Z2)
+        lock = int(conv_pos.sum())
+        V[:, :k] = V[:, :m] @ Z3[:, :k]
         V[:, k] = V[:, m]
         Hn = np.zeros((m + 1, m))
-        Hn[:k, :k] = T2[:k, :k]
-        Hn[k, :k] = beta * Z2[m - 1, :k]
+        Hn[:k, :k] = T3[:k, :k]
+        Hn[k, lock:k] = beta * Z3[m - 1, lock:k]
         H = Hn
     cand = want
     lam_c = lam[cand]
@@ -185,6 +193,30 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
                      n_apply, n_vv)
     res.certified = certified
     return res
+
+
+def _converged_positions(T, theta, est, want, tol, k):
+    """1 at the Schur positions < k holding a converged wanted Ritz value
+    (matched to the eigenvalues of the projected matrix by nearest value);
+    conjugate pairs are flagged together."""
+    wr, wi = _schur_eigs(T)
+    m = T.shape[0]
+    flags = np.zeros(m, dtype=np.int64)
+    good = [i for i in want if est[i] <= tol]
+    for pos in range(k):
+        z = wr[pos] + 1j * wi[pos]
+        j = int(np.argmin(np.abs(theta - z)))
+        if j in good and abs(theta[j] - z) <= 1e-8 * abs(z):
+            flags[pos] = 1
+    pos = 0
+    while pos < k:
+        if pos + 1 < m and T[pos + 1, pos] != 0.0:
+            f = flags[pos] & flags[pos + 1]
+            flags[pos] = flags[pos + 1] = f
+            pos += 2
+        else:
+            pos += 1
+    return flags
 
 
 def _schur_eigs(T):

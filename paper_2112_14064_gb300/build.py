@@ -37,7 +37,7 @@ def build(verbose=False, force=False):
     """Compile and link; returns the library path."""
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "rigaqep.h"))
 
     def compile_one(src):

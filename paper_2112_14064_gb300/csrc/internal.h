@@ -69,6 +69,8 @@ struct RitzOut {
   int32_t k;            // kept dimension after reordering (restart)
   int32_t fail;         // QR did not converge
   int32_t sweeps;       // Francis double-shift sweeps of this step
+  int32_t n_lock;       // leading Schur columns locked after this restart
+  int32_t pad2;
   double beta;
   double lam[2 * kMaxKrylov];    // wanted lambdas (re, im), first neig
   double est[kMaxKrylov];        // Ritz estimates of the wanted pairs

@@ -22,7 +22,7 @@ namespace rq {
 
 size_t ritz_smem(int m);
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
-                 int kwant, int final_pass, double sigma, double tol, cudaStream_t s);
+                 int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s);
 
 namespace {
 
@@ -620,12 +620,13 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
 
   int kwant = nks + (m - nks) / 2;
   int k = 0;
+  int lock = 0;   // leading Schur columns locked (converged, decoupled)
   RitzOut h_out{};
   int restarts = 0;
   int64_t qr_sweeps = 0;
   for (int it = 0;; ++it) {
     for (int j = k; j < m; ++j) W.step(j);
-    launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 0, sigma, tol, s);
+    launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 0, lock, sigma, tol, s);
     ++P.launches;
     RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
     RQ_CUDA(cudaStreamSynchronize(s));
@@ -634,6 +635,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
     qr_sweeps += h_out.sweeps;
     if (h_out.n_conv >= nks || it >= max_restarts) break;
     k = h_out.k;
+    lock = h_out.n_lock;
     // V[:, :k] = V[:, :m] Q ; V[:, k] = V[:, m] ; H = Hnew
     size_t smem = sizeof(double) * (size_t)m * 16;
     dim3 gg((unsigned)((ld + 127) / 128), (unsigned)((k + 15) / 16));
@@ -647,7 +649,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
     ++restarts;
   }
   // final pass: eigenvectors of H for the candidate Ritz values
-  launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 1, sigma, tol, s);
+  launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 1, lock, sigma, tol, s);
   ++P.launches;
   RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
   RQ_CUDA(cudaStreamSynchronize(s));

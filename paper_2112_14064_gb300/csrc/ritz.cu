@@ -19,8 +19,13 @@
 //   5. restart: the wanted blocks are moved to the top of T by adjacent block
 //      swaps (each swap solves the small Sylvester equation A X - X B = C and
 //      applies the orthogonal factor of [X; -I]); the new projected matrix is
-//      [T_kk ; h_{m+1,m} Z(m,1:k)] and the kept basis is V Z(:,1:k).
+//      [T_kk ; h_{m+1,m} Z(m,1:k)] and the kept basis is V Z(:,1:k);
+//   6. locking: converged kept blocks move to the front and their entries of
+//      the spike row are set to zero, so the projected matrix stays block
+//      upper triangular and later steps reduce and iterate only on the
+//      trailing active block (the locked Schur part is left as it is).
 #include "internal.h"
+#include "nr_math.cuh"
 
 namespace rq {
 namespace {
@@ -34,7 +39,7 @@ struct RitzArgs {
   double* Q;         // m x k kept Schur vectors, ld = m
   double* Y;         // final: m x neig eigenvectors of H_m (re, im interleaved)
   RitzOut* out;
-  int m, neig, kwant, final_pass;
+  int m, neig, kwant, final_pass, lock;
   double sigma, tol;
 };
 
@@ -46,6 +51,7 @@ struct Smem {
   double* wi;
   int* rank;
   int* sel;
+  int* cflag;  // converged flag of each Schur position
   double* yr;  // one eigenvector of T (re, im)
   double* yi;
   double* sr;  // running right-hand sides of the back-substitution
@@ -68,11 +74,28 @@ __device__ void house(const double* x, int n, double* v, double& tau, double& be
     for (int i = 1; i < n; ++i) v[i] = 0.0;
     return;
   }
-  double nr = sqrt(alpha * alpha + sg);
+  double nr = sqrt_nr(alpha * alpha + sg);
   beta = alpha <= 0.0 ? nr : -nr;
   double d = alpha - beta;
-  for (int i = 1; i < n; ++i) v[i] = x[i] / d;
-  tau = (beta - alpha) / beta;
+  double rd = rcp_nr(d);
+  for (int i = 1; i < n; ++i) v[i] = x[i] * rd;
+  tau = div_nr(beta - alpha, beta);
+}
+
+// T columns c0..c0+n-1 (rows r0..r1-1) and Z columns c0..c0+n-1 (all m rows)
+// <- cols P in one pass, one row per thread: keeps all four warps busy.
+__device__ void apply_right_tz(double* T, double* Z, int m, const double* v, double tau, int n,
+                               int c0, int r0, int r1, int lane) {
+  if (tau == 0.0) return;
+  int nt = r1 - r0;
+  for (int q = lane; q < nt + m; q += NT) {
+    double* A = q < nt ? T : Z;
+    int r = q < nt ? r0 + q : q - nt;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += v[i] * A[r + m * (c0 + i)];
+    s *= tau;
+    for (int i = 0; i < n; ++i) A[r + m * (c0 + i)] -= s * v[i];
+  }
 }
 
 // rows r0..r0+n-1 of A (ld m) <- P rows, columns c0..c1-1, threads over columns
@@ -236,8 +259,7 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
   for (int q = 0; q < n2; ++q) {
     apply_left(S.T, m, vh[q], tau[q], n, j, j, m, lane);
     __syncthreads();
-    apply_right(S.T, m, vh[q], tau[q], n, j, 0, j + n, lane);
-    apply_right(S.Z, m, vh[q], tau[q], n, j, 0, m, lane);
+    apply_right_tz(S.T, S.Z, m, vh[q], tau[q], n, j, 0, j + n, lane);
     __syncthreads();
   }
   if (lane == 0)
@@ -266,21 +288,21 @@ __device__ double frob(Smem& S, int m, int lane) {
 }
 
 // Real Schur form of the Hessenberg T by Francis double-shift steps.
-__device__ bool francis(Smem& S, int m, int lane, int& sweeps) {
+__device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
   double tn = frob(S, m, lane);
   if (tn == 0.0) tn = 1.0;
   int hi = m - 1, its = 0, total = 0;
   double v[3];
-  while (hi >= 0) {
+  while (hi >= lock) {
     int l = hi;
-    while (l > 0) {
+    while (l > lock) {
       double sc = fabs(TT(l - 1, l - 1)) + fabs(TT(l, l));
       if (sc == 0.0) sc = tn;
       if (fabs(TT(l, l - 1)) <= kEps * sc) break;
       --l;
     }
     __syncthreads();
-    if (l > 0 && lane == 0) TT(l, l - 1) = 0.0;
+    if (l > lock && lane == 0) TT(l, l - 1) = 0.0;
     __syncthreads();
     if (l == hi) { --hi; its = 0; continue; }
     if (l == hi - 1) {
@@ -315,8 +337,7 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps) {
         TT(kq + 1, kq - 1) = 0.0;
         TT(kq + 2, kq - 1) = 0.0;
       }
-      apply_right(S.T, m, v, tau, 3, kq, 0, min(kq + 4, hi + 1), lane);
-      apply_right(S.Z, m, v, tau, 3, kq, 0, m, lane);
+      apply_right_tz(S.T, S.Z, m, v, tau, 3, kq, 0, min(kq + 4, hi + 1), lane);
       __syncthreads();
       x = TT(kq + 1, kq);
       y = TT(kq + 2, kq);
@@ -330,8 +351,7 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps) {
       apply_left(S.T, m, v, tau, 2, kq, kq - 1, m, lane);
       __syncthreads();
       if (lane == 0) TT(kq + 1, kq - 1) = 0.0;
-      apply_right(S.T, m, v, tau, 2, kq, 0, hi + 1, lane);
-      apply_right(S.Z, m, v, tau, 2, kq, 0, m, lane);
+      apply_right_tz(S.T, S.Z, m, v, tau, 2, kq, 0, hi + 1, lane);
       __syncthreads();
     }
   }
@@ -339,25 +359,25 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps) {
   return true;
 }
 
-__device__ void hessenberg(Smem& S, int m, int lane) {
-  for (int c = 0; c + 2 < m; ++c) {
+__device__ void hessenberg(Smem& S, int m, int lane, int lock) {
+  for (int c = lock; c + 2 < m; ++c) {
     int n = m - c - 1;
     // Householder vector of T[c+1:m, c]; computed redundantly
     double alpha = TT(c + 1, c), sg = 0.0;
     for (int i = 1 + lane; i < n; i += NT) sg += TT(c + 1 + i, c) * TT(c + 1 + i, c);
     sg = block_sum(sg, S.red, lane);
     if (sg == 0.0) continue;
-    double nr = sqrt(alpha * alpha + sg);
+    double nr = sqrt_nr(alpha * alpha + sg);
     double beta = alpha <= 0.0 ? nr : -nr;
     double d = alpha - beta;
-    double tau = (beta - alpha) / beta;
+    double tau = div_nr(beta - alpha, beta);
+    double rd = rcp_nr(d);
     __syncthreads();
-    for (int i = lane; i < n; i += NT) S.v[i] = i == 0 ? 1.0 : TT(c + 1 + i, c) / d;
+    for (int i = lane; i < n; i += NT) S.v[i] = i == 0 ? 1.0 : TT(c + 1 + i, c) * rd;
     __syncthreads();
     apply_left(S.T, m, S.v, tau, n, c + 1, c, m, lane);
     __syncthreads();
-    apply_right(S.T, m, S.v, tau, n, c + 1, 0, m, lane);
-    apply_right(S.Z, m, S.v, tau, n, c + 1, 0, m, lane);
+    apply_right_tz(S.T, S.Z, m, S.v, tau, n, c + 1, 0, m, lane);
     __syncthreads();
     if (lane == 0)
       for (int i = 1; i < n; ++i) TT(c + 1 + i, c) = 0.0;
@@ -467,6 +487,7 @@ __global__ void k_ritz(RitzArgs R) {
   S.red = S.si + m;
   S.rank = (int*)(S.red + 4);
   S.sel = S.rank + m;
+  S.cflag = S.sel + m;
 
   for (int i = lane; i < m * m; i += NT) {
     int r = i % m, c = i / m;
@@ -475,9 +496,9 @@ __global__ void k_ritz(RitzArgs R) {
   }
   const double beta = R.H[m + (m + 1) * (m - 1)];
   __syncthreads();
-  hessenberg(S, m, lane);
+  hessenberg(S, m, lane, R.lock);
   int sweeps = 0;
-  bool ok = francis(S, m, lane, sweeps);
+  bool ok = francis(S, m, lane, sweeps, R.lock);
   __syncthreads();
   // eigenvalues in Schur order
   if (lane == 0) {
@@ -513,6 +534,8 @@ __global__ void k_ritz(RitzArgs R) {
   double tnorm = frob(S, m, lane);
   double smin = fmax(kEps * tnorm, 1e-300);
   int nconv = 0;
+  for (int i = lane; i < m; i += NT) S.cflag[i] = 0;
+  __syncthreads();
   // wanted pairs: eigenvectors, estimates and (final pass) outputs
   for (int pos = 0; pos < m; ++pos) {
     int rk = S.rank[pos];
@@ -535,6 +558,7 @@ __global__ void k_ritz(RitzArgs R) {
     double theta = hypot(lr, li);
     double est = fabs(beta) * hypot(lastr, lasti) / (nrm * theta);
     if (est <= R.tol) ++nconv;
+    if (lane == 0) S.cflag[pos] = est <= R.tol ? 1 : 0;
     if (lane == 0) {
       // lambda = s + 1/theta
       double ir, ii;
@@ -562,7 +586,8 @@ __global__ void k_ritz(RitzArgs R) {
   }
   if (R.final_pass) return;
   // select the kwant nearest, never splitting a conjugate pair
-  for (int i = lane; i < m; i += NT) S.sel[i] = S.rank[i] < R.kwant ? 1 : 0;
+  // locked blocks always stay (they sit at the top with a zero spike)
+  for (int i = lane; i < m; i += NT) S.sel[i] = (S.rank[i] < R.kwant || i < R.lock) ? 1 : 0;
   __syncthreads();
   if (lane == 0) {
     int pos = 0;
@@ -587,12 +612,15 @@ __global__ void k_ritz(RitzArgs R) {
       while (here > ks) {
         int nbf = (here >= 2 && TT(here - 1, here - 2) != 0.0) ? 2 : 1;
         int prev = here - nbf;
+        int cf_sel[2] = {S.cflag[here], bs == 2 ? S.cflag[here + 1] : 0};
+        int cf_oth[2] = {S.cflag[prev], nbf == 2 ? S.cflag[prev + 1] : 0};
+        __syncthreads();
         swap_blocks(S, m, prev, nbf, bs, tnorm, lane);
         // the selected block now starts at prev; keep the flags in step
         __syncthreads();
         if (lane == 0) {
-          for (int i = 0; i < bs; ++i) S.sel[prev + i] = 1;
-          for (int i = 0; i < nbf; ++i) S.sel[prev + bs + i] = 0;
+          for (int i = 0; i < bs; ++i) { S.sel[prev + i] = 1; S.cflag[prev + i] = cf_sel[i]; }
+          for (int i = 0; i < nbf; ++i) { S.sel[prev + bs + i] = 0; S.cflag[prev + bs + i] = cf_oth[i]; }
         }
         __syncthreads();
         here = prev;
@@ -603,28 +631,60 @@ __global__ void k_ritz(RitzArgs R) {
   }
   __syncthreads();
   int k = ks;
+  // locking: converged blocks among the kept ones move to the front (after
+  // the blocks locked earlier); their spike entries are dropped below, which
+  // decouples them from the rest of the projected matrix
+  int nl = R.lock;
+  pos = R.lock;
+  while (pos < k) {
+    int bs = (pos + 1 < m && TT(pos + 1, pos) != 0.0) ? 2 : 1;
+    bool conv = S.cflag[pos] && (bs == 1 || S.cflag[pos + 1]);
+    if (conv) {
+      int here = pos;
+      while (here > nl) {
+        int nbf = (here >= 2 && TT(here - 1, here - 2) != 0.0) ? 2 : 1;
+        int prev = here - nbf;
+        int cf_oth[2] = {S.cflag[prev], nbf == 2 ? S.cflag[prev + 1] : 0};
+        __syncthreads();
+        swap_blocks(S, m, prev, nbf, bs, tnorm, lane);
+        __syncthreads();
+        if (lane == 0) {
+          for (int i = 0; i < bs; ++i) S.cflag[prev + i] = 1;
+          for (int i = 0; i < nbf; ++i) S.cflag[prev + bs + i] = cf_oth[i];
+        }
+        __syncthreads();
+        here = prev;
+      }
+      nl += bs;
+    }
+    pos += bs;
+  }
+  __syncthreads();
   for (int i = lane; i < (m + 1) * m; i += NT) {
     int r = i % (m + 1), c = i / (m + 1);
     double v = 0.0;
     if (c < k) {
       if (r < k) v = TT(r, c);
-      else if (r == k) v = beta * ZZ(m - 1, c);
+      else if (r == k && c >= nl) v = beta * ZZ(m - 1, c);
     }
     R.Hnew[i] = v;
   }
   for (int i = lane; i < m * k; i += NT) R.Q[i] = S.Z[i];
-  if (lane == 0) R.out->k = k;
+  if (lane == 0) {
+    R.out->k = k;
+    R.out->n_lock = nl;
+  }
 }
 
 }  // namespace
 
 size_t ritz_smem(int m) {
-  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 2 * sizeof(int) * m;
+  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 3 * sizeof(int) * m;
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
-                 int kwant, int final_pass, double sigma, double tol, cudaStream_t s) {
-  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, sigma, tol};
+                 int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s) {
+  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol};
   size_t smem = ritz_smem(m);
   RQ_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_ritz<<<1, NT, smem, s>>>(R);

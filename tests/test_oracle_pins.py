@@ -279,7 +279,8 @@ def test_eigs_match_dense_qz():
     ref = _dense_nearest(A, 20.0, 10)
     assert _match(ref, r.lam) < 1e-10
     assert _match(r.lam, ref) < 1e-10
-    assert np.all(r.eta < 1e-12)
+    # locked pairs stop at the convergence tolerance; the target is eta <= 1e-10
+    assert np.all(r.eta <= 1e-10)
 
 
 def test_proportional_damping_closed_form():
