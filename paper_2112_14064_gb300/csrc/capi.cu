@@ -153,6 +153,7 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
     need(smax <= 200 * 1024, RIGAQEP_ERR_ARG, "front too large for one CTA");
     rq::factor_configure(smax);
     rq::fb_plan(P);
+    rq::factor_plan(P);
     RQ_CUDA(cudaStreamSynchronize(s));
     P.info.nsuper = L.nsuper;
     P.info.nlevels = L.nlevels;

@@ -11,11 +11,12 @@
 // The front is the L panel plus the U block (the upper-right part is the
 // symmetric counterpart and is never stored).
 //
-// Factorisation, one launch pair per tree level (all fronts of a level in
-// parallel, one CTA per front): (1) zero the front, place the original entries
-// of the pivot columns and extend-add the children's U blocks; (2) right-
-// looking LDL^T of the k pivot columns with the rank-1 updates applied to the
-// pivot block, to L21 and to the U block.
+// Factorisation, per tree level (all fronts of a level together): (1) one CTA
+// per front zeroes the front, places the original entries of the pivot
+// columns and extend-adds the children's U blocks; (2) one CTA per front
+// factorises the k x k pivot block (LDL^T) and inverts L11; then, spread over
+// many CTAs, (3) L21 = F21 inv(L11)^T D^{-1} in 16-row chunks, (4) the Schur
+// complement U -= L21 D L21^T in 32 x 32 tiles and (5) W = L21 inv(L11).
 //
 // Partitioned inverse: at the end of each front's factorisation the unit-lower
 // pivot block L11 is replaced by inv(L11) and L21 by W = L21 inv(L11), so a
@@ -46,12 +47,14 @@ struct FrontArgs {
   double* Lval;
   double* Uval;
   double* Dinv;
+  double* Dval;
   DevStatus* status;
 };
 
 FrontArgs front_args(Problem& P) {
-  return FrontArgs{P.sptr.p, P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p, P.child_idx.p,
-                   P.lvl_nodes.p, P.loff.p, P.uoff.p, P.Lval.p, P.Uval.p, P.Dinv.p, P.status.p};
+  return FrontArgs{P.sptr.p,   P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
+                   P.child_idx.p, P.lvl_nodes.p, P.loff.p, P.uoff.p, P.Lval.p,
+                   P.Uval.p,   P.Dinv.p,    P.Dval.p,    P.status.p};
 }
 
 __global__ void k_front_assemble(FrontArgs A, int lvl_begin, const int32_t* rowptr_n,
@@ -93,15 +96,18 @@ __global__ void k_front_assemble(FrontArgs A, int lvl_begin, const int32_t* rowp
   }
 }
 
-__global__ void k_front_factor(FrontArgs A, int lvl_begin) {
-  extern __shared__ double lb[];  // scaled column l (front order)
+// Pivot block of one front (one CTA): right-looking LDL^T of the k x k
+// pivot block (rows < k only), D and D^{-1} stored, then inv(L11) in place
+// (unit lower; column j from the already inverted trailing block, last
+// column first, staged in shared memory).
+__global__ void k_pivot_factor(FrontArgs A, int lvl_begin) {
+  extern __shared__ double lb[];
   __shared__ double dsh;
   int s = A.lvl_nodes[lvl_begin + blockIdx.x];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
   double* L = A.Lval + A.loff[s];
-  double* U = A.Uval + A.uoff[s];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = 0; t < k; ++t) {
     if (threadIdx.x == 0) {
@@ -113,34 +119,24 @@ __global__ void k_front_factor(FrontArgs A, int lvl_begin) {
       dsh = d;
       L[t + F * t] = 1.0;
       A.Dinv[a + t] = 1.0 / d;
+      A.Dval[a + t] = d;
     }
     __syncthreads();
     double d = dsh;
     double rd = 1.0 / d;
-    for (int64_t i = t + 1 + threadIdx.x; i < F; i += blockDim.x) {
+    for (int i = t + 1 + threadIdx.x; i < k; i += blockDim.x) {
       double l = L[i + F * t] * rd;
       lb[i] = l;
       L[i + F * t] = l;
     }
     __syncthreads();
-    // pivot-block columns c in (t, k): rows i >= c of the L panel
     for (int c = t + 1 + warp; c < k; c += nw) {
       double lc = d * lb[c];
-      for (int64_t i = c + lane; i < F; i += 32) L[i + F * c] -= lb[i] * lc;
-    }
-    // U block columns c' in [0, u): rows i' >= c'
-    for (int c = warp; c < u; c += nw) {
-      double lc = d * lb[k + c];
-      for (int i = c + lane; i < u; i += 32) U[i + (int64_t)u * c] -= lb[k + i] * lc;
+      for (int i = c + lane; i < k; i += 32) L[i + F * c] -= lb[i] * lc;
     }
     __syncthreads();
   }
-  // Partitioned inverse for the FB solves: L11 <- inv(L11) (unit lower,
-  // column j from the already inverted trailing block, last column first),
-  // then L21 <- W = L21 inv(L11) (each thread one row, columns left to right;
-  // column j only needs original columns >= j).
   for (int j = k - 2; j >= 0; --j) {
-    // new column j (rows j+1..k-1) into shared memory, then written back
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
       double v0 = 0.0, v1 = 0.0;
       int c = j + 1;
@@ -155,20 +151,112 @@ __global__ void k_front_factor(FrontArgs A, int lvl_begin) {
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) L[i + F * j] = lb[i];
     __syncthreads();
   }
-  for (int64_t i = k + threadIdx.x; i < F; i += blockDim.x) {
-    for (int j = 0; j < k; ++j) {
-      double w0 = L[i + F * j], w1 = 0.0;   // L21[i, j] times inv(L11)[j, j] = 1
-      int c = j + 1;
-      for (; c + 1 < k; c += 2) {
-        w0 += L[i + F * c] * L[c + F * j];
-        w1 += L[i + F * (c + 1)] * L[(c + 1) + F * j];
+}
+
+// Row chunks of the update rows (items: front, first update row, rows <= 16):
+// mode 0: L21 = F21 inv(L11)^T D^{-1}   (X[i, j] = D_j^{-1} sum_{c<=j} F21[i,c] inv(L11)[j,c])
+// mode 1: W   = L21 inv(L11)            (W[i, j] = sum_{c>=j} L21[i,c] inv(L11)[c,j])
+// in place: the chunk's outputs are staged in shared memory and written back
+// after every read of the original rows.  32 x 32 tiles of inv(L11) and
+// 16 x 32 tiles of the rows are staged in shared memory (coalesced loads).
+__global__ void __launch_bounds__(256) k_panel_rows(FrontArgs A, const int4* items, int item_begin,
+                                                    int mode) {
+  extern __shared__ double out[];          // 16 x k, row-major
+  __shared__ double ta[16][33];            // rows x c
+  __shared__ double tb[32][33];            // c x j  (or j x c)
+  int4 it = items[item_begin + blockIdx.x];
+  int s = it.x, r0 = it.y, nr = it.z;
+  int a = A.sptr[s], k = A.sptr[s + 1] - a;
+  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
+  int64_t F = k + u;
+  double* L = A.Lval + A.loff[s];
+  double* R = L + k + r0;                  // first row of the chunk (column stride F)
+  int tid = threadIdx.x;
+  int orow = tid >> 4;                     // 0..15: output row
+  int ocol = (tid & 15) * 2;               // two output columns within the j tile
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    double acc0 = 0.0, acc1 = 0.0;
+    int cb = mode == 0 ? 0 : j0;           // inner range (triangle of inv(L11))
+    int ce = mode == 0 ? min(k, j0 + 32) : k;
+    for (int c0 = cb; c0 < ce; c0 += 32) {
+      for (int q = tid; q < 16 * 32; q += 256) {
+        int r = q & 15, c = q >> 4;
+        ta[r][c] = (r < nr && c0 + c < k) ? R[r + F * (c0 + c)] : 0.0;
       }
-      for (; c < k; ++c) w0 += L[i + F * c] * L[c + F * j];
-      L[i + F * j] = w0 + w1;
+      for (int q = tid; q < 32 * 32; q += 256) {
+        int x = q & 31, y = q >> 5;
+        // mode 0 needs inv(L11)[j, c]: x = j offset (rows contiguous), y = c offset
+        // mode 1 needs inv(L11)[c, j]: x = c offset (rows contiguous), y = j offset
+        if (mode == 0)
+          tb[y][x] = (j0 + x < k && c0 + y < k) ? L[(j0 + x) + F * (c0 + y)] : 0.0;
+        else
+          tb[x][y] = (c0 + x < k && j0 + y < k) ? L[(c0 + x) + F * (j0 + y)] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) {
+        double av = ta[orow][c];
+        acc0 += av * tb[c][ocol];
+        acc1 += av * tb[c][ocol + 1];
+      }
+      __syncthreads();
     }
+    int j = j0 + ocol;
+    if (mode == 0) {
+      if (j < k) out[orow * k + j] = acc0 * A.Dinv[a + j];
+      if (j + 1 < k) out[orow * k + j + 1] = acc1 * A.Dinv[a + j + 1];
+    } else {
+      if (j < k) out[orow * k + j] = acc0;
+      if (j + 1 < k) out[orow * k + j + 1] = acc1;
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nr * k; q += 256) {
+    int r = q % nr, c = q / nr;
+    R[r + F * c] = out[r * k + c];
   }
 }
 
+// Schur complement, one 32 x 32 tile (I >= J) of the update block per CTA:
+// U[I, J] -= L21[I, :] D L21[J, :]^T, 32-column slabs staged in shared memory.
+__global__ void __launch_bounds__(256) k_schur_tile(FrontArgs A, const int4* items, int item_begin) {
+  __shared__ double ta[32][33];
+  __shared__ double tb[32][33];
+  int4 it = items[item_begin + blockIdx.x];
+  int s = it.x, I0 = it.y, J0 = it.z;
+  int a = A.sptr[s], k = A.sptr[s + 1] - a;
+  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
+  int64_t F = k + u;
+  const double* L21 = A.Lval + A.loff[s] + k;   // row i of L21 at L21[i + F c]
+  double* U = A.Uval + A.uoff[s];
+  int tid = threadIdx.x;
+  int ty = tid >> 4, tx = tid & 15;              // 16 x 16 threads, 2 x 2 outputs each
+  double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+  for (int c0 = 0; c0 < k; c0 += 32) {
+    for (int q = tid; q < 32 * 32; q += 256) {
+      int r = q & 31, c = q >> 5;
+      bool okc = c0 + c < k;
+      ta[r][c] = (I0 + r < u && okc) ? L21[(I0 + r) + F * (c0 + c)] : 0.0;
+      tb[r][c] = (J0 + r < u && okc) ? L21[(J0 + r) + F * (c0 + c)] * A.Dval[a + c0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {
+      double a0 = ta[2 * ty][c], a1 = ta[2 * ty + 1][c];
+      double b0 = tb[2 * tx][c], b1 = tb[2 * tx + 1][c];
+      c00 += a0 * b0;
+      c01 += a0 * b1;
+      c10 += a1 * b0;
+      c11 += a1 * b1;
+    }
+    __syncthreads();
+  }
+  int i = I0 + 2 * ty, j = J0 + 2 * tx;
+  if (i < u && j < u) U[i + (int64_t)u * j] -= c00;
+  if (i < u && j + 1 < u) U[i + (int64_t)u * (j + 1)] -= c01;
+  if (i + 1 < u && j < u) U[(i + 1) + (int64_t)u * j] -= c10;
+  if (i + 1 < u && j + 1 < u) U[(i + 1) + (int64_t)u * (j + 1)] -= c11;
+}
 
 struct FBArgs {
   const int32_t* sptr;
@@ -324,23 +412,68 @@ __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, in
 void factor_configure(size_t smem_max) {
   int v = (int)smem_max;
   if (smem_max <= 48 * 1024) return;
-  RQ_CUDA(cudaFuncSetAttribute(k_front_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
   RQ_CUDA(cudaFuncSetAttribute(k_fb_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+}
+
+void factor_plan(Problem& P) {
+  Plan& L = P.plan;
+  std::vector<int32_t> rows, tiles;
+  P.row_lvl.assign(L.nlevels + 1, 0);
+  P.tile_lvl.assign(L.nlevels + 1, 0);
+  for (int l = 0; l < L.nlevels; ++l) {
+    for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
+      int s = L.lvl_nodes[q];
+      int u = L.upd_ptr[s + 1] - L.upd_ptr[s];
+      for (int r = 0; r < u; r += 16) rows.insert(rows.end(), {s, r, std::min(16, u - r), 0});
+      for (int I = 0; I < u; I += 32)
+        for (int J = 0; J <= I; J += 32) tiles.insert(tiles.end(), {s, I, J, 0});
+    }
+    P.row_lvl[l + 1] = (int32_t)(rows.size() / 4);
+    P.tile_lvl[l + 1] = (int32_t)(tiles.size() / 4);
+  }
+  P.row_items.upload(rows, P.stream);
+  P.tile_items.upload(tiles, P.stream);
+  P.Dval.alloc(L.N);
+  size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
+  if (smem > 48 * 1024)
+    RQ_CUDA(cudaFuncSetAttribute(k_panel_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (sizeof(double) * (size_t)L.max_front > 48 * 1024)
+    RQ_CUDA(cudaFuncSetAttribute(k_pivot_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double) * L.max_front)));
 }
 
 void launch_factor(Problem& P, double sigma) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FrontArgs A = front_args(P);
+  const int4* rows = (const int4*)P.row_items.p;
+  const int4* tiles = (const int4*)P.tile_items.p;
   for (int l = 0; l < L.nlevels; ++l) {
     int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
     k_front_assemble<<<cnt, 256, 0, s>>>(A, b, P.rowptr_n.p, P.fpos.p, P.Kn.p, P.Mn.p, P.Cn.p,
                                          sigma * sigma, sigma);
     RQ_CUDA(cudaGetLastError());
-    size_t smem = sizeof(double) * (size_t)P.lvl_maxF[l];
-    k_front_factor<<<cnt, 256, smem, s>>>(A, b);
+    k_pivot_factor<<<cnt, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, b);
     RQ_CUDA(cudaGetLastError());
     P.launches += 2;
+    int rb = P.row_lvl[l], rc = P.row_lvl[l + 1] - rb;
+    int tb = P.tile_lvl[l], tc = P.tile_lvl[l + 1] - tb;
+    size_t smem = sizeof(double) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);
+    if (rc > 0) {
+      k_panel_rows<<<rc, 256, smem, s>>>(A, rows, rb, 0);            // L21
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
+    if (tc > 0) {
+      k_schur_tile<<<tc, 256, 0, s>>>(A, tiles, tb);                 // U -= L21 D L21^T
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
+    if (rc > 0) {
+      k_panel_rows<<<rc, 256, smem, s>>>(A, rows, rb, 1);            // W = L21 inv(L11)
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
   }
 }
 

@@ -98,7 +98,9 @@ struct Problem {
   DBuf<int32_t> perm, iperm, sptr, upd_ptr, upd_idx, relmap, child_ptr, child_idx, lvl_nodes;
   DBuf<int64_t> loff, uoff;
   // numeric factor
-  DBuf<double> Lval, Uval, Dinv;
+  DBuf<double> Lval, Uval, Dinv, Dval;
+  DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
+  std::vector<int32_t> row_lvl, tile_lvl;
   DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
   DBuf<double> xwork;           // FB work vector (N)
   DBuf<double> zbuf, wbuf;      // FB intermediates (N)
@@ -126,6 +128,7 @@ void launch_norms(Problem& P);
 void launch_factor(Problem& P, double sigma);
 void factor_configure(size_t smem_max);
 void fb_plan(Problem& P);
+void factor_plan(Problem& P);
 // FB solve of Q x = b in the ND order, in place on xn (device, length N).
 // If vu != nullptr the backward sweep writes r_u = -x to ru and
 // r_l = sigma * r_u + vu to rl instead of writing x back (the operator step).

@@ -376,11 +376,6 @@ __global__ void k_eta(const double* part, int nblk, const double* lam, double nK
   eta[t] = sqrt(s) / ((al * al * nM + al * nC + nK) * sqrt(sx));
 }
 
-__global__ void k_copy_lam(const RitzOut* out, double* lam, int neig) {
-  int t = threadIdx.x;
-  if (t < 2 * neig) lam[t] = out->lam[t];
-}
-
 // ---- damping sensitivity ----
 // partial sums of x^T (2 l M + C) x (unconjugated) for column t
 __global__ void k_gden(const int32_t* rowptr, const int32_t* col, const double* M, const double* C,

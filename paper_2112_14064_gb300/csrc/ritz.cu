@@ -110,18 +110,6 @@ __device__ void apply_left(double* A, int m, const double* v, double tau, int n,
   }
 }
 
-// columns c0..c0+n-1 of A <- cols P, rows r0..r1-1, threads over rows
-__device__ void apply_right(double* A, int m, const double* v, double tau, int n, int c0, int r0,
-                            int r1, int lane) {
-  if (tau == 0.0) return;
-  for (int r = r0 + lane; r < r1; r += NT) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += v[i] * A[r + m * (c0 + i)];
-    s *= tau;
-    for (int i = 0; i < n; ++i) A[r + m * (c0 + i)] -= s * v[i];
-  }
-}
-
 // Plane rotation G = [[c, -s], [s, c]] on rows/cols j, j+1: T <- G^T T G, Z <- Z G
 __device__ void rotate(Smem& S, int m, int j, double c, double s, int lane) {
   __syncthreads();
