@@ -5,7 +5,7 @@ C^0 lines every 16 elements (82,369 DOFs): Gauss-quadrature assembly of
 K, M, C, the symbolic phase, the multifrontal factorisation and the
 Krylov-Schur eigensolve of the 20 eigenpairs nearest the target 500
 (FP64).  The spectral shift is placed inside the spectrum region (shift 0,
-56 candidates, Krylov dimension 72) and the selection nearest the target is
+56 candidates, Krylov dimension 88) and the selection nearest the target is
 certified; a pair counts only when its backward error is <= 1e-10 and the
 selection is certified.
 
@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "p3_256_b16"
-TARGET_KW = dict(m=72, shift=0.0, ncand=56)
+TARGET_KW = dict(m=88, shift=0.0, ncand=56)
 ETA_MAX = 1e-10
 METRIC = "eigenpairs/s at rel. residual <= 1e-10 (FP64)"
 UNIT = "eigenpairs/s"
@@ -295,7 +295,8 @@ def run_ours(args):
         "factor": {"tflops": inf["factor_flops"] / (inf["factor_ms"] * 1e-3) / 1e12,
                    "ms": inf["factor_ms"], "flops": inf["factor_flops"]},
         "solve": {"n_apply": inf["n_apply"], "n_restarts": inf["n_restarts"],
-                  "certified": inf["certified"], "eigs_ms": inf["eigs_ms"]},
+                  "certified": inf["certified"], "eigs_ms": inf["eigs_ms"],
+                  "fb_ms": inf["fb_ms"], "ritz_ms": inf["ritz_ms"]},
         "clocks": clocks.summary(),
         "e2e": {"value": 1e3 * all_e2e_pairs / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (cfg["ne"] ** 2) + 16 * N,

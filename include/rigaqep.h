@@ -123,6 +123,10 @@ typedef struct {
   double cert_margin;    /* lower bound on the distance of any other eigenvalue to the
                             target, minus the largest returned distance (>= 0 when certified) */
   int64_t n_launches;    /* kernels launched by the last eigs (including its factorisation) */
+  double ritz_ms;        /* device time of its Ritz/restart steps (before the final pass) */
+  double ritz_phase_cycles[6];  /* SM cycles of those steps by phase: Hessenberg reduction,
+                                   QR sweeps, eigenvalues and ranks, Ritz vectors and
+                                   estimates, reordering, locking */
 } rigaqep_info;
 
 /* Create a handle and assemble K, M, C (original DOF order, one CSR

@@ -72,6 +72,7 @@ struct RitzOut {
   int32_t n_lock;       // leading Schur columns locked after this restart
   int32_t pad2;
   double beta;
+  long long phase_cycles[6];     // hessenberg, QR, eigenvalues+ranks, eigvecs, reorder, lock
   double lam[2 * kMaxKrylov];    // wanted lambdas (re, im), first neig
   double est[kMaxKrylov];        // Ritz estimates of the wanted pairs
 };

@@ -489,8 +489,12 @@ struct Work {
   std::vector<cudaEvent_t> ev;
   int ev_used = 0;
   double fb_ms = 0.0;
+  cudaEvent_t rz[2] = {nullptr, nullptr};   // around each Ritz step
+  double ritz_ms = 0.0;
   ~Work() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : rz)
+      if (e) cudaEventDestroy(e);
   }
   void fb_events(int count) {
     while ((int)ev.size() < 2 * count) {
@@ -577,6 +581,8 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   const uint64_t seed = E.seed;
   Work W{P, m, L.N, 0, 0, 0, s, sigma};
   W.fb_events(m + 1);
+  RQ_CUDA(cudaEventCreate(&W.rz[0]));
+  RQ_CUDA(cudaEventCreate(&W.rz[1]));
   W.Np = (L.N + 31) / 32 * 32;
   W.ld = 2 * W.Np;
   W.nblk = 2 * 152;
@@ -618,16 +624,25 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   int lock = 0;   // leading Schur columns locked (converged, decoupled)
   RitzOut h_out{};
   int restarts = 0;
+  for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] = 0.0;
   int64_t qr_sweeps = 0;
   for (int it = 0;; ++it) {
     for (int j = k; j < m; ++j) W.step(j);
+    RQ_CUDA(cudaEventRecord(W.rz[0], s));
     launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 0, lock, sigma, tol, s);
+    RQ_CUDA(cudaEventRecord(W.rz[1], s));
     ++P.launches;
     RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
     RQ_CUDA(cudaStreamSynchronize(s));
     W.fb_collect();
+    {
+      float ms = 0.f;
+      RQ_CUDA(cudaEventElapsedTime(&ms, W.rz[0], W.rz[1]));
+      W.ritz_ms += ms;
+    }
     if (h_out.fail) throw Error(RIGAQEP_ERR_INTERNAL, "QR iteration on the projected matrix did not converge");
     qr_sweeps += h_out.sweeps;
+    for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] += (double)h_out.phase_cycles[q];
     if (h_out.n_conv >= nks || it >= max_restarts) break;
     k = h_out.k;
     lock = h_out.n_lock;
@@ -729,6 +744,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   P.info.n_vv = W.n_vv;
   P.info.n_qr_sweeps = qr_sweeps;
   P.info.fb_ms = W.fb_ms;
+  P.info.ritz_ms = W.ritz_ms;
   P.info.n_launches = P.launches;
   *n_conv = sel_conv;
 }

@@ -57,6 +57,7 @@ struct Smem {
   double* sr;  // running right-hand sides of the back-substitution
   double* si;
   double* red; // 4 partial sums
+  struct Refl* refl;  // reflectors of the current QR sweep
 };
 
 #define TT(r, c) S.T[(r) + m * (c)]
@@ -144,21 +145,36 @@ __device__ bool standardize2(Smem& S, int m, int j, int lane) {
   bool cplx;
   if (disc >= 0.0) {
     // eigenvector of the eigenvalue l1; g1 = (c, s) spans it
-    double rt = sqrt(disc);
+    double rt = sqrt_nr(disc);
     double l1 = 0.5 * (a + d) + (hp >= 0.0 ? rt : -rt);
     double x1 = b, y1 = l1 - a;      // from the first row
     double x2 = l1 - d, y2 = e;      // from the second row
     double n1 = x1 * x1 + y1 * y1, n2 = x2 * x2 + y2 * y2;
     double x = n1 >= n2 ? x1 : x2, y = n1 >= n2 ? y1 : y2;
-    double nr = sqrt(x * x + y * y);
-    c = x / nr;
-    s = y / nr;
+    double rn = rcp_nr(sqrt_nr(x * x + y * y));
+    c = x * rn;
+    s = y * rn;
     cplx = false;
   } else {
-    // T'11 - T'22 = cos(2t)(a - d) + sin(2t)(b + e) = 0
-    double th = 0.5 * atan2(-(a - d), b + e);
-    c = cos(th);
-    s = sin(th);
+    // T'11 - T'22 = cos(2t)(a - d) + sin(2t)(b + e) = 0: with
+    // (cos 2t, sin 2t) = (q, p)/r, half-angle formulas give (cos t, sin t)
+    double pp = -(a - d), qq = b + e;
+    double r2 = pp * pp + qq * qq;
+    if (r2 == 0.0) {
+      c = 1.0;
+      s = 0.0;
+    } else {
+      double rr = rcp_nr(sqrt_nr(r2));
+      double c2 = qq * rr, s2 = pp * rr;
+      if (c2 >= 0.0) {
+        c = sqrt_nr(0.5 * (1.0 + c2));
+        s = s2 * 0.5 * rcp_nr(c);
+      } else {
+        s = sqrt_nr(0.5 * (1.0 - c2));
+        if (s2 < 0.0) s = -s;
+        c = s2 * 0.5 * rcp_nr(s);
+      }
+    }
     cplx = true;
   }
   rotate(S, m, j, c, s, lane);
@@ -211,8 +227,9 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
         G[piv][c] = t;
       }
     if (fabs(G[col][col]) < smin) G[col][col] = G[col][col] >= 0.0 ? smin : -smin;
+    double rp = rcp_nr(G[col][col]);
     for (int r = col + 1; r < ns; ++r) {
-      double f = G[r][col] / G[col][col];
+      double f = G[r][col] * rp;
       for (int c = col; c <= ns; ++c) G[r][c] -= f * G[col][c];
     }
   }
@@ -220,7 +237,7 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
   for (int r = ns - 1; r >= 0; --r) {
     double t = G[r][ns];
     for (int c = r + 1; c < ns; ++c) t -= G[r][c] * xs[c];
-    xs[r] = t / G[r][r];
+    xs[r] = t * rcp_nr(G[r][r]);
   }
   // W = [X; -I] (n x n2); Householder QR, reflectors kept in vh
   double W[4][2];
@@ -276,11 +293,61 @@ __device__ double frob(Smem& S, int m, int lane) {
 }
 
 // Real Schur form of the Hessenberg T by Francis double-shift steps.
+// Reflector P = I - tau u u^T with P x = beta e_0 for x of length n (2 or 3):
+// u = x - beta e_0, beta = -sign(x_0) ||x||, and u^T u = 2 beta (beta - x_0),
+// so tau = 2 / u^T u = 1 / (beta (beta - x_0)): one square root, one reciprocal.
+struct Refl {
+  double u0, u1, u2, tau;
+  int pos, n;
+};
+
+__device__ __forceinline__ void make_refl(double x0, double x1, double x2, int n, Refl& r) {
+  double sg = x1 * x1 + (n == 3 ? x2 * x2 : 0.0);
+  r.n = n;
+  if (sg == 0.0) {
+    r.u0 = 1.0; r.u1 = 0.0; r.u2 = 0.0; r.tau = 0.0;
+    return;
+  }
+  double nr = sqrt_nr(x0 * x0 + sg);
+  double beta = x0 <= 0.0 ? nr : -nr;
+  r.u0 = x0 - beta;
+  r.u1 = x1;
+  r.u2 = n == 3 ? x2 : 0.0;
+  r.tau = rcp_nr(beta * (beta - x0));
+}
+
+// rows pos..pos+n-1 of column c of A (ld m) <- P (rows)
+__device__ __forceinline__ void refl_col(double* A, int m, const Refl& r, int c) {
+  double* a = A + r.pos + m * c;
+  double s = r.u0 * a[0] + r.u1 * a[1];
+  if (r.n == 3) s += r.u2 * a[2];
+  s *= r.tau;
+  a[0] -= s * r.u0;
+  a[1] -= s * r.u1;
+  if (r.n == 3) a[2] -= s * r.u2;
+}
+
+// columns pos..pos+n-1 of row i of A <- (cols) P
+__device__ __forceinline__ void refl_row(double* A, int m, const Refl& r, int i) {
+  double* a = A + i + m * r.pos;
+  double s = r.u0 * a[0] + r.u1 * a[m];
+  if (r.n == 3) s += r.u2 * a[2 * m];
+  s *= r.tau;
+  a[0] -= s * r.u0;
+  a[m] -= s * r.u1;
+  if (r.n == 3) a[2 * m] -= s * r.u2;
+}
+
+// Real Schur form of the Hessenberg T by Francis double-shift sweeps.  During
+// a sweep on the active window [l, hi] only window entries are updated (the
+// bulge chase reads nothing else); the sweep's reflectors are kept and, after
+// it, applied to the columns right of the window, the rows above it and Z,
+// one column or row per thread in order, without barriers.
 __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
   double tn = frob(S, m, lane);
   if (tn == 0.0) tn = 1.0;
   int hi = m - 1, its = 0, total = 0;
-  double v[3];
+  Refl* rl = S.refl;
   while (hi >= lock) {
     int l = hi;
     while (l > lock) {
@@ -314,34 +381,51 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
     double x = TT(l, l) * TT(l, l) + TT(l, l + 1) * TT(l + 1, l) - sh * TT(l, l) + th;
     double y = TT(l + 1, l) * (TT(l, l) + TT(l + 1, l + 1) - sh);
     double z = TT(l + 1, l) * TT(l + 2, l + 1);
-    for (int kq = l; kq <= hi - 2; ++kq) {
-      double xv[3] = {x, y, z}, tau, beta;
-      house(xv, 3, v, tau, beta);
+    int nref = 0;
+    for (int kq = l; kq <= hi - 1; ++kq) {
+      int n = kq <= hi - 2 ? 3 : 2;
+      Refl r;
+      make_refl(x, y, z, n, r);
+      r.pos = kq;
+      if (lane == 0) rl[nref] = r;
+      ++nref;
       int c0 = kq > l ? kq - 1 : l;
       __syncthreads();
-      apply_left(S.T, m, v, tau, 3, kq, c0, m, lane);
+      if (r.tau != 0.0)
+        for (int c = c0 + lane; c <= hi; c += NT) refl_col(S.T, m, r, c);
       __syncthreads();
       if (kq > l && lane == 0) {
         TT(kq + 1, kq - 1) = 0.0;
-        TT(kq + 2, kq - 1) = 0.0;
+        if (n == 3) TT(kq + 2, kq - 1) = 0.0;
       }
-      apply_right_tz(S.T, S.Z, m, v, tau, 3, kq, 0, min(kq + 4, hi + 1), lane);
+      if (r.tau != 0.0)
+        for (int i = l + lane; i <= min(kq + 3, hi); i += NT) refl_row(S.T, m, r, i);
       __syncthreads();
-      x = TT(kq + 1, kq);
-      y = TT(kq + 2, kq);
-      if (kq < hi - 2) z = TT(kq + 3, kq);
+      if (n == 3) {
+        x = TT(kq + 1, kq);
+        y = TT(kq + 2, kq);
+        if (kq < hi - 2) z = TT(kq + 3, kq);
+      }
     }
-    {
-      double xv[2] = {x, y}, tau, beta;
-      house(xv, 2, v, tau, beta);
-      int kq = hi - 1;
-      __syncthreads();
-      apply_left(S.T, m, v, tau, 2, kq, kq - 1, m, lane);
-      __syncthreads();
-      if (lane == 0) TT(kq + 1, kq - 1) = 0.0;
-      apply_right_tz(S.T, S.Z, m, v, tau, 2, kq, 0, hi + 1, lane);
-      __syncthreads();
+    // deferred off-window updates: columns hi+1..m-1 of T (left), rows
+    // 0..l-1 of T and all rows of Z (right), reflectors in sweep order
+    int ncol = m - 1 - hi, nrow = l;
+    for (int q = lane; q < ncol + nrow + m; q += NT) {
+      if (q < ncol) {
+        int c = hi + 1 + q;
+        for (int t = 0; t < nref; ++t)
+          if (rl[t].tau != 0.0) refl_col(S.T, m, rl[t], c);
+      } else if (q < ncol + nrow) {
+        int i = q - ncol;
+        for (int t = 0; t < nref; ++t)
+          if (rl[t].tau != 0.0) refl_row(S.T, m, rl[t], i);
+      } else {
+        int i = q - ncol - nrow;
+        for (int t = 0; t < nref; ++t)
+          if (rl[t].tau != 0.0) refl_row(S.Z, m, rl[t], i);
+      }
     }
+    __syncthreads();
   }
   sweeps = total;
   return true;
@@ -374,14 +458,15 @@ __device__ void hessenberg(Smem& S, int m, int lane, int lock) {
 }
 
 __device__ inline void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
+  // (ar + i ai) / (br + i bi), scaled by the larger of |br|, |bi| (Smith)
   if (fabs(br) >= fabs(bi)) {
-    double r = bi / br, d = br + bi * r;
-    cr = (ar + ai * r) / d;
-    ci = (ai - ar * r) / d;
+    double r = bi * rcp_nr(br), d = rcp_nr(br + bi * r);
+    cr = (ar + ai * r) * d;
+    ci = (ai - ar * r) * d;
   } else {
-    double r = br / bi, d = bi + br * r;
-    cr = (ar * r + ai) / d;
-    ci = (ai * r - ar) / d;
+    double r = br * rcp_nr(bi), d = rcp_nr(bi + br * r);
+    cr = (ar * r + ai) * d;
+    ci = (ai * r - ar) * d;
   }
 }
 
@@ -476,6 +561,7 @@ __global__ void k_ritz(RitzArgs R) {
   S.rank = (int*)(S.red + 4);
   S.sel = S.rank + m;
   S.cflag = S.sel + m;
+  S.refl = (Refl*)(((uintptr_t)(S.cflag + m) + 15) & ~(uintptr_t)15);
 
   for (int i = lane; i < m * m; i += NT) {
     int r = i % m, c = i / m;
@@ -484,9 +570,13 @@ __global__ void k_ritz(RitzArgs R) {
   }
   const double beta = R.H[m + (m + 1) * (m - 1)];
   __syncthreads();
+  long long t_ph[7];
+  t_ph[0] = clock64();
   hessenberg(S, m, lane, R.lock);
+  t_ph[1] = clock64();
   int sweeps = 0;
   bool ok = francis(S, m, lane, sweeps, R.lock);
+  t_ph[2] = clock64();
   __syncthreads();
   // eigenvalues in Schur order
   if (lane == 0) {
@@ -507,20 +597,22 @@ __global__ void k_ritz(RitzArgs R) {
   __syncthreads();
   // ranks by |lambda - s| = 1/|theta|, Im lambda > 0 first on ties
   // (lambda - s = 1/theta, so Im lambda has the sign of -Im theta)
+  // |lambda - s| = 1/|theta|: nearer means larger |theta|^2
   for (int i = lane; i < m; i += NT) {
-    double ti = 1.0 / hypot(S.wr[i], S.wi[i]);
+    double ti = S.wr[i] * S.wr[i] + S.wi[i] * S.wi[i];
     int ci = S.wi[i] < 0.0 ? 0 : (S.wi[i] == 0.0 ? 1 : 2);
     int rk = 0;
     for (int q = 0; q < m; ++q) {
-      double tq = 1.0 / hypot(S.wr[q], S.wi[q]);
+      double tq = S.wr[q] * S.wr[q] + S.wi[q] * S.wi[q];
       int cq = S.wi[q] < 0.0 ? 0 : (S.wi[q] == 0.0 ? 1 : 2);
-      if (tq < ti || (tq == ti && (cq < ci || (cq == ci && q < i)))) ++rk;
+      if (tq > ti || (tq == ti && (cq < ci || (cq == ci && q < i)))) ++rk;
     }
     S.rank[i] = rk;
   }
   __syncthreads();
   double tnorm = frob(S, m, lane);
   double smin = fmax(kEps * tnorm, 1e-300);
+  t_ph[3] = clock64();
   int nconv = 0;
   for (int i = lane; i < m; i += NT) S.cflag[i] = 0;
   __syncthreads();
@@ -528,6 +620,19 @@ __global__ void k_ritz(RitzArgs R) {
   for (int pos = 0; pos < m; ++pos) {
     int rk = S.rank[pos];
     if (rk >= R.neig) continue;
+    if (!R.final_pass && pos < R.lock) {
+      // locked: converged and decoupled, its estimate is zero
+      ++nconv;
+      if (lane == 0) {
+        double ir, ii;
+        cdiv(1.0, 0.0, S.wr[pos], S.wi[pos], ir, ii);
+        R.out->lam[2 * rk] = R.sigma + ir;
+        R.out->lam[2 * rk + 1] = ii;
+        R.out->est[rk] = 0.0;
+        S.cflag[pos] = 1;
+      }
+      continue;
+    }
     double lr = S.wr[pos], li = S.wi[pos];
     int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
     double lri = lr, lii = fabs(li);
@@ -566,6 +671,7 @@ __global__ void k_ritz(RitzArgs R) {
     }
     __syncthreads();
   }
+  t_ph[4] = clock64();
   if (lane == 0) {
     R.out->n_conv = nconv;
     R.out->fail = ok ? 0 : 1;
@@ -619,6 +725,7 @@ __global__ void k_ritz(RitzArgs R) {
   }
   __syncthreads();
   int k = ks;
+  t_ph[5] = clock64();
   // locking: converged blocks among the kept ones move to the front (after
   // the blocks locked earlier); their spike entries are dropped below, which
   // decouples them from the rest of the projected matrix
@@ -661,13 +768,16 @@ __global__ void k_ritz(RitzArgs R) {
   if (lane == 0) {
     R.out->k = k;
     R.out->n_lock = nl;
+    t_ph[6] = clock64();
+    for (int q = 0; q < 6; ++q) R.out->phase_cycles[q] = t_ph[q + 1] - t_ph[q];
   }
 }
 
 }  // namespace
 
 size_t ritz_smem(int m) {
-  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 3 * sizeof(int) * m;
+  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 3 * sizeof(int) * m + 16 +
+         sizeof(Refl) * (size_t)m;
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,

@@ -53,10 +53,14 @@ class Info(ctypes.Structure):
                 + [(n, ctypes.c_double) for n in
                    ("norm_K", "norm_M", "norm_C", "factor_ms", "eigs_ms", "fb_ms")]
                 + [("certified", ctypes.c_int64), ("cert_margin", ctypes.c_double),
-                   ("n_launches", ctypes.c_int64)])
+                   ("n_launches", ctypes.c_int64), ("ritz_ms", ctypes.c_double),
+                   ("ritz_phase_cycles", ctypes.c_double * 6)])
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d["ritz_phase_cycles"] = list(self.ritz_phase_cycles)
+        return d
+
 
 
 _lib = None
