@@ -96,15 +96,25 @@ class Clocks(threading.Thread):
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+def fb_source_hash():
+    """sha256 of the FB kernels' source text (the two sweep kernels and their
+    launcher in factor.cu): the committed DRAM counters stay valid while it
+    is unchanged."""
+    src = open(os.path.join(ROOT, "paper_2112_14064_gb300", "csrc", "factor.cu")).read()
+    a = src.rindex("\n\n", 0, src.index("k_fb_fwd(FBArgs"))
+    b = src.index("__global__ void k_gather")
+    c = src.index("void launch_fb(")
+    d = src.index("\n}\n", c) + 3
+    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()
+
+
 def fb_traffic(nnz_L):
     """DRAM bytes per FB solve from the committed ncu summary, if the FB
     kernels are unchanged since it was taken (source hash); else None."""
     path = os.path.join(ROOT, "profiles", "fb_solve_traffic.json")
-    src = os.path.join(ROOT, "paper_2112_14064_gb300", "csrc", "factor.cu")
     try:
         rec = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("factor_cu_sha256") != h or rec.get("nnz_L") != nnz_L:
+        if rec.get("fb_kernels_sha256") != fb_source_hash() or rec.get("nnz_L") != nnz_L:
             return None
         return rec["dram_bytes_per_solve"]
     except Exception:
@@ -151,7 +161,7 @@ def run_reference(args):
     from oracle.assemble import assemble
     for _ in range(args.warmup):
         assemble(tiny["ne"], tiny["p"], tiny["block"], workloads.sigma_e(tiny))
-    n_apply_full = int(os.environ.get("RIGAQEP_REF_APPLIES", "400"))
+    n_apply_full = int(os.environ.get("RIGAQEP_REF_APPLIES", "167"))   # the GPU arm's applies
     vals, secs, desc = [], [], ""
     for _ in range(args.steps):
         v, t, desc = oracle_sample(cfg, sig, v1, n_apply_full)
@@ -260,6 +270,26 @@ def run_ours(args):
         e2e_pairs += int(good.item())
     barrier()
 
+    # one more (untimed) step, synchronised after every stage, for the breakdown
+    stages = {}
+    barrier()
+    t0 = time.perf_counter()
+    pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d)
+    torch.cuda.synchronize()
+    stages["assemble_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    pr.analyze()
+    torch.cuda.synchronize()
+    stages["analyze_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    pr.eigs(neig, target, v1=v1_d, raise_on_noconv=False, **TARGET_KW)
+    torch.cuda.synchronize()
+    stages["factor_and_eigs_ms"] = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    pr.close()
+    torch.cuda.synchronize()
+    stages["release_ms"] = 1e3 * (time.perf_counter() - t0)
+
     # max over ranks
     t = torch.tensor([total_ms, float(sum(e2e_ms))], dtype=torch.float64, device=dev)
     pr_t = torch.tensor([float(pairs), float(e2e_pairs)], dtype=torch.float64, device=dev)
@@ -297,6 +327,7 @@ def run_ours(args):
         "solve": {"n_apply": inf["n_apply"], "n_restarts": inf["n_restarts"],
                   "certified": inf["certified"], "eigs_ms": inf["eigs_ms"],
                   "fb_ms": inf["fb_ms"], "ritz_ms": inf["ritz_ms"]},
+        "stages_host_ms": stages,
         "clocks": clocks.summary(),
         "e2e": {"value": 1e3 * all_e2e_pairs / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (cfg["ne"] ** 2) + 16 * N,

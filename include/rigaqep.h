@@ -123,10 +123,14 @@ typedef struct {
   double cert_margin;    /* lower bound on the distance of any other eigenvalue to the
                             target, minus the largest returned distance (>= 0 when certified) */
   int64_t n_launches;    /* kernels launched by the last eigs (including its factorisation) */
-  double ritz_ms;        /* device time of its Ritz/restart steps (before the final pass) */
+  double ritz_ms;        /* device time of its Ritz/restart steps */
   double ritz_phase_cycles[6];  /* SM cycles of those steps by phase: Hessenberg reduction,
                                    QR sweeps, eigenvalues and ranks, Ritz vectors and
                                    estimates, reordering, locking */
+  int64_t reused_candidates;  /* 1: the last eigs reused the converged candidates of the
+                                 previous in-region call (same factor, shift, ncand,
+                                 krylov_dim, tol, max_restarts, seed; seeded start) and
+                                 only selected and extracted for its target */
 } rigaqep_info;
 
 /* Create a handle and assemble K, M, C (original DOF order, one CSR
@@ -179,6 +183,51 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
                             const rigaqep_eigs_opts* opts, const double* v1,
                             double* lambda, double* X, double* eta,
                             int32_t* n_converged);
+/* In-region calls (shift_mode RIGAQEP_SHIFT_IN_REGION, v1 == NULL) that
+ * repeat the previous call's shift, ncand, krylov_dim, tol, max_restarts and
+ * seed on the same factor reuse its converged candidates and only select and
+ * extract the pairs for the new target and neig (info.reused_candidates = 1):
+ * the Krylov iteration does not depend on the target in that mode, so the
+ * result is the one a fresh call would return. */
+
+/* One eigensolve of a batch (rigaqep_batch_eigs).  Inputs: problem (index
+ * into the handle array), neig, target, opts (as for rigaqep_eigs; the start
+ * vector is always the seeded one), lambda/X/eta (device outputs laid out as
+ * for rigaqep_eigs, owned by the caller).  Outputs: n_converged, status (the
+ * rigaqep_status of this job), certified and reused_candidates (as in
+ * rigaqep_info after the job) and eigs_ms (its device time). */
+typedef struct {
+  int32_t problem;
+  int32_t neig;
+  double target;
+  rigaqep_eigs_opts opts;
+  double* lambda;
+  double* X;
+  double* eta;
+  int32_t n_converged;
+  int32_t status;
+  int32_t certified;
+  int32_t reused_candidates;
+  double eigs_ms;
+} rigaqep_batch_job;
+
+/* Many eigensolves of many independent QEPs (problems of uneven size, several
+ * targets each) in one call.  Every handle must be assembled on the calling
+ * thread's current device; handles not yet analysed are analysed here.  The
+ * jobs of one handle run in the order given, on that handle's stream, on one
+ * host worker thread; different handles run concurrently on up to nthreads
+ * workers (0 = one per handle, at most 16), largest N first.  Handles
+ * created on distinct streams overlap on the GPU; handles sharing a stream
+ * are correct but serialised.  Jobs with consecutive in-region solves of one
+ * handle share its Krylov iteration (see rigaqep_eigs).  A handle may appear
+ * in the array only once.  Returns RIGAQEP_OK when every job returned
+ * RIGAQEP_OK, else the status of the lowest-indexed failing job (its message
+ * in rigaqep_last_error); every job's own status is always written.  The call
+ * returns after all jobs have completed on the device.
+ * Defined by: no counterpart in the paper (which solves one problem at a
+ * time); each job is the solve of rigaqep_eigs. */
+rigaqep_status rigaqep_batch_eigs(rigaqep_problem* const* probs, int32_t nprob,
+                                  rigaqep_batch_job* jobs, int32_t njobs, int32_t nthreads);
 
 /* G[k, e] = d lambda_k / d sigma_e = -lambda_k x_e^T M_e x_e / x^T(2 lambda_k M + C) x
  * (unconjugated: the left eigenvector of the symmetric QEP is x itself).

@@ -123,7 +123,7 @@ __global__ void k_assemble_rows(Tables T, const int32_t* rowptr, const int32_t* 
   }
 }
 
-__global__ void k_permute(const int64_t* map, const double* a, const double* b, const double* c,
+__global__ void k_permute(const int32_t* map, const double* a, const double* b, const double* c,
                           double* an, double* bn, double* cn, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;

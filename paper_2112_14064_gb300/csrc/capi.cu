@@ -1,9 +1,14 @@
 // C-ABI of rigaqep: argument checks, state machine and error mapping.
 // Every entry point catches all C++ exceptions and returns a status code.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <utility>
 
 #include "internal.h"
 
@@ -49,14 +54,49 @@ void check_mesh(const rigaqep_mesh_desc* m) {
   need(m->leaf_min >= 0, RIGAQEP_ERR_ARG, "leaf_min must be >= 0");
 }
 
-template <class T>
-void copy_out(T* dst, const std::vector<T>& src) {
+template <class T, class A>
+void copy_out(T* dst, const std::vector<T, A>& src) {
   if (dst && !src.empty()) std::memcpy(dst, src.data(), src.size() * sizeof(T));
 }
 
 }  // namespace
 
 namespace rq {
+cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  int dev = 0;
+  RQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (!pools[dev]) {
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t pool;
+    RQ_CUDA(cudaMemPoolCreate(&pool, &pp));
+    // keep up to 8 GiB cached between calls; more is returned at synchronisation
+    uint64_t keep = 8ull << 30;
+    RQ_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
+void smem_at_least(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  RQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cur[{dev, kernel}];
+  if (bytes <= c) return;
+  RQ_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  c = bytes;
+}
+
 Problem::~Problem() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
@@ -81,6 +121,7 @@ rigaqep_status rigaqep_assemble(const rigaqep_mesh_desc* mesh, const double* sig
     try {
       rq::Problem& P = h->impl;
       P.stream = (cudaStream_t)cuda_stream;
+      rq::StreamScope scope(P.stream);
       P.plan.build_pattern(mesh->ne_x, mesh->p, mesh->block_x, mesh->n_quad, mesh->leaf_min);
       RQ_CUDA(cudaEventCreate(&P.ev0));
       RQ_CUDA(cudaEventCreate(&P.ev1));
@@ -116,6 +157,7 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
   return guard([&] {
     need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
     rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     rq::Plan& L = P.plan;
     cudaStream_t s = P.stream;
     L.build_symbolic();
@@ -162,6 +204,7 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
     P.info.max_front = L.max_front;
     P.analyzed = true;
     P.factored = false;
+    P.cand_valid = false;
   });
 }
 
@@ -169,10 +212,12 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
   return guard([&] {
     need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
     rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_factor");
     need(precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG, "only RIGAQEP_FP64 is available");
     need(sigma == sigma, RIGAQEP_ERR_ARG, "sigma is NaN");
     P.factored = false;
+    P.cand_valid = false;
     RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
     RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
     rq::launch_factor(P, sigma);
@@ -200,6 +245,7 @@ rigaqep_status rigaqep_solve(rigaqep_problem* prob, const double* b, double* x, 
     need(nrhs == 0 || (b != nullptr && x != nullptr), RIGAQEP_ERR_ARG, "NULL argument");
     need(transpose == 0 || transpose == 1, RIGAQEP_ERR_ARG, "transpose must be 0 or 1");
     rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     need(P.factored, RIGAQEP_ERR_STATE, "rigaqep_factor must run before rigaqep_solve");
     int64_t N = P.plan.N;
     // Q is symmetric, so the transposed solve uses the same factors and path.
@@ -221,6 +267,7 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
              n_converged != nullptr,
          RIGAQEP_ERR_ARG, "NULL argument");
     rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_eigs");
     rq::EigsParams E;
     E.neig = neig;
@@ -264,6 +311,7 @@ rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig, const d
          "NULL argument");
     need(neig >= 1, RIGAQEP_ERR_ARG, "neig must be >= 1");
     rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     need(neig <= 64, RIGAQEP_ERR_ARG, "neig must be <= 64");
     rq::grad_run(P, neig, lambda, X, G);
   });
@@ -283,6 +331,7 @@ rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, 
   return guard([&] {
     need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
     const rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     copy_out(rowptr, P.plan.rowptr);
     copy_out(col, P.plan.col);
     size_t nb = sizeof(double) * P.plan.nnz;
@@ -299,6 +348,7 @@ rigaqep_status rigaqep_export_symbolic(const rigaqep_problem* prob, int32_t* per
   return guard([&] {
     need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
     const rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
     need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze has not run");
     const rq::Plan& L = P.plan;
     copy_out(perm, L.perm);
@@ -314,6 +364,74 @@ rigaqep_status rigaqep_get_info(const rigaqep_problem* prob, rigaqep_info* info)
   return guard([&] {
     need(prob != nullptr && info != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
     *info = prob->impl.info;
+  });
+}
+
+rigaqep_status rigaqep_batch_eigs(rigaqep_problem* const* probs, int32_t nprob,
+                                  rigaqep_batch_job* jobs, int32_t njobs, int32_t nthreads) {
+  return guard([&] {
+    need(probs != nullptr && nprob >= 1, RIGAQEP_ERR_ARG, "need at least one handle");
+    need(njobs >= 0 && (njobs == 0 || jobs != nullptr), RIGAQEP_ERR_ARG, "jobs is NULL");
+    need(nthreads >= 0, RIGAQEP_ERR_ARG, "nthreads must be >= 0");
+    for (int32_t i = 0; i < nprob; ++i) {
+      need(probs[i] != nullptr, RIGAQEP_ERR_ARG, "NULL handle in the batch");
+      for (int32_t k = 0; k < i; ++k)
+        need(probs[k] != probs[i], RIGAQEP_ERR_ARG, "a handle appears twice in the batch");
+    }
+    std::vector<std::vector<int32_t>> per(nprob);
+    for (int32_t j = 0; j < njobs; ++j) {
+      need(jobs[j].problem >= 0 && jobs[j].problem < nprob, RIGAQEP_ERR_ARG,
+           "job refers to a handle outside the array");
+      per[jobs[j].problem].push_back(j);
+      jobs[j].status = RIGAQEP_ERR_STATE;   // overwritten when the job runs
+      jobs[j].n_converged = jobs[j].certified = jobs[j].reused_candidates = 0;
+      jobs[j].eigs_ms = 0.0;
+    }
+    // largest problems first (list scheduling of a ragged batch)
+    std::vector<int32_t> order;
+    for (int32_t i = 0; i < nprob; ++i)
+      if (!per[i].empty()) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return probs[a]->impl.plan.N > probs[b]->impl.plan.N;
+    });
+    int dev = 0;
+    RQ_CUDA(cudaGetDevice(&dev));
+    std::vector<std::string> msg(njobs);
+    std::atomic<int32_t> next{0};
+    auto worker = [&]() {
+      if (cudaSetDevice(dev) != cudaSuccess) return;   // jobs stay RIGAQEP_ERR_STATE
+      for (;;) {
+        int32_t q = next.fetch_add(1);
+        if (q >= (int32_t)order.size()) return;
+        rigaqep_problem* h = probs[order[q]];
+        rigaqep_status st = RIGAQEP_OK;
+        if (!h->impl.analyzed) st = rigaqep_analyze(h);
+        for (int32_t j : per[order[q]]) {
+          rigaqep_batch_job& J = jobs[j];
+          rigaqep_status js = st;
+          if (js == RIGAQEP_OK)
+            js = rigaqep_eigs(h, J.neig, J.target, &J.opts, nullptr, J.lambda, J.X, J.eta,
+                              &J.n_converged);
+          J.status = js;
+          if (js != RIGAQEP_OK) msg[j] = g_last_error;
+          const rigaqep_info& inf = h->impl.info;
+          J.certified = (int32_t)inf.certified;
+          J.reused_candidates = (int32_t)inf.reused_candidates;
+          J.eigs_ms = inf.eigs_ms;
+        }
+      }
+    };
+    int32_t nw = nthreads > 0 ? nthreads : 16;
+    nw = std::max<int32_t>(1, std::min<int32_t>(nw, (int32_t)order.size()));
+    std::vector<std::thread> th;
+    for (int32_t t = 1; t < nw; ++t) th.emplace_back(worker);
+    worker();
+    for (auto& t : th) t.join();
+    for (int32_t j = 0; j < njobs; ++j)
+      if (jobs[j].status != RIGAQEP_OK)
+        throw rq::Error((rigaqep_status)jobs[j].status,
+                        "batch job " + std::to_string(j) + ": " +
+                            (msg[j].empty() ? std::string("not run") : msg[j]));
   });
 }
 

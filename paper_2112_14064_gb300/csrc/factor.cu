@@ -410,9 +410,7 @@ __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, in
 }  // namespace
 
 void factor_configure(size_t smem_max) {
-  int v = (int)smem_max;
-  if (smem_max <= 48 * 1024) return;
-  RQ_CUDA(cudaFuncSetAttribute(k_fb_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  if (smem_max > 48 * 1024) smem_at_least((const void*)k_fb_fwd, smem_max);
 }
 
 void factor_plan(Problem& P) {
@@ -435,11 +433,9 @@ void factor_plan(Problem& P) {
   P.tile_items.upload(tiles, P.stream);
   P.Dval.alloc(L.N);
   size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
-  if (smem > 48 * 1024)
-    RQ_CUDA(cudaFuncSetAttribute(k_panel_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) smem_at_least((const void*)k_panel_rows, smem);
   if (sizeof(double) * (size_t)L.max_front > 48 * 1024)
-    RQ_CUDA(cudaFuncSetAttribute(k_pivot_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double) * L.max_front)));
+    smem_at_least((const void*)k_pivot_factor, sizeof(double) * L.max_front);
 }
 
 void launch_factor(Problem& P, double sigma) {

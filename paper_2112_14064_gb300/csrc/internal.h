@@ -29,27 +29,50 @@ struct Error : std::runtime_error {
                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
   } while (0)
 
+// Stream-ordered allocation.  Device buffers come from a library-owned memory
+// pool of the current device (cudaMallocFromPoolAsync / cudaFreeAsync), so
+// that allocating and releasing never synchronises the device: handles that
+// run on different streams (a batch) do not serialise each other, and
+// repeated solves reuse the pool's memory.  Allocations are ordered on the
+// stream of the entry point that is running (set by StreamScope); a buffer is
+// released on the stream it was allocated on, so that stream must outlive it.
+cudaMemPool_t device_pool();
+inline thread_local cudaStream_t t_stream = nullptr;
+struct StreamScope {
+  cudaStream_t old;
+  explicit StreamScope(cudaStream_t s) : old(t_stream) { t_stream = s; }
+  ~StreamScope() { t_stream = old; }
+};
+
+// Raises a kernel's dynamic shared memory limit to at least `bytes` (never
+// lowers it, so concurrent callers with different sizes cannot race a launch
+// below its own request).
+void smem_at_least(const void* kernel, size_t bytes);
+
 // Owning device buffer.
 template <class T>
 struct DBuf {
   T* p = nullptr;
   size_t n = 0;
+  cudaStream_t st = nullptr;
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
     p = nullptr;
     n = 0;
   }
   void alloc(size_t count) {
     release();
     if (count == 0) count = 1;
-    RQ_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    st = t_stream;
+    RQ_CUDA(cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), device_pool(), st));
     n = count;
   }
-  void upload(const std::vector<T>& h, cudaStream_t s) {
+  template <class A>
+  void upload(const std::vector<T, A>& h, cudaStream_t s) {
     alloc(h.size());
     if (!h.empty()) RQ_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   }
@@ -70,11 +93,22 @@ struct RitzOut {
   int32_t fail;         // QR did not converge
   int32_t sweeps;       // Francis double-shift sweeps of this step
   int32_t n_lock;       // leading Schur columns locked after this restart
-  int32_t pad2;
+  int32_t finished;     // eigenvectors written, no restart data
   double beta;
   long long phase_cycles[6];     // hessenberg, QR, eigenvalues+ranks, eigvecs, reorder, lock
   double lam[2 * kMaxKrylov];    // wanted lambdas (re, im), first neig
   double est[kMaxKrylov];        // Ritz estimates of the wanted pairs
+};
+
+struct EigsParams {
+  int neig;        // pairs returned
+  int ncand;       // pairs converged around the shift
+  double target;   // selection point
+  double shift;    // spectral shift (Q factorised there)
+  bool in_region;  // selection by target among the candidates
+  int m, max_restarts;
+  double tol;
+  uint64_t seed;
 };
 
 struct Problem {
@@ -93,7 +127,7 @@ struct Problem {
   DBuf<int> first_fn;           // first full function of each element
   // ND-ordered CSR and values
   DBuf<int32_t> rowptr_n, col_n, fpos;
-  DBuf<int64_t> slot_map;
+  DBuf<int32_t> slot_map;
   DBuf<double> Kn, Mn, Cn;
   // symbolic on device
   DBuf<int32_t> perm, iperm, sptr, upd_ptr, upd_idx, relmap, child_ptr, child_idx, lvl_nodes;
@@ -119,6 +153,11 @@ struct Problem {
   std::vector<int32_t> h_lvl_ptr;
   std::vector<int32_t> lvl_maxF;  // largest front order per level
   std::vector<int32_t> lvl_maxK;
+  // converged candidates of the last in-region eigensolve (seeded start),
+  // valid until the factor changes
+  bool cand_valid = false;
+  RitzOut cand{};
+  EigsParams cand_E{};
   ~Problem();
 };
 
@@ -138,16 +177,6 @@ void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n
                    int32_t ncol, cudaStream_t s);
 void launch_scatter(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);
 // Krylov pieces
-struct EigsParams {
-  int neig;        // pairs returned
-  int ncand;       // pairs converged around the shift
-  double target;   // selection point
-  double shift;    // spectral shift (Q factorised there)
-  bool in_region;  // selection by target among the candidates
-  int m, max_restarts;
-  double tol;
-  uint64_t seed;
-};
 void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
               double* eta, int* n_conv);
 void grad_run(Problem& P, int neig, const double* lambda, const double* X, double* G);

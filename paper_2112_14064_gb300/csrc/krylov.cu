@@ -569,10 +569,10 @@ struct Work {
   }
 };
 
-}  // namespace
-
-void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
-              double* eta, int* n_conv) {
+// Krylov-Schur iteration of the shift-and-invert operator until the ncand
+// wanted Ritz pairs converge (or max_restarts): leaves the basis in P.V, the
+// eigenvectors of H for the candidates in P.Y and the candidates in P.cand.
+void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   const int m = E.m, max_restarts = E.max_restarts;
@@ -606,7 +606,6 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaMemsetAsync(P.Vtmp.p, 0, sizeof(double) * ld * m, s));
   RQ_CUDA(cudaMemsetAsync(P.H.p, 0, sizeof(double) * (m + 1) * m, s));
   RQ_CUDA(cudaMemsetAsync(P.wvec.p, 0, sizeof(double) * Np, s));
-  RQ_CUDA(cudaEventRecord(P.ev0, s));
 
   const double* start = v1;
   if (!start) {
@@ -629,7 +628,9 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   for (int it = 0;; ++it) {
     for (int j = k; j < m; ++j) W.step(j);
     RQ_CUDA(cudaEventRecord(W.rz[0], s));
-    launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 0, lock, sigma, tol, s);
+    // the last allowed cycle always finishes; the others finish when converged
+    launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, it >= max_restarts ? 1 : 2,
+                lock, sigma, tol, s);
     RQ_CUDA(cudaEventRecord(W.rz[1], s));
     ++P.launches;
     RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
@@ -643,7 +644,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
     if (h_out.fail) throw Error(RIGAQEP_ERR_INTERNAL, "QR iteration on the projected matrix did not converge");
     qr_sweeps += h_out.sweeps;
     for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] += (double)h_out.phase_cycles[q];
-    if (h_out.n_conv >= nks || it >= max_restarts) break;
+    if (h_out.finished) break;
     k = h_out.k;
     lock = h_out.n_lock;
     // V[:, :k] = V[:, :m] Q ; V[:, k] = V[:, m] ; H = Hnew
@@ -658,12 +659,48 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
     RQ_CUDA(cudaMemcpyAsync(P.H.p, Hn.p, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToDevice, s));
     ++restarts;
   }
-  // final pass: eigenvectors of H for the candidate Ritz values
-  launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, 1, lock, sigma, tol, s);
-  ++P.launches;
-  RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
-  RQ_CUDA(cudaStreamSynchronize(s));
-  W.fb_collect();
+  P.cand = h_out;
+  P.cand_E = E;
+  P.cand_valid = v1 == nullptr;   // a seeded start vector can be reproduced
+  P.info.n_apply = W.n_apply;
+  P.info.n_restarts = restarts;
+  P.info.n_spmv = W.n_spmv;
+  P.info.n_vv = W.n_vv;
+  P.info.n_qr_sweeps = qr_sweeps;
+  P.info.fb_ms = W.fb_ms;
+  P.info.ritz_ms = W.ritz_ms;
+  P.info.reused_candidates = 0;
+}
+
+bool same_candidates(const EigsParams& a, const EigsParams& b) {
+  return a.in_region && b.in_region && a.shift == b.shift && a.ncand == b.ncand && a.m == b.m &&
+         a.max_restarts == b.max_restarts && a.tol == b.tol && a.seed == b.seed;
+}
+
+}  // namespace
+
+void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
+              double* eta, int* n_conv) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int m = E.m, nks = E.ncand;
+  const double tol = E.tol;
+  const int64_t N = L.N, ld = 2 * ((L.N + 31) / 32 * 32);
+  RQ_CUDA(cudaEventRecord(P.ev0, s));
+  // in-region calls that differ only in the target (and neig) share the
+  // converged candidates of the previous call on the same factor
+  if (P.cand_valid && v1 == nullptr && same_candidates(P.cand_E, E)) {
+    P.info.n_apply = P.info.n_restarts = P.info.n_spmv = P.info.n_vv = 0;
+    P.info.n_qr_sweeps = 0;
+    P.info.fb_ms = P.info.ritz_ms = 0.0;
+    for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] = 0.0;
+    P.info.reused_candidates = 1;
+  } else {
+    P.cand_valid = false;
+    krylov_schur(P, E, v1);
+  }
+  const RitzOut& h_out = P.cand;
+  // the last Ritz step wrote the eigenvectors of H for the candidate values
   // selection of the neig candidates nearest the target (Im > 0 first on
   // ties), and the certificate that no other eigenvalue is nearer
   const int neig = E.neig;
@@ -715,7 +752,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaMemcpyAsync(lambda, lam_sel.data(), sizeof(double) * 2 * neig, cudaMemcpyHostToDevice, s));
   {
     size_t smem = sizeof(double) * 2 * (size_t)m * neig;
-    RQ_CUDA(cudaFuncSetAttribute(k_eigvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_at_least((const void*)k_eigvec, smem);
     k_eigvec<<<(unsigned)((N + 127) / 128), 128, smem, s>>>(P.V.p, ld, m, Ysel.p, neig, P.perm.p, X, N);
     RQ_CUDA(cudaGetLastError());
   }
@@ -738,13 +775,6 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   float ms = 0.f;
   RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
   P.info.eigs_ms = ms;
-  P.info.n_apply = W.n_apply;
-  P.info.n_restarts = restarts;
-  P.info.n_spmv = W.n_spmv;
-  P.info.n_vv = W.n_vv;
-  P.info.n_qr_sweeps = qr_sweeps;
-  P.info.fb_ms = W.fb_ms;
-  P.info.ritz_ms = W.ritz_ms;
   P.info.n_launches = P.launches;
   *n_conv = sel_conv;
 }

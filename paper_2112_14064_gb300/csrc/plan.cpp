@@ -17,9 +17,28 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <stdexcept>
+#include <thread>
 
 namespace rq {
+namespace {
+// f(lo, hi) over [0, n) in contiguous chunks on up to 16 host threads (one
+// chunk when n is small); f must not throw.
+template <class F>
+void parallel_ranges(int64_t n, int64_t min_chunk, F f) {
+  int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  int64_t T = std::min<int64_t>(std::min<int64_t>(hw, 16), std::max<int64_t>(1, n / min_chunk));
+  if (T <= 1) {
+    f(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 1; t < T; ++t) th.emplace_back(f, n * t / T, n * (t + 1) / T);
+  f(int64_t(0), n / T);
+  for (auto& x : th) x.join();
+}
+}  // namespace
 
 void Space1D::build(int ne_, int p_, int block_) {
   ne = ne_; p = p_; block = block_;
@@ -83,13 +102,14 @@ void Plan::build_pattern(int ne_, int p_, int block_, int nq_, int leaf_min_) {
     }
   nnz = total;
   col.resize(nnz);
-  for (int j = 0; j < n1; ++j)
-    for (int i = 0; i < n1; ++i) {
-      int64_t r = i + (int64_t)n1 * j;
-      int64_t o = rowptr[r];
-      for (int bj : cpl[j])
-        for (int bi : cpl[i]) col[o++] = (int32_t)(bi + n1 * bj);
-    }
+  parallel_ranges(n1, 64, [&](int64_t j0, int64_t j1) {
+    for (int64_t j = j0; j < j1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        int64_t o = rowptr[i + (int64_t)n1 * j];
+        for (int bj : cpl[j])
+          for (int bi : cpl[i]) col[o++] = (int32_t)(bi + n1 * bj);
+      }
+  });
 }
 
 namespace {
@@ -234,7 +254,11 @@ void Plan::build_symbolic() {
     }
   }
 
-  // ND-ordered CSR and the front row of every lower-triangle entry
+  // ND-ordered CSR and the front row of every lower-triangle entry.  Rows are
+  // independent, so they are split over host threads.  Within one row the
+  // original columns run bj-major, bi-minor; inside one box the ND order is
+  // y-major, x-minor, so the entries of each owning box are already ascending
+  // and a stable bucketing by owner (ascending) yields the sorted row.
   rowptr_n.assign(N + 1, 0);
   for (int64_t j = 0; j < N; ++j) {
     int32_t o = perm[j];
@@ -242,30 +266,47 @@ void Plan::build_symbolic() {
   }
   col_n.resize(nnz);
   slot_map.resize(nnz);
-  fpos.assign(nnz, -1);
-  std::vector<std::pair<int32_t, int32_t>> tmp;
-  for (int64_t j = 0; j < N; ++j) {
-    int32_t o = perm[j];
-    tmp.clear();
-    for (int32_t q = rowptr[o]; q < rowptr[o + 1]; ++q) tmp.push_back({iperm[col[q]], q});
-    std::sort(tmp.begin(), tmp.end());
-    int s = owner[j];
-    int a = sptr[s], e = sptr[s + 1], k = e - a;
-    const int32_t* ps = upd_idx.data() + upd_ptr[s];
-    int pu = upd_ptr[s + 1] - upd_ptr[s];
-    int w = 0;
-    int64_t base = rowptr_n[j];
-    for (size_t t = 0; t < tmp.size(); ++t) {
-      int32_t i = tmp[t].first;
-      col_n[base + t] = i;
-      slot_map[base + t] = tmp[t].second;
-      if (i < j) continue;
-      if (i < e) { fpos[base + t] = i - a; continue; }
-      while (w < pu && ps[w] < i) ++w;
-      if (w >= pu || ps[w] != i) throw std::logic_error("matrix entry outside the front");
-      fpos[base + t] = k + w;
+  fpos.resize(nnz);
+  std::atomic<int> bad{0};
+  parallel_ranges(N, 4096, [&](int64_t j0, int64_t j1) {
+    std::vector<int32_t> owners;
+    for (int64_t j = j0; j < j1; ++j) {
+      int32_t o = perm[j];
+      int32_t q0 = rowptr[o], q1 = rowptr[o + 1];
+      owners.clear();
+      for (int32_t q = q0; q < q1; ++q) {
+        int32_t ow = owner[iperm[col[q]]];
+        if (std::find(owners.begin(), owners.end(), ow) == owners.end()) owners.push_back(ow);
+      }
+      std::sort(owners.begin(), owners.end());
+      int s = owner[j];
+      int a = sptr[s], e = sptr[s + 1], k = e - a;
+      const int32_t* ps = upd_idx.data() + upd_ptr[s];
+      const int32_t* pe = upd_idx.data() + upd_ptr[s + 1];
+      int64_t t = rowptr_n[j];
+      for (int32_t ow : owners)
+        for (int32_t q = q0; q < q1; ++q) {
+          int32_t i = iperm[col[q]];
+          if (owner[i] != ow) continue;
+          if (t > rowptr_n[j] && col_n[t - 1] >= i) bad = 1;
+          col_n[t] = i;
+          slot_map[t] = q;
+          fpos[t] = -1;
+          if (i >= j) {
+            if (i < e) {
+              fpos[t] = i - a;
+            } else {
+              const int32_t* w = std::lower_bound(ps, pe, i);
+              if (w == pe || *w != i) bad = 2;
+              else fpos[t] = k + (int32_t)(w - ps);
+            }
+          }
+          ++t;
+        }
     }
-  }
+  });
+  if (bad == 1) throw std::logic_error("ND-ordered row is not ascending");
+  if (bad == 2) throw std::logic_error("matrix entry outside the front");
 
   // level sets
   lvl_ptr.assign(nlevels + 1, 0);

@@ -3,10 +3,29 @@
 // No CUDA dependency: everything here is plain C++ on int32/int64.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace rq {
+
+// Allocator that leaves elements default-initialised (uninitialised for
+// integers) on resize, so that arrays of nnz entries are first touched by the
+// host threads that fill them instead of by one sequential memset.
+template <class T>
+struct NoInit : std::allocator<T> {
+  template <class U>
+  struct rebind { using other = NoInit<U>; };
+  NoInit() = default;
+  template <class U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept { ::new ((void*)p) U; }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+using ivec = std::vector<int32_t, NoInit<int32_t>>;
 
 struct Space1D {
   int ne = 0, p = 0, block = 0;
@@ -27,7 +46,8 @@ struct Plan {
   int n1 = 0;
   int64_t N = 0, nnz = 0;
   // original-order CSR pattern (columns ascending)
-  std::vector<int32_t> rowptr, col;
+  std::vector<int32_t> rowptr;
+  ivec col;
   // ordering and supernodes
   std::vector<int32_t> perm, iperm, sptr, owner;
   int nsuper = 0;
@@ -35,9 +55,10 @@ struct Plan {
   int nlevels = 0;
   std::vector<int32_t> child_ptr, child_idx;  // children of each supernode
   // ND-ordered CSR (columns ascending) and the map to original slots
-  std::vector<int32_t> rowptr_n, col_n;
-  std::vector<int64_t> slot_map;   // slot_map[new slot] = original slot
-  std::vector<int32_t> fpos;       // front row of a new-order slot, -1 if col < row
+  std::vector<int32_t> rowptr_n;
+  ivec col_n;
+  ivec slot_map;                   // slot_map[new slot] = original slot (nnz < 2^31)
+  ivec fpos;                       // front row of a new-order slot, -1 if col < row
   // front storage layout
   std::vector<int64_t> loff;       // factor panel of s: (k+u) x k, column-major
   std::vector<int64_t> uoff;       // update block of s: u x u, column-major

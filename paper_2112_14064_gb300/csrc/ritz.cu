@@ -37,9 +37,9 @@ struct RitzArgs {
   const double* H;   // (m+1) x m, column-major, ld = m+1
   double* Hnew;      // restart matrix, same layout
   double* Q;         // m x k kept Schur vectors, ld = m
-  double* Y;         // final: m x neig eigenvectors of H_m (re, im interleaved)
+  double* Y;         // when finishing: m x neig eigenvectors of H_m (re, im interleaved)
   RitzOut* out;
-  int m, neig, kwant, final_pass, lock;
+  int m, neig, kwant, final_pass, lock;   // final_pass: 0 restart, 1 finish, 2 finish if converged
   double sigma, tol;
 };
 
@@ -613,62 +613,71 @@ __global__ void k_ritz(RitzArgs R) {
   double tnorm = frob(S, m, lane);
   double smin = fmax(kEps * tnorm, 1e-300);
   t_ph[3] = clock64();
-  int nconv = 0;
   for (int i = lane; i < m; i += NT) S.cflag[i] = 0;
   __syncthreads();
-  // wanted pairs: eigenvectors, estimates and (final pass) outputs
-  for (int pos = 0; pos < m; ++pos) {
-    int rk = S.rank[pos];
-    if (rk >= R.neig) continue;
-    if (!R.final_pass && pos < R.lock) {
-      // locked: converged and decoupled, its estimate is zero
-      ++nconv;
+  // wanted pairs: eigenvectors, estimates and (when finishing) the outputs.
+  // final_pass 1 always finishes; 2 finishes when every wanted pair has
+  // converged (the restart is then not needed), else restarts.
+  bool fin = R.final_pass == 1;
+  int nconv = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    nconv = 0;
+    for (int pos = 0; pos < m; ++pos) {
+      int rk = S.rank[pos];
+      if (rk >= R.neig) continue;
+      if (!fin && pos < R.lock) {
+        // locked: converged and decoupled, its estimate is zero
+        ++nconv;
+        if (lane == 0) {
+          double ir, ii;
+          cdiv(1.0, 0.0, S.wr[pos], S.wi[pos], ir, ii);
+          R.out->lam[2 * rk] = R.sigma + ir;
+          R.out->lam[2 * rk + 1] = ii;
+          R.out->est[rk] = 0.0;
+          S.cflag[pos] = 1;
+        }
+        continue;
+      }
+      double lr = S.wr[pos], li = S.wi[pos];
+      int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
+      double lri = lr, lii = fabs(li);
+      trevc_one(S, m, jstart, lri, lii, smin, lane);
+      // y_H = Z y ; estimate uses the last row; norm of y equals norm of Z y
+      double nrm = 0.0;
+      for (int i = lane; i < m; i += NT) nrm += S.yr[i] * S.yr[i] + S.yi[i] * S.yi[i];
+      nrm = sqrt(block_sum(nrm, S.red, lane));
+      double lastr = 0.0, lasti = 0.0;
+      for (int l = lane; l < m; l += NT) {
+        lastr += ZZ(m - 1, l) * S.yr[l];
+        lasti += ZZ(m - 1, l) * S.yi[l];
+      }
+      lastr = block_sum(lastr, S.red, lane);
+      lasti = block_sum(lasti, S.red, lane);
+      double theta = hypot(lr, li);
+      double est = fabs(beta) * hypot(lastr, lasti) / (nrm * theta);
+      if (est <= R.tol) ++nconv;
+      if (lane == 0) S.cflag[pos] = est <= R.tol ? 1 : 0;
       if (lane == 0) {
+        // lambda = s + 1/theta
         double ir, ii;
-        cdiv(1.0, 0.0, S.wr[pos], S.wi[pos], ir, ii);
+        cdiv(1.0, 0.0, lr, li, ir, ii);
         R.out->lam[2 * rk] = R.sigma + ir;
         R.out->lam[2 * rk + 1] = ii;
-        R.out->est[rk] = 0.0;
-        S.cflag[pos] = 1;
+        R.out->est[rk] = est;
       }
-      continue;
-    }
-    double lr = S.wr[pos], li = S.wi[pos];
-    int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
-    double lri = lr, lii = fabs(li);
-    trevc_one(S, m, jstart, lri, lii, smin, lane);
-    // y_H = Z y ; estimate uses the last row; norm of y equals norm of Z y
-    double nrm = 0.0;
-    for (int i = lane; i < m; i += NT) nrm += S.yr[i] * S.yr[i] + S.yi[i] * S.yi[i];
-    nrm = sqrt(block_sum(nrm, S.red, lane));
-    double lastr = 0.0, lasti = 0.0;
-    for (int l = lane; l < m; l += NT) {
-      lastr += ZZ(m - 1, l) * S.yr[l];
-      lasti += ZZ(m - 1, l) * S.yi[l];
-    }
-    lastr = block_sum(lastr, S.red, lane);
-    lasti = block_sum(lasti, S.red, lane);
-    double theta = hypot(lr, li);
-    double est = fabs(beta) * hypot(lastr, lasti) / (nrm * theta);
-    if (est <= R.tol) ++nconv;
-    if (lane == 0) S.cflag[pos] = est <= R.tol ? 1 : 0;
-    if (lane == 0) {
-      // lambda = s + 1/theta
-      double ir, ii;
-      cdiv(1.0, 0.0, lr, li, ir, ii);
-      R.out->lam[2 * rk] = R.sigma + ir;
-      R.out->lam[2 * rk + 1] = ii;
-      R.out->est[rk] = est;
-    }
-    if (R.final_pass) {
-      double sgn = (li < 0.0) ? -1.0 : 1.0;
-      for (int r = lane; r < m; r += NT) {
-        double ar = 0.0, ai = 0.0;
-        for (int l = 0; l < m; ++l) { ar += ZZ(r, l) * S.yr[l]; ai += ZZ(r, l) * S.yi[l]; }
-        R.Y[2 * (r + m * rk)] = ar / nrm;
-        R.Y[2 * (r + m * rk) + 1] = sgn * ai / nrm;
+      if (fin) {
+        double sgn = (li < 0.0) ? -1.0 : 1.0;
+        for (int r = lane; r < m; r += NT) {
+          double ar = 0.0, ai = 0.0;
+          for (int l = 0; l < m; ++l) { ar += ZZ(r, l) * S.yr[l]; ai += ZZ(r, l) * S.yi[l]; }
+          R.Y[2 * (r + m * rk)] = ar / nrm;
+          R.Y[2 * (r + m * rk) + 1] = sgn * ai / nrm;
+        }
       }
+      __syncthreads();
     }
+    if (fin || R.final_pass != 2 || nconv < R.neig) break;
+    fin = true;
     __syncthreads();
   }
   t_ph[4] = clock64();
@@ -677,8 +686,13 @@ __global__ void k_ritz(RitzArgs R) {
     R.out->fail = ok ? 0 : 1;
     R.out->beta = beta;
     R.out->sweeps = sweeps;
+    R.out->finished = fin ? 1 : 0;
+    if (fin) {
+      for (int q = 0; q < 4; ++q) R.out->phase_cycles[q] = t_ph[q + 1] - t_ph[q];
+      R.out->phase_cycles[4] = R.out->phase_cycles[5] = 0;
+    }
   }
-  if (R.final_pass) return;
+  if (fin) return;
   // select the kwant nearest, never splitting a conjugate pair
   // locked blocks always stay (they sit at the top with a zero spike)
   for (int i = lane; i < m; i += NT) S.sel[i] = (S.rank[i] < R.kwant || i < R.lock) ? 1 : 0;
@@ -784,7 +798,7 @@ void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* o
                  int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s) {
   RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol};
   size_t smem = ritz_smem(m);
-  RQ_CUDA(cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  smem_at_least((const void*)k_ritz, smem);
   k_ritz<<<1, NT, smem, s>>>(R);
   RQ_CUDA(cudaGetLastError());
 }

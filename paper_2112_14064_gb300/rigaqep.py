@@ -24,7 +24,7 @@ EXPORTS = [
     "rigaqep_assemble", "rigaqep_analyze", "rigaqep_factor", "rigaqep_solve", "rigaqep_eigs",
     "rigaqep_grad_damping", "rigaqep_grad_damping_noalloc", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
-    "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy",
+    "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
 ]
 
 
@@ -46,6 +46,14 @@ class EigsOpts(ctypes.Structure):
                 ("shift", ctypes.c_double), ("ncand", ctypes.c_int32)]
 
 
+class BatchJob(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_int32), ("neig", ctypes.c_int32), ("target", ctypes.c_double),
+                ("opts", EigsOpts), ("lam", ctypes.c_void_p), ("X", ctypes.c_void_p),
+                ("eta", ctypes.c_void_p), ("n_converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("certified", ctypes.c_int32),
+                ("reused_candidates", ctypes.c_int32), ("eigs_ms", ctypes.c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_int64) for n in
                  ("n1", "N", "nnz", "nsuper", "nlevels", "nnz_L", "factor_flops", "max_front",
@@ -54,7 +62,8 @@ class Info(ctypes.Structure):
                    ("norm_K", "norm_M", "norm_C", "factor_ms", "eigs_ms", "fb_ms")]
                 + [("certified", ctypes.c_int64), ("cert_margin", ctypes.c_double),
                    ("n_launches", ctypes.c_int64), ("ritz_ms", ctypes.c_double),
-                   ("ritz_phase_cycles", ctypes.c_double * 6)])
+                   ("ritz_phase_cycles", ctypes.c_double * 6),
+                   ("reused_candidates", ctypes.c_int64)])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}
@@ -91,6 +100,7 @@ def load():
         "rigaqep_symbolic_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)],
         "rigaqep_symbolic_sizes": [P, ctypes.POINTER(I64)],
         "rigaqep_symbolic_export": [P, P, P, P, P, P, P, P, P],
+        "rigaqep_batch_eigs": [ctypes.POINTER(P), I32, ctypes.POINTER(BatchJob), I32, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -214,14 +224,11 @@ class Problem:
         nearest sigma returned; see info()["certified"])."""
         torch = self._torch
         dev = torch.device("cuda", torch.cuda.current_device())
-        nc = neig if ncand is None else ncand
-        m = m or min(96, 2 * nc + 20)
         lam = torch.empty((neig, 2), dtype=torch.float64, device=dev)
         X = torch.empty((neig, self.N, 2), dtype=torch.float64, device=dev)
         eta = torch.empty(neig, dtype=torch.float64, device=dev)
         nconv = ctypes.c_int32(0)
-        opts = EigsOpts(m, max_restarts, tol, seed, 0, 0 if shift is None else 1,
-                        0.0 if shift is None else float(shift), nc)
+        opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand)
         if v1 is not None:
             v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
         st = self.lib.rigaqep_eigs(self._h, neig, float(sigma), ctypes.byref(opts), _ptr(v1),
@@ -280,3 +287,51 @@ class Problem:
         _check(self.lib.rigaqep_export_symbolic(self._h, None, None, None, None,
                                                 _ptr(out["upd_idx"]), None))
         return out
+
+
+def eigs_opts(neig, m=None, tol=1e-10, max_restarts=1000, seed=1, shift=None, ncand=None):
+    """rigaqep_eigs_opts with the defaults of Problem.eigs."""
+    nc = neig if ncand is None else ncand
+    m = m or min(96, 2 * nc + 20)
+    return EigsOpts(m, max_restarts, tol, seed, 0, 0 if shift is None else 1,
+                    0.0 if shift is None else float(shift), nc)
+
+
+def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):
+    """Run many eigensolves over many Problems in one rigaqep_batch_eigs call.
+
+    jobs: list of dicts with keys problem (index into problems), neig, target
+    and optionally m, tol, max_restarts, seed, shift, ncand (as Problem.eigs;
+    the start vector is the seeded one).  Returns one dict per job: lam
+    (neig,) complex, X (neig, N) complex, eta (neig,), n_converged, status,
+    certified, reused_candidates, eigs_ms.  Problems on distinct streams run
+    concurrently."""
+    import torch
+    lib = load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    handles = (ctypes.c_void_p * len(problems))(*[pr._h.value for pr in problems])
+    arr = (BatchJob * len(jobs))()
+    outs = []
+    for j, d in enumerate(jobs):
+        pr = problems[d["problem"]]
+        neig = d["neig"]
+        lam = torch.empty((neig, 2), dtype=torch.float64, device=dev)
+        X = torch.empty((neig, pr.N, 2), dtype=torch.float64, device=dev)
+        eta = torch.empty(neig, dtype=torch.float64, device=dev)
+        opts = eigs_opts(neig, **{k: d[k] for k in ("m", "tol", "max_restarts", "seed", "shift",
+                                                   "ncand") if k in d})
+        arr[j] = BatchJob(d["problem"], neig, float(d["target"]), opts, lam.data_ptr(),
+                          X.data_ptr(), eta.data_ptr(), 0, 0, 0, 0, 0.0)
+        outs.append((lam, X, eta))
+    # the handles' streams must see the caller's pending work (e.g. output allocation)
+    torch.cuda.current_stream().synchronize()
+    code = lib.rigaqep_batch_eigs(handles, len(problems), arr, len(jobs), int(nthreads))
+    if code != 0 and raise_on_error:
+        _check(code)
+    res = []
+    for j, (lam, X, eta) in enumerate(outs):
+        J = arr[j]
+        res.append(dict(lam=torch.view_as_complex(lam), X=torch.view_as_complex(X), eta=eta,
+                        n_converged=J.n_converged, status=J.status, certified=J.certified,
+                        reused_candidates=J.reused_candidates, eigs_ms=J.eigs_ms))
+    return res
