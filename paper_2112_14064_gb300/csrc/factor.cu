@@ -280,32 +280,17 @@ FBArgs fb_args(Problem& P) {
                 (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
-// Butterfly transpose-reduction of 32 per-lane accumulators: afterwards lane
-// l holds the warp-wide sum of acc[l] in acc[0] (31 additions per lane).
-__device__ __forceinline__ double warp_transpose_reduce(double (&acc)[32], int lane) {
-#pragma unroll
-  for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
-    bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < len / 2; ++i) {
-      double send = up ? acc[i] : acc[i + len / 2];
-      double keep = up ? acc[i + len / 2] : acc[i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return acc[0];
-}
-
 // Forward sweep, one work item = up to 32 consecutive rows of one front's
 // panel P = [inv(L11); W], W = L21 inv(L11):
 //   xg  = x_s + (children's update vectors at the pivot rows)
 //   z   = inv(L11) xg           -> zbuf = D^{-1} z   (pivot rows)
 //   y_s = (children at the update rows) - W xg      (update rows)
-// Lanes run down the rows (coalesced columns), the four warps split the
-// columns; pivot rows only use the columns up to the chunk's last row.
-__global__ void __launch_bounds__(128) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
+// Lanes run down the rows (coalesced columns), the eight warps split the
+// columns and keep eight loads in flight each; pivot rows only use the
+// columns up to the chunk's last row.
+__global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
   extern __shared__ double xg[];
-  __shared__ double part[4][32];
+  __shared__ double part[8][32];
   __shared__ double yadd[32];
   int4 it = A.fwd_items[item_begin + blockIdx.x];
   int s = it.x, r0 = it.y, nr = it.z;
@@ -331,22 +316,32 @@ __global__ void __launch_bounds__(128) k_fb_fwd(FBArgs A, int item_begin, const 
   }
   int row = r0 + min(lane, nr - 1);
   int cend = r0 + nr <= k ? r0 + nr : k;     // triangle: columns <= last pivot row
-  int q = (cend + 3) / 4;
+  int q = (cend + 7) / 8;
   int cb = warp * q, ce = min(cend, cb + q);
   const double* pr = P + row;
-  double s0 = 0.0, s1 = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int c = cb;
-  for (; c + 1 < ce; c += 2) {
-    s0 += pr[F * c] * xg[c];
-    s1 += pr[F * (c + 1)] * xg[c + 1];
+  for (; c + 7 < ce; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = pr[F * (c + t)];
+    s0 += v[0] * xg[c];
+    s1 += v[1] * xg[c + 1];
+    s2 += v[2] * xg[c + 2];
+    s3 += v[3] * xg[c + 3];
+    s0 += v[4] * xg[c + 4];
+    s1 += v[5] * xg[c + 5];
+    s2 += v[6] * xg[c + 6];
+    s3 += v[7] * xg[c + 7];
   }
-  if (c < ce) s0 += pr[F * c] * xg[c];
-  part[warp][lane] = s0 + s1;
+  for (; c < ce; ++c) s0 += pr[F * c] * xg[c];
+  part[warp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (threadIdx.x < nr) {
     int i = r0 + threadIdx.x;
-    double dot = (part[0][threadIdx.x] + part[1][threadIdx.x]) +
-                 (part[2][threadIdx.x] + part[3][threadIdx.x]);
+    const int l = threadIdx.x;
+    double dot = ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l])) +
+                 ((part[4][l] + part[5][l]) + (part[6][l] + part[7][l]));
     if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
     else A.yvec[A.upd_ptr[s] + (i - k)] = yadd[threadIdx.x] - dot;
   }
@@ -355,12 +350,17 @@ __global__ void __launch_bounds__(128) k_fb_fwd(FBArgs A, int item_begin, const 
 // Backward sweep, one work item = up to 32 pivot columns c of one front:
 //   x_c = sum_{i >= c, i < k} inv(L11)[i, c] zbuf_i - sum_i W[i, c] x_struct(i)
 // i.e. x_s = inv(L11)^T (D^{-1} z - L21^T x_struct) with W = L21 inv(L11).
-// Warps split the rows, lanes run down them (coalesced), butterfly to one
-// column per lane.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
-__global__ void __launch_bounds__(256) k_fb_bwd(FBArgs A, int item_begin, double* x,
+// Each warp takes 32-row blocks of the item's columns: it loads the 32 x 32
+// block with coalesced column reads (lanes down the rows) into shared
+// memory, then each lane forms its own column's dot product from the staged
+// block, so no lane-transpose reduction is needed; the four warps' partial
+// sums are added at the end.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
+__global__ void __launch_bounds__(128) k_fb_bwd(FBArgs A, int item_begin, double* x,
                                                 double sigma, const double* vu, double* ru,
                                                 double* rl) {
-  __shared__ double red[8][32];
+  __shared__ double tile[4][32][33];
+  __shared__ double gs[4][32];
+  __shared__ double red[4][32];
   int4 it = A.bwd_items[item_begin + blockIdx.x];
   int s = it.x, c0 = it.y, nc = it.z;
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
@@ -369,26 +369,30 @@ __global__ void __launch_bounds__(256) k_fb_bwd(FBArgs A, int item_begin, double
   const double* P = A.Lval + A.loff[s] + F * c0;
   const int32_t* st = A.upd_idx + A.upd_ptr[s];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc[32];
-#pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-  for (int64_t i = c0 + threadIdx.x; i < F; i += blockDim.x) {
-    double g = i < k ? A.zbuf[a + i] : -x[st[i - k]];
-    const double* pr = P + i;
+  double acc = 0.0;
+  for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 128) {
+    int64_t i = r0 + lane;
+    int64_t ic = i < F ? i : F - 1;
+    double g = 0.0;
+    if (i < F) g = i < k ? A.zbuf[a + i] : -x[st[i - k]];
+    const double* pr = P + ic;
     double v[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
+    gs[warp][lane] = g;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) acc[q] += v[q] * g;
+    for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[q];
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+    __syncwarp();
   }
-  double v = warp_transpose_reduce(acc, lane);
-  red[warp][lane] = v;
+  red[warp][lane] = acc;
   __syncthreads();
   if (threadIdx.x < nc) {
-    double sum = 0.0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) sum += red[w][threadIdx.x];
-    int cc = a + c0 + threadIdx.x;
+    const int l = threadIdx.x;
+    double sum = (red[0][l] + red[1][l]) + (red[2][l] + red[3][l]);
+    int cc = a + c0 + l;
     x[cc] = sum;
     if (ru) {
       ru[cc] = -sum;
@@ -500,13 +504,13 @@ void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* r
   FBArgs A = fb_args(P);
   for (int l = 0; l < L.nlevels; ++l) {
     int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
-    k_fb_fwd<<<ic, 128, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
+    k_fb_fwd<<<ic, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
-    k_fb_bwd<<<ic, 256, 0, s>>>(A, ib, xn, sigma, vu, ru, rl);
+    k_fb_bwd<<<ic, 128, 0, s>>>(A, ib, xn, sigma, vu, ru, rl);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }
