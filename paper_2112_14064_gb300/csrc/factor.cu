@@ -258,25 +258,24 @@ __global__ void __launch_bounds__(256) k_schur_tile(FrontArgs A, const int4* ite
   if (i + 1 < u && j + 1 < u) U[(i + 1) + (int64_t)u * (j + 1)] -= c11;
 }
 
+// FB work item: 12 int32, loaded as three int4:
+//   {front, first row/column, count <= 32, first pivot a,
+//    k, u, gather base (forward) / upd_ptr (backward), upd_ptr (forward),
+//    panel offset low, panel offset high, children's entries (forward), 0}
 struct FBArgs {
-  const int32_t* sptr;
-  const int32_t* upd_ptr;
   const int32_t* upd_idx;
-  const int32_t* relmap;
-  const int32_t* child_ptr;
-  const int32_t* child_idx;
-  const int64_t* loff;
+  const int32_t* gptr;     // per front position: its children's update entries (CSR)
+  const int32_t* gsrc;     // yvec slots of those entries, in child order
   const double* Lval;
   const double* Dinv;
   double* yvec;    // update vectors of the forward sweep (one per supernode)
   double* zbuf;    // forward result D^{-1} inv(L11) x of the pivot rows
-  const int4* fwd_items;  // (front, first panel row, rows <= 32, 0)
-  const int4* bwd_items;  // (front, first pivot column, columns <= 32, 0)
+  const int4* fwd_items;
+  const int4* bwd_items;
 };
 
 FBArgs fb_args(Problem& P) {
-  return FBArgs{P.sptr.p, P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p, P.child_idx.p,
-                P.loff.p, P.Lval.p, P.Dinv.p, P.yvec.p, P.zbuf.p,
+  return FBArgs{P.upd_idx.p, P.fb_gptr.p, P.fb_gsrc.p, P.Lval.p, P.Dinv.p, P.yvec.p, P.zbuf.p,
                 (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
@@ -292,37 +291,56 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
   extern __shared__ double xg[];
   __shared__ double part[8][32];
   __shared__ double yadd[32];
-  int4 it = A.fwd_items[item_begin + blockIdx.x];
-  int s = it.x, r0 = it.y, nr = it.z;
-  int a = A.sptr[s], k = A.sptr[s + 1] - a;
-  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
+  const int4* ip = A.fwd_items + 3 * (int64_t)(item_begin + blockIdx.x);
+  int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
+  int r0 = i0.y, nr = i0.z, a = i0.w;
+  int k = i1.x, u = i1.y, gbase = i1.z;
   int64_t F = k + u;
-  const double* P = A.Lval + A.loff[s];
+  const double* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32));
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < k; t += blockDim.x) xg[t] = xin[a + t];
-  if (threadIdx.x < 32) yadd[threadIdx.x] = 0.0;
-  __syncthreads();
-  for (int ci = A.child_ptr[s]; ci < A.child_ptr[s + 1]; ++ci) {
-    int c = A.child_idx[ci];
-    int uc = A.upd_ptr[c + 1] - A.upd_ptr[c];
-    const int32_t* rm = A.relmap + A.upd_ptr[c];
-    const double* yc = A.yvec + A.upd_ptr[c];
-    for (int r = threadIdx.x; r < uc; r += blockDim.x) {
-      int pos = rm[r];
-      if (pos < k) xg[pos] += yc[r];
-      else if (pos >= r0 && pos < r0 + nr) yadd[pos - r0] += yc[r];
-    }
-    __syncthreads();
-  }
   int row = r0 + min(lane, nr - 1);
   int cend = r0 + nr <= k ? r0 + nr : k;     // triangle: columns <= last pivot row
   int q = (cend + 7) / 8;
   int cb = warp * q, ce = min(cend, cb + q);
   const double* pr = P + row;
+  // the first eight panel entries do not depend on the gathered vector
+  double v[8];
+  const bool pre = cb + 7 < ce;
+  if (pre) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = pr[F * (cb + t)];
+  }
+  // right-hand side plus the children's update vectors, summed per front
+  // position in child order (deterministic, no write conflicts)
+  const bool kids = i2.z != 0;   // the front has children's update entries
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    double acc = xin[a + t];
+    if (kids)
+      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g) acc += A.yvec[A.gsrc[g]];
+    xg[t] = acc;
+  }
+  if (threadIdx.x < nr && r0 + (int)threadIdx.x >= k) {
+    int pos = r0 + threadIdx.x;
+    double acc = 0.0;
+    if (kids)
+      for (int g = A.gptr[gbase + pos]; g < A.gptr[gbase + pos + 1]; ++g) acc += A.yvec[A.gsrc[g]];
+    yadd[threadIdx.x] = acc;
+  }
+  __syncthreads();
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int c = cb;
+  if (pre) {
+    s0 += v[0] * xg[c];
+    s1 += v[1] * xg[c + 1];
+    s2 += v[2] * xg[c + 2];
+    s3 += v[3] * xg[c + 3];
+    s0 += v[4] * xg[c + 4];
+    s1 += v[5] * xg[c + 5];
+    s2 += v[6] * xg[c + 6];
+    s3 += v[7] * xg[c + 7];
+    c += 8;
+  }
   for (; c + 7 < ce; c += 8) {
-    double v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = pr[F * (c + t)];
     s0 += v[0] * xg[c];
@@ -343,7 +361,7 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
     double dot = ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l])) +
                  ((part[4][l] + part[5][l]) + (part[6][l] + part[7][l]));
     if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
-    else A.yvec[A.upd_ptr[s] + (i - k)] = yadd[threadIdx.x] - dot;
+    else A.yvec[i1.w + (i - k)] = yadd[threadIdx.x] - dot;
   }
 }
 
@@ -353,24 +371,27 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
 // Each warp takes 32-row blocks of the item's columns: it loads the 32 x 32
 // block with coalesced column reads (lanes down the rows) into shared
 // memory, then each lane forms its own column's dot product from the staged
-// block, so no lane-transpose reduction is needed; the four warps' partial
-// sums are added at the end.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
-__global__ void __launch_bounds__(128) k_fb_bwd(FBArgs A, int item_begin, double* x,
-                                                double sigma, const double* vu, double* ru,
-                                                double* rl) {
-  __shared__ double tile[4][32][33];
-  __shared__ double gs[4][32];
-  __shared__ double red[4][32];
-  int4 it = A.bwd_items[item_begin + blockIdx.x];
-  int s = it.x, c0 = it.y, nc = it.z;
-  int a = A.sptr[s], k = A.sptr[s + 1] - a;
-  int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
+// block, so no lane-transpose reduction is needed; the warps' partial sums
+// are added at the end in warp order.  Levels with few items (the top of the
+// tree, long panels) use eight warps per item, the others four.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, int item_begin, double* x,
+                                                   double sigma, const double* vu, double* ru,
+                                                   double* rl) {
+  extern __shared__ double bwd_smem[];
+  double(*tile)[32][33] = reinterpret_cast<double(*)[32][33]>(bwd_smem);
+  __shared__ double gs[NW][32];
+  __shared__ double red[NW][32];
+  const int4* ip = A.bwd_items + 3 * (int64_t)(item_begin + blockIdx.x);
+  int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
+  int c0 = i0.y, nc = i0.z, a = i0.w;
+  int k = i1.x, u = i1.y;
   int64_t F = k + u;
-  const double* P = A.Lval + A.loff[s] + F * c0;
-  const int32_t* st = A.upd_idx + A.upd_ptr[s];
+  const double* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32)) + F * c0;
+  const int32_t* st = A.upd_idx + i1.z;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double acc = 0.0;
-  for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 128) {
+  for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 32 * NW) {
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
     double g = 0.0;
@@ -391,7 +412,9 @@ __global__ void __launch_bounds__(128) k_fb_bwd(FBArgs A, int item_begin, double
   __syncthreads();
   if (threadIdx.x < nc) {
     const int l = threadIdx.x;
-    double sum = (red[0][l] + red[1][l]) + (red[2][l] + red[3][l]);
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sum += red[w][l];
     int cc = a + c0 + l;
     x[cc] = sum;
     if (ru) {
@@ -413,7 +436,11 @@ __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, in
 
 }  // namespace
 
+constexpr size_t kBwdSmem4 = sizeof(double) * 4 * 32 * 33;
+constexpr size_t kBwdSmem8 = sizeof(double) * 8 * 32 * 33;
+
 void factor_configure(size_t smem_max) {
+  smem_at_least((const void*)k_fb_bwd<8>, kBwdSmem8);
   if (smem_max > 48 * 1024) smem_at_least((const void*)k_fb_fwd, smem_max);
 }
 
@@ -479,21 +506,46 @@ void launch_factor(Problem& P, double sigma) {
 
 void fb_plan(Problem& P) {
   Plan& L = P.plan;
+  // per-front-position gather lists of the children's update entries
+  std::vector<int32_t> gbase(L.nsuper + 1, 0);
+  for (int s = 0; s < L.nsuper; ++s)
+    gbase[s + 1] = gbase[s] + (L.sptr[s + 1] - L.sptr[s]) + (L.upd_ptr[s + 1] - L.upd_ptr[s]);
+  std::vector<int32_t> cnt(gbase[L.nsuper] + 1, 0);
+  for (int s = 0; s < L.nsuper; ++s)
+    for (int ci = L.child_ptr[s]; ci < L.child_ptr[s + 1]; ++ci) {
+      int c = L.child_idx[ci];
+      for (int q = L.upd_ptr[c]; q < L.upd_ptr[c + 1]; ++q) ++cnt[gbase[s] + L.relmap[q] + 1];
+    }
+  std::vector<int32_t> gptr(cnt.size(), 0);
+  for (size_t i = 1; i < cnt.size(); ++i) gptr[i] = gptr[i - 1] + cnt[i];
+  std::vector<int32_t> gsrc(gptr.back()), fill(gptr.begin(), gptr.end() - 1);
+  for (int s = 0; s < L.nsuper; ++s)
+    for (int ci = L.child_ptr[s]; ci < L.child_ptr[s + 1]; ++ci) {   // child order
+      int c = L.child_idx[ci];
+      for (int q = L.upd_ptr[c]; q < L.upd_ptr[c + 1]; ++q) gsrc[fill[gbase[s] + L.relmap[q]]++] = q;
+    }
   std::vector<int32_t> fwd, bwd;
   P.fwd_lvl.assign(L.nlevels + 1, 0);
   P.bwd_lvl.assign(L.nlevels + 1, 0);
   for (int l = 0; l < L.nlevels; ++l) {
     for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
       int s = L.lvl_nodes[q];
-      int k = L.sptr[s + 1] - L.sptr[s], u = L.upd_ptr[s + 1] - L.upd_ptr[s];
-      for (int r = 0; r < k + u; r += 32) fwd.insert(fwd.end(), {s, r, std::min(32, k + u - r), 0});
-      for (int c = 0; c < k; c += 32) bwd.insert(bwd.end(), {s, c, std::min(32, k - c), 0});
+      int a = L.sptr[s], k = L.sptr[s + 1] - a, u = L.upd_ptr[s + 1] - L.upd_ptr[s];
+      int32_t lo = (int32_t)(uint32_t)(L.loff[s] & 0xffffffffll), hi = (int32_t)(L.loff[s] >> 32);
+      int nkid = gptr[gbase[s + 1]] - gptr[gbase[s]];   // children's update entries
+      for (int r = 0; r < k + u; r += 32)
+        fwd.insert(fwd.end(), {s, r, std::min(32, k + u - r), a, k, u, gbase[s], L.upd_ptr[s],
+                               lo, hi, nkid, 0});
+      for (int c = 0; c < k; c += 32)
+        bwd.insert(bwd.end(), {s, c, std::min(32, k - c), a, k, u, L.upd_ptr[s], 0, lo, hi, 0, 0});
     }
-    P.fwd_lvl[l + 1] = (int32_t)(fwd.size() / 4);
-    P.bwd_lvl[l + 1] = (int32_t)(bwd.size() / 4);
+    P.fwd_lvl[l + 1] = (int32_t)(fwd.size() / 12);
+    P.bwd_lvl[l + 1] = (int32_t)(bwd.size() / 12);
   }
   P.fwd_items.upload(fwd, P.stream);
   P.bwd_items.upload(bwd, P.stream);
+  P.fb_gptr.upload(gptr, P.stream);
+  P.fb_gsrc.upload(gsrc, P.stream);
   P.zbuf.alloc(L.N);
   P.wbuf.alloc(1);
 }
@@ -510,7 +562,10 @@ void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* r
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
-    k_fb_bwd<<<ic, 128, 0, s>>>(A, ib, xn, sigma, vu, ru, rl);
+    if (ic < 2 * 152)
+      k_fb_bwd<8><<<ic, 256, kBwdSmem8, s>>>(A, ib, xn, sigma, vu, ru, rl);
+    else
+      k_fb_bwd<4><<<ic, 128, kBwdSmem4, s>>>(A, ib, xn, sigma, vu, ru, rl);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }

@@ -139,7 +139,8 @@ struct Problem {
   DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
   DBuf<double> xwork;           // FB work vector (N)
   DBuf<double> zbuf, wbuf;      // FB intermediates (N)
-  DBuf<int32_t> fwd_items, bwd_items;   // FB work items (front, start, count, 0)
+  DBuf<int32_t> fwd_items, bwd_items;   // FB work items (12 int32 each, see factor.cu)
+  DBuf<int32_t> fb_gptr, fb_gsrc;       // per front position: children's update entries
   std::vector<int32_t> fwd_lvl, bwd_lvl;  // work items of each level
   // Krylov workspace
   DBuf<double> V, Vtmp, H, part, hvec, wvec, yop, scal, Y;

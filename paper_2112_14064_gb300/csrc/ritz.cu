@@ -338,16 +338,38 @@ __device__ __forceinline__ void refl_row(double* A, int m, const Refl& r, int i)
   if (r.n == 3) a[2 * m] -= s * r.u2;
 }
 
-// Real Schur form of the Hessenberg T by Francis double-shift sweeps.  During
-// a sweep on the active window [l, hi] only window entries are updated (the
-// bulge chase reads nothing else); the sweep's reflectors are kept and, after
-// it, applied to the columns right of the window, the rows above it and Z,
-// one column or row per thread in order, without barriers.
+// Real Schur form of the Hessenberg T by Francis double-shift sweeps.
+//
+// A sweep on the active window [l, hi] chases a chain of up to kBulges
+// double-shift bulges (one per warp), each kBulgeGap rows behind the one
+// ahead of it; with at most one bulge the sweep is the classical one.
+// Bulge b uses the eigenvalues of the 2 x 2 diagonal block ending at row
+// hi - 2b as its shift pair (b = 0: the Wilkinson-type Francis shift, with
+// the usual exceptional shift every 11th sweep).  Each round every bulge
+// moves one position:
+//   warp b: build its reflector and apply it from the right (columns
+//           kq..kq+2, window rows up to kq+3);
+//   barrier;
+//   warp b: apply it from the left (rows kq..kq+2, window columns from kq-1);
+//   barrier.
+// With the bulges at least four rows apart the right-hand updates of one
+// round touch disjoint columns and the left-hand updates disjoint rows; the
+// only overlap between bulges (the rows of a bulge behind against the
+// columns of the bulge ahead) sees the ahead bulge's right-hand update before
+// the behind bulge's left-hand update, as in the one-bulge-at-a-time order.
+// A left and a right application of one reflector commute.  Only window
+// entries are updated during the sweep; its reflectors are kept and, after
+// it, applied in (round, bulge) order to the columns right of the window,
+// the rows above it and Z, one column or row per thread, without barriers.
+constexpr int kBulges = NT / 32;
+constexpr int kBulgeGap = 4;
+
 __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
   double tn = frob(S, m, lane);
   if (tn == 0.0) tn = 1.0;
   int hi = m - 1, its = 0, total = 0;
   Refl* rl = S.refl;
+  const int warp = lane >> 5, wl = lane & 31;
   while (hi >= lock) {
     int l = hi;
     while (l > lock) {
@@ -368,47 +390,63 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
     }
     if (++total > 40 * m) { sweeps = total; return false; }
     ++its;
-    double sh, th;
-    if (its % 11 == 10) {
-      double w = fabs(TT(hi, hi - 1)) + fabs(TT(hi - 1, hi - 2));
-      double z0 = TT(hi, hi) + 0.75 * w;
-      sh = 2.0 * z0;
-      th = z0 * z0 + 0.4375 * w * w;
-    } else {
-      sh = TT(hi - 1, hi - 1) + TT(hi, hi);
-      th = TT(hi - 1, hi - 1) * TT(hi, hi) - TT(hi - 1, hi) * TT(hi, hi - 1);
+    const int nw = hi - l + 1;
+    const int nb = nw >= kBulges * (kBulgeGap + 2) ? kBulges : 1;
+    // this warp's shift pair (sum sh, product th)
+    double sh = 0.0, th = 0.0;
+    if (warp < nb) {
+      int p = hi - 1 - 2 * warp;
+      if (warp == 0 && its % 11 == 10) {
+        double w = fabs(TT(hi, hi - 1)) + fabs(TT(hi - 1, hi - 2));
+        double z0 = TT(hi, hi) + 0.75 * w;
+        sh = 2.0 * z0;
+        th = z0 * z0 + 0.4375 * w * w;
+      } else {
+        sh = TT(p, p) + TT(p + 1, p + 1);
+        th = TT(p, p) * TT(p + 1, p + 1) - TT(p, p + 1) * TT(p + 1, p);
+      }
     }
-    double x = TT(l, l) * TT(l, l) + TT(l, l + 1) * TT(l + 1, l) - sh * TT(l, l) + th;
-    double y = TT(l + 1, l) * (TT(l, l) + TT(l + 1, l + 1) - sh);
-    double z = TT(l + 1, l) * TT(l + 2, l + 1);
-    int nref = 0;
-    for (int kq = l; kq <= hi - 1; ++kq) {
-      int n = kq <= hi - 2 ? 3 : 2;
+    const int rounds = (hi - 1 - l) + kBulgeGap * (nb - 1) + 1;
+    for (int t = 0; t < rounds; ++t) {
+      const int kq = l + t - kBulgeGap * warp;
+      const bool act = warp < nb && kq >= l && kq <= hi - 1;
       Refl r;
-      make_refl(x, y, z, n, r);
+      r.tau = 0.0;
+      r.n = 0;
       r.pos = kq;
-      if (lane == 0) rl[nref] = r;
-      ++nref;
-      int c0 = kq > l ? kq - 1 : l;
-      __syncthreads();
-      if (r.tau != 0.0)
-        for (int c = c0 + lane; c <= hi; c += NT) refl_col(S.T, m, r, c);
-      __syncthreads();
-      if (kq > l && lane == 0) {
-        TT(kq + 1, kq - 1) = 0.0;
-        if (n == 3) TT(kq + 2, kq - 1) = 0.0;
+      if (act) {
+        int n = kq <= hi - 2 ? 3 : 2;
+        double x, y, z;
+        if (kq == l) {
+          x = TT(l, l) * TT(l, l) + TT(l, l + 1) * TT(l + 1, l) - sh * TT(l, l) + th;
+          y = TT(l + 1, l) * (TT(l, l) + TT(l + 1, l + 1) - sh);
+          z = n == 3 ? TT(l + 1, l) * TT(l + 2, l + 1) : 0.0;
+        } else {
+          x = TT(kq, kq - 1);
+          y = TT(kq + 1, kq - 1);
+          z = n == 3 ? TT(kq + 2, kq - 1) : 0.0;
+        }
+        make_refl(x, y, z, n, r);
+        r.pos = kq;
+        if (r.tau != 0.0)
+          for (int i = l + wl; i <= min(kq + 3, hi); i += 32) refl_row(S.T, m, r, i);
       }
-      if (r.tau != 0.0)
-        for (int i = l + lane; i <= min(kq + 3, hi); i += NT) refl_row(S.T, m, r, i);
+      if (warp < nb && wl == 0) rl[t * nb + warp] = r;
       __syncthreads();
-      if (n == 3) {
-        x = TT(kq + 1, kq);
-        y = TT(kq + 2, kq);
-        if (kq < hi - 2) z = TT(kq + 3, kq);
+      if (act) {
+        int c0 = kq > l ? kq - 1 : l;
+        if (r.tau != 0.0)
+          for (int c = c0 + wl; c <= hi; c += 32) refl_col(S.T, m, r, c);
+        if (kq > l && wl == 0) {
+          TT(kq + 1, kq - 1) = 0.0;
+          if (r.n == 3) TT(kq + 2, kq - 1) = 0.0;
+        }
       }
+      __syncthreads();
     }
     // deferred off-window updates: columns hi+1..m-1 of T (left), rows
-    // 0..l-1 of T and all rows of Z (right), reflectors in sweep order
+    // 0..l-1 of T and all rows of Z (right), reflectors in (round, bulge) order
+    const int nref = rounds * nb;
     int ncol = m - 1 - hi, nrow = l;
     for (int q = lane; q < ncol + nrow + m; q += NT) {
       if (q < ncol) {
@@ -791,7 +829,7 @@ __global__ void k_ritz(RitzArgs R) {
 
 size_t ritz_smem(int m) {
   return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 3 * sizeof(int) * m + 16 +
-         sizeof(Refl) * (size_t)m;
+         sizeof(Refl) * (size_t)(NT / 32) * (size_t)(m + 16);
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
