@@ -303,13 +303,14 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
   int q = (cend + 7) / 8;
   int cb = warp * q, ce = min(cend, cb + q);
   const double* pr = P + row;
-  // the first eight panel entries do not depend on the gathered vector
+  // Columns in chunks of eight with unconditional loads (clamped to a valid
+  // column, weight zero past the warp's range) so that a chunk's loads are all
+  // in flight together; the first chunk does not depend on the gathered
+  // vector and is issued before the gather.
+  const int cl = max(cend - 1, 0);
   double v[8];
-  const bool pre = cb + 7 < ce;
-  if (pre) {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = pr[F * (cb + t)];
-  }
+  for (int t = 0; t < 8; ++t) v[t] = pr[F * min(cb + t, cl)];
   // right-hand side plus the children's update vectors, summed per front
   // position in child order (deterministic, no write conflicts)
   const bool kids = i2.z != 0;   // the front has children's update entries
@@ -328,31 +329,23 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
   }
   __syncthreads();
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = cb;
-  if (pre) {
-    s0 += v[0] * xg[c];
-    s1 += v[1] * xg[c + 1];
-    s2 += v[2] * xg[c + 2];
-    s3 += v[3] * xg[c + 3];
-    s0 += v[4] * xg[c + 4];
-    s1 += v[5] * xg[c + 5];
-    s2 += v[6] * xg[c + 6];
-    s3 += v[7] * xg[c + 7];
-    c += 8;
-  }
-  for (; c + 7 < ce; c += 8) {
+  for (int c = cb;;) {
+    double w[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = pr[F * (c + t)];
-    s0 += v[0] * xg[c];
-    s1 += v[1] * xg[c + 1];
-    s2 += v[2] * xg[c + 2];
-    s3 += v[3] * xg[c + 3];
-    s0 += v[4] * xg[c + 4];
-    s1 += v[5] * xg[c + 5];
-    s2 += v[6] * xg[c + 6];
-    s3 += v[7] * xg[c + 7];
+    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : 0.0;
+    s0 += v[0] * w[0];
+    s1 += v[1] * w[1];
+    s2 += v[2] * w[2];
+    s3 += v[3] * w[3];
+    s0 += v[4] * w[4];
+    s1 += v[5] * w[5];
+    s2 += v[6] * w[6];
+    s3 += v[7] * w[7];
+    c += 8;
+    if (c >= ce) break;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = pr[F * min(c + t, cl)];
   }
-  for (; c < ce; ++c) s0 += pr[F * c] * xg[c];
   part[warp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (threadIdx.x < nr) {

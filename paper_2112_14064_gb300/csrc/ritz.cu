@@ -52,10 +52,6 @@ struct Smem {
   int* rank;
   int* sel;
   int* cflag;  // converged flag of each Schur position
-  double* yr;  // one eigenvector of T (re, im)
-  double* yi;
-  double* sr;  // running right-hand sides of the back-substitution
-  double* si;
   double* red; // 4 partial sums
   struct Refl* refl;  // reflectors of the current QR sweep
 };
@@ -343,9 +339,8 @@ __device__ __forceinline__ void refl_row(double* A, int m, const Refl& r, int i)
 // A sweep on the active window [l, hi] chases a chain of up to kBulges
 // double-shift bulges (one per warp), each kBulgeGap rows behind the one
 // ahead of it; with at most one bulge the sweep is the classical one.
-// Bulge b uses the eigenvalues of the 2 x 2 diagonal block ending at row
-// hi - 2b as its shift pair (b = 0: the Wilkinson-type Francis shift, with
-// the usual exceptional shift every 11th sweep).  Each round every bulge
+// The bulges use the Francis shift pair of the trailing 2 x 2 block (bulge 0
+// with the usual exceptional shift every 11th sweep).  Each round every bulge
 // moves one position:
 //   warp b: build its reflector and apply it from the right (columns
 //           kq..kq+2, window rows up to kq+3);
@@ -392,10 +387,13 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
     ++its;
     const int nw = hi - l + 1;
     const int nb = nw >= kBulges * (kBulgeGap + 2) ? kBulges : 1;
-    // this warp's shift pair (sum sh, product th)
+    // this warp's shift pair (sum sh, product th): every bulge takes the
+    // eigenvalues of the trailing 2 x 2 block (measured: fewer sweeps and
+    // less time than shifts from the 2 x 2 blocks above it); bulge 0 takes
+    // the exceptional shift every 11th sweep
     double sh = 0.0, th = 0.0;
     if (warp < nb) {
-      int p = hi - 1 - 2 * warp;
+      int p = hi - 1;
       if (warp == 0 && its % 11 == 10) {
         double w = fabs(TT(hi, hi - 1)) + fabs(TT(hi - 1, hi - 2));
         double z0 = TT(hi, hi) + 0.75 * w;
@@ -508,77 +506,95 @@ __device__ inline void cdiv(double ar, double ai, double br, double bi, double& 
   }
 }
 
-// Eigenvector y of quasi-triangular T for the eigenvalue at diagonal
-// position j (wr, wi; wi > 0 means j is the first row of its 2x2 block).
-__device__ void trevc_one(Smem& S, int m, int j, double lr, double li, double smin, int lane) {
-  bool pair = (li != 0.0);
+// Per-warp buffers of the eigenvector back substitution (6 vectors of m).
+struct WarpVec {
+  double *yr, *yi, *sr, *si, *dr, *di;
+};
+
+// Eigenvector y of the quasi-triangular T for the eigenvalue at diagonal
+// position j (lr, li; li > 0 means j starts its 2 x 2 block), computed by one
+// warp: y = e_j (or the block's null vector) above which rows are solved
+// from the bottom up, (T_ii - lambda) y_i = -sum_{c>i} T_ic y_c, with the reciprocals of the
+// diagonal 1 x 1 shifts T_ii - lambda and of the 2 x 2 block determinants
+// formed first, in parallel over the lanes, so that the sequential chain per
+// row is a complex multiply and a residual update.
+__device__ void trevc_warp(const double* T, int m, int j, double lr, double li, double smin,
+                           const double* wi, int wl, WarpVec& B) {
+  const bool pair = (li != 0.0);
+  for (int i = wl; i < m; i += 32) { B.yr[i] = 0.0; B.yi[i] = 0.0; }
+  __syncwarp();
   int top;
-  for (int i = lane; i < m; i += NT) { S.yr[i] = 0.0; S.yi[i] = 0.0; }
-  __syncthreads();
   if (!pair) {
-    if (lane == 0) S.yr[j] = 1.0;
+    if (wl == 0) B.yr[j] = 1.0;
     top = j;
   } else {
-    // (T_blk - lambda I) [y_j; y_j+1] = 0 with T_blk = [[a, b], [e, a]]
-    if (lane == 0) {
-      S.yr[j] = TT(j, j + 1);
-      S.yi[j] = 0.0;
-      S.yr[j + 1] = lr - TT(j, j);
-      S.yi[j + 1] = li;
+    if (wl == 0) {
+      B.yr[j] = T[j + m * (j + 1)];
+      B.yi[j] = 0.0;
+      B.yr[j + 1] = lr - T[j + m * j];
+      B.yi[j + 1] = li;
     }
     top = j + 1;
   }
-  __syncthreads();
-  for (int r = lane; r < m; r += NT) {
+  __syncwarp();
+  for (int r = wl; r < j; r += 32) {
     double ar = 0.0, ai = 0.0;
-    if (r < j)
-      for (int l = j; l <= top; ++l) { ar -= TT(r, l) * S.yr[l]; ai -= TT(r, l) * S.yi[l]; }
-    S.sr[r] = ar;
-    S.si[r] = ai;
+    for (int l = j; l <= top; ++l) { ar -= T[r + m * l] * B.yr[l]; ai -= T[r + m * l] * B.yi[l]; }
+    B.sr[r] = ar;
+    B.si[r] = ai;
+    // reciprocal of the shifted diagonal (1 x 1 rows) or of the determinant of
+    // the shifted 2 x 2 block (stored at its first row)
+    if (wi[r] == 0.0) {
+      double dr = T[r + m * r] - lr, di = -li;
+      if (fabs(dr) + fabs(di) < smin) dr = smin;
+      cdiv(1.0, 0.0, dr, di, B.dr[r], B.di[r]);
+    } else if (wi[r] > 0.0) {
+      int i0 = r, i1 = r + 1;
+      double ar2 = T[i0 + m * i0] - lr, ai2 = -li, br = T[i0 + m * i1], cr = T[i1 + m * i0];
+      double dr = T[i1 + m * i1] - lr, di = -li;
+      double detr = ar2 * dr - ai2 * di - br * cr, deti = ar2 * di + ai2 * dr;
+      if (fabs(detr) + fabs(deti) < smin) detr = smin;
+      cdiv(1.0, 0.0, detr, deti, B.dr[r], B.di[r]);
+    }
   }
-  __syncthreads();
+  __syncwarp();
   int i = j - 1;
   while (i >= 0) {
-    bool blk2 = (i >= 1 && TT(i, i - 1) != 0.0);
-    if (!blk2) {
-      double dr = TT(i, i) - lr, di = -li;
-      if (fabs(dr) + fabs(di) < smin) dr = smin;
-      double yr, yi;
-      cdiv(S.sr[i], S.si[i], dr, di, yr, yi);
-      __syncthreads();
-      if (lane == 0) { S.yr[i] = yr; S.yi[i] = yi; }
-      for (int r = lane; r < i; r += NT) {
-        S.sr[r] -= TT(r, i) * yr;
-        S.si[r] -= TT(r, i) * yi;
+    if (wi[i] >= 0.0) {   // 1 x 1 row
+      double s_r = B.sr[i], s_i = B.si[i], pr = B.dr[i], pi = B.di[i];
+      double yr = s_r * pr - s_i * pi, yi = s_r * pi + s_i * pr;
+      if (wl == 0) { B.yr[i] = yr; B.yi[i] = yi; }
+      for (int r = wl; r < i; r += 32) {
+        B.sr[r] -= T[r + m * i] * yr;
+        B.si[r] -= T[r + m * i] * yi;
       }
-      __syncthreads();
+      __syncwarp();
       i -= 1;
-    } else {
-      // [[a - l, b], [c, d - l]] [y0; y1] = [s0; s1]  (complex)
+    } else {              // rows i-1, i form a 2 x 2 block
       int i0 = i - 1;
-      double ar = TT(i0, i0) - lr, ai = -li, br = TT(i0, i), cr = TT(i, i0);
-      double dr = TT(i, i) - lr, di = -li;
-      double s0r = S.sr[i0], s0i = S.si[i0], s1r = S.sr[i], s1i = S.si[i];
-      // det = (a-l)(d-l) - b c
-      double detr = ar * dr - ai * di - br * cr, deti = ar * di + ai * dr;
-      if (fabs(detr) + fabs(deti) < smin) detr = smin;
-      // y0 = (s0 (d-l) - b s1) / det ; y1 = ((a-l) s1 - c s0) / det
+      double ar = T[i0 + m * i0] - lr, ai = -li, br = T[i0 + m * i], cr = T[i + m * i0];
+      double dr = T[i + m * i] - lr, di = -li;
+      double s0r = B.sr[i0], s0i = B.si[i0], s1r = B.sr[i], s1i = B.si[i];
       double n0r = s0r * dr - s0i * di - br * s1r, n0i = s0r * di + s0i * dr - br * s1i;
       double n1r = ar * s1r - ai * s1i - cr * s0r, n1i = ar * s1i + ai * s1r - cr * s0i;
-      double y0r, y0i, y1r, y1i;
-      cdiv(n0r, n0i, detr, deti, y0r, y0i);
-      cdiv(n1r, n1i, detr, deti, y1r, y1i);
-      __syncthreads();
-      if (lane == 0) { S.yr[i0] = y0r; S.yi[i0] = y0i; S.yr[i] = y1r; S.yi[i] = y1i; }
-      for (int r = lane; r < i0; r += NT) {
-        S.sr[r] -= TT(r, i0) * y0r + TT(r, i) * y1r;
-        S.si[r] -= TT(r, i0) * y0i + TT(r, i) * y1i;
+      double pr = B.dr[i0], pi = B.di[i0];
+      double y0r = n0r * pr - n0i * pi, y0i = n0r * pi + n0i * pr;
+      double y1r = n1r * pr - n1i * pi, y1i = n1r * pi + n1i * pr;
+      if (wl == 0) { B.yr[i0] = y0r; B.yi[i0] = y0i; B.yr[i] = y1r; B.yi[i] = y1i; }
+      for (int r = wl; r < i0; r += 32) {
+        B.sr[r] -= T[r + m * i0] * y0r + T[r + m * i] * y1r;
+        B.si[r] -= T[r + m * i0] * y0i + T[r + m * i] * y1i;
       }
-      __syncthreads();
+      __syncwarp();
       i -= 2;
     }
   }
-  __syncthreads();
+  __syncwarp();
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 __global__ void k_ritz(RitzArgs R) {
@@ -591,15 +607,17 @@ __global__ void k_ritz(RitzArgs R) {
   S.v = S.Z + m * m;
   S.wr = S.v + m;
   S.wi = S.wr + m;
-  S.yr = S.wi + m;
-  S.yi = S.yr + m;
-  S.sr = S.yi + m;
-  S.si = S.sr + m;
-  S.red = S.si + m;
+  S.red = S.wi + m;
   S.rank = (int*)(S.red + 4);
   S.sel = S.rank + m;
   S.cflag = S.sel + m;
   S.refl = (Refl*)(((uintptr_t)(S.cflag + m) + 15) & ~(uintptr_t)15);
+  double* wbuf = (double*)(S.refl + (NT / 32) * (m + 16));
+  int* wlist = (int*)(wbuf + 6 * (NT / 32) * m);
+  const int warp = lane >> 5, wl = lane & 31;
+  WarpVec B{wbuf + 6 * m * warp,         wbuf + 6 * m * warp + m, wbuf + 6 * m * warp + 2 * m,
+            wbuf + 6 * m * warp + 3 * m, wbuf + 6 * m * warp + 4 * m, wbuf + 6 * m * warp + 5 * m};
+  __shared__ int wcount[NT / 32];
 
   for (int i = lane; i < m * m; i += NT) {
     int r = i % m, c = i / m;
@@ -658,15 +676,25 @@ __global__ void k_ritz(RitzArgs R) {
   // converged (the restart is then not needed), else restarts.
   bool fin = R.final_pass == 1;
   int nconv = 0;
+  // wanted positions in Schur order; each warp takes every fourth one
+  if (lane == 0) {
+    int c = 0;
+    for (int pos = 0; pos < m; ++pos)
+      if (S.rank[pos] < R.neig) wlist[c++] = pos;
+    wcount[0] = c;
+  }
+  __syncthreads();
+  const int nwant = wcount[0];
+  __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
-    nconv = 0;
-    for (int pos = 0; pos < m; ++pos) {
-      int rk = S.rank[pos];
-      if (rk >= R.neig) continue;
+    int myconv = 0;
+    for (int e = warp; e < nwant; e += NT / 32) {
+      const int pos = wlist[e];
+      const int rk = S.rank[pos];
       if (!fin && pos < R.lock) {
         // locked: converged and decoupled, its estimate is zero
-        ++nconv;
-        if (lane == 0) {
+        ++myconv;
+        if (wl == 0) {
           double ir, ii;
           cdiv(1.0, 0.0, S.wr[pos], S.wi[pos], ir, ii);
           R.out->lam[2 * rk] = R.sigma + ir;
@@ -678,24 +706,22 @@ __global__ void k_ritz(RitzArgs R) {
       }
       double lr = S.wr[pos], li = S.wi[pos];
       int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
-      double lri = lr, lii = fabs(li);
-      trevc_one(S, m, jstart, lri, lii, smin, lane);
+      trevc_warp(S.T, m, jstart, lr, fabs(li), smin, S.wi, wl, B);
       // y_H = Z y ; estimate uses the last row; norm of y equals norm of Z y
-      double nrm = 0.0;
-      for (int i = lane; i < m; i += NT) nrm += S.yr[i] * S.yr[i] + S.yi[i] * S.yi[i];
-      nrm = sqrt(block_sum(nrm, S.red, lane));
-      double lastr = 0.0, lasti = 0.0;
-      for (int l = lane; l < m; l += NT) {
-        lastr += ZZ(m - 1, l) * S.yr[l];
-        lasti += ZZ(m - 1, l) * S.yi[l];
+      double nrm = 0.0, lastr = 0.0, lasti = 0.0;
+      for (int l = wl; l < m; l += 32) {
+        nrm += B.yr[l] * B.yr[l] + B.yi[l] * B.yi[l];
+        lastr += ZZ(m - 1, l) * B.yr[l];
+        lasti += ZZ(m - 1, l) * B.yi[l];
       }
-      lastr = block_sum(lastr, S.red, lane);
-      lasti = block_sum(lasti, S.red, lane);
+      nrm = sqrt(warp_sum(nrm));
+      lastr = warp_sum(lastr);
+      lasti = warp_sum(lasti);
       double theta = hypot(lr, li);
       double est = fabs(beta) * hypot(lastr, lasti) / (nrm * theta);
-      if (est <= R.tol) ++nconv;
-      if (lane == 0) S.cflag[pos] = est <= R.tol ? 1 : 0;
-      if (lane == 0) {
+      if (est <= R.tol) ++myconv;
+      if (wl == 0) {
+        S.cflag[pos] = est <= R.tol ? 1 : 0;
         // lambda = s + 1/theta
         double ir, ii;
         cdiv(1.0, 0.0, lr, li, ir, ii);
@@ -705,15 +731,20 @@ __global__ void k_ritz(RitzArgs R) {
       }
       if (fin) {
         double sgn = (li < 0.0) ? -1.0 : 1.0;
-        for (int r = lane; r < m; r += NT) {
+        for (int r = wl; r < m; r += 32) {
           double ar = 0.0, ai = 0.0;
-          for (int l = 0; l < m; ++l) { ar += ZZ(r, l) * S.yr[l]; ai += ZZ(r, l) * S.yi[l]; }
+          for (int l = 0; l < m; ++l) { ar += ZZ(r, l) * B.yr[l]; ai += ZZ(r, l) * B.yi[l]; }
           R.Y[2 * (r + m * rk)] = ar / nrm;
           R.Y[2 * (r + m * rk) + 1] = sgn * ai / nrm;
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
+    if (wl == 0) wcount[warp] = myconv;
+    __syncthreads();
+    nconv = 0;
+    for (int w = 0; w < NT / 32; ++w) nconv += wcount[w];
+    __syncthreads();
     if (fin || R.final_pass != 2 || nconv < R.neig) break;
     fin = true;
     __syncthreads();
@@ -828,8 +859,9 @@ __global__ void k_ritz(RitzArgs R) {
 }  // namespace
 
 size_t ritz_smem(int m) {
-  return sizeof(double) * (2 * (size_t)m * m + 8 * (size_t)m + 4) + 3 * sizeof(int) * m + 16 +
-         sizeof(Refl) * (size_t)(NT / 32) * (size_t)(m + 16);
+  return sizeof(double) * (2 * (size_t)m * m + 4 * (size_t)m + 4) + 3 * sizeof(int) * m + 16 +
+         sizeof(Refl) * (size_t)(NT / 32) * (size_t)(m + 16) +
+         sizeof(double) * 6 * (NT / 32) * (size_t)m + sizeof(int) * (size_t)m;
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
