@@ -103,7 +103,7 @@ def fb_source_hash():
     launcher in factor.cu): the committed DRAM counters stay valid while it
     is unchanged."""
     src = open(os.path.join(ROOT, "paper_2112_14064_gb300", "csrc", "factor.cu")).read()
-    a = src.rindex("\n\n", 0, src.index("k_fb_fwd(FBArgs"))
+    a = src.index("// Forward sweep, one work item")
     b = src.index("__global__ void k_gather")
     c = src.index("void launch_fb(")
     d = src.index("\n}\n", c) + 3

@@ -286,12 +286,13 @@ FBArgs fb_args(Problem& P) {
 //   y_s = (children at the update rows) - W xg      (update rows)
 // Lanes run down the rows (coalesced columns), the eight warps split the
 // columns and keep eight loads in flight each; pivot rows only use the
-// columns up to the chunk's last row.
-__global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
-  extern __shared__ double xg[];
+// columns up to the chunk's last row.  Vectors written by other work items
+// (update vectors, right-hand side) are read through L2 (__ldcg).
+__device__ __forceinline__ void fb_fwd_item(const FBArgs& A, int item, const double* xin,
+                                            double* xg) {
   __shared__ double part[8][32];
   __shared__ double yadd[32];
-  const int4* ip = A.fwd_items + 3 * (int64_t)(item_begin + blockIdx.x);
+  const int4* ip = A.fwd_items + 3 * (int64_t)item;
   int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
   int r0 = i0.y, nr = i0.z, a = i0.w;
   int k = i1.x, u = i1.y, gbase = i1.z;
@@ -315,16 +316,18 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
   // position in child order (deterministic, no write conflicts)
   const bool kids = i2.z != 0;   // the front has children's update entries
   for (int t = threadIdx.x; t < k; t += blockDim.x) {
-    double acc = xin[a + t];
+    double acc = __ldcg(xin + a + t);
     if (kids)
-      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g) acc += A.yvec[A.gsrc[g]];
+      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g)
+        acc += __ldcg(A.yvec + A.gsrc[g]);
     xg[t] = acc;
   }
   if (threadIdx.x < nr && r0 + (int)threadIdx.x >= k) {
     int pos = r0 + threadIdx.x;
     double acc = 0.0;
     if (kids)
-      for (int g = A.gptr[gbase + pos]; g < A.gptr[gbase + pos + 1]; ++g) acc += A.yvec[A.gsrc[g]];
+      for (int g = A.gptr[gbase + pos]; g < A.gptr[gbase + pos + 1]; ++g)
+        acc += __ldcg(A.yvec + A.gsrc[g]);
     yadd[threadIdx.x] = acc;
   }
   __syncthreads();
@@ -356,6 +359,12 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
     if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
     else A.yvec[i1.w + (i - k)] = yadd[threadIdx.x] - dot;
   }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
+  extern __shared__ double xg[];
+  fb_fwd_item(A, item_begin + blockIdx.x, xin, xg);
 }
 
 // Backward sweep, one work item = up to 32 pivot columns c of one front:
@@ -366,16 +375,16 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
 // memory, then each lane forms its own column's dot product from the staged
 // block, so no lane-transpose reduction is needed; the warps' partial sums
 // are added at the end in warp order.  Levels with few items (the top of the
-// tree, long panels) use eight warps per item, the others four.  Optionally writes r_u = -x, r_l = sigma r_u + v_u.
+// tree, long panels) use eight warps per item, the others four.  Optionally
+// writes r_u = -x, r_l = sigma r_u + v_u.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, int item_begin, double* x,
-                                                   double sigma, const double* vu, double* ru,
-                                                   double* rl) {
-  extern __shared__ double bwd_smem[];
-  double(*tile)[32][33] = reinterpret_cast<double(*)[32][33]>(bwd_smem);
+__device__ __forceinline__ void fb_bwd_item(const FBArgs& A, int item, double* x, double sigma,
+                                            const double* vu, double* ru, double* rl,
+                                            double* smem) {
+  double(*tile)[32][33] = reinterpret_cast<double(*)[32][33]>(smem);
   __shared__ double gs[NW][32];
   __shared__ double red[NW][32];
-  const int4* ip = A.bwd_items + 3 * (int64_t)(item_begin + blockIdx.x);
+  const int4* ip = A.bwd_items + 3 * (int64_t)item;
   int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
   int c0 = i0.y, nc = i0.z, a = i0.w;
   int k = i1.x, u = i1.y;
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, i
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
     double g = 0.0;
-    if (i < F) g = i < k ? A.zbuf[a + i] : -x[st[i - k]];
+    if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
     const double* pr = P + ic;
     double v[32];
 #pragma unroll
@@ -415,6 +424,15 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, i
       rl[cc] = sigma * (-sum) + vu[cc];
     }
   }
+  __syncthreads();
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, int item_begin, double* x,
+                                                   double sigma, const double* vu, double* ru,
+                                                   double* rl) {
+  extern __shared__ double bwd_smem[];
+  fb_bwd_item<NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
 }
 
 __global__ void k_gather(const int32_t* idx, const double* src, double* dst, int64_t n) {
