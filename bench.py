@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "p3_256_b16"
-TARGET_KW = dict(m=88, shift=0.0, ncand=56)
+TARGET_KW = dict(m=96, shift=0.0, ncand=56)
 ETA_MAX = 1e-10
 METRIC = "eigenpairs/s at rel. residual <= 1e-10 (FP64)"
 UNIT = "eigenpairs/s"

@@ -19,7 +19,8 @@ Plain FP64 restatement, test infrastructure only.
 Readings where the paper is silent:
 * wanted set = the neig Ritz values nearest s; for equal distances Im > 0
   first (conjugate pairs tie exactly for a real shift);
-* k = neig + (m - neig)//2, plus one when that would split a conjugate pair;
+* k = ncand + 2 kept (at most m - 2, at least ncand), plus one when that would
+  split a conjugate pair;
 * a Ritz pair is converged when |h_{m+1,m} y_m| / |theta| <= tol (y unit);
 * the QEP eigenvector is the upper block x = V_u y, scaled to unit 2-norm with
   its largest-modulus entry real and positive (lowest index on ties);
@@ -138,7 +139,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
         T, Z = sla.schur(Hm, output='real')
         wr, wi = _schur_eigs(T)
         order = wanted_order(s + 1.0 / (wr + 1j * wi), s)
-        kk = ncand + (m - ncand) // 2
+        kk = min(ncand + 2, max(ncand, m - 2))
         sel_idx = set(order[:kk].tolist()) | set(range(lock))
         # keep conjugate partners together
         pos = 0

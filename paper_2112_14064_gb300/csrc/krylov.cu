@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace rq {
 
@@ -126,6 +127,124 @@ __global__ void __launch_bounds__(128) k_dots(const double* V, int64_t ld, int n
     double v = red[0][threadIdx.x] + red[1][threadIdx.x];
     h[c_off + threadIdx.x] = v;
     H[c_off + threadIdx.x + (int64_t)ldh * j] += v;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// The same dot products with the basis streamed through shared memory by
+// TMA: tiles of 128 rows x up to 64 columns (two 128 x 32 boxes), two stages,
+// the next tile's copy in flight while the current one is used.  Warp w
+// takes rows 32 (w mod 4) .. +31 of a tile and column half w / 4; each lane
+// keeps 32 column sums for its rows, reduced over the warp by a butterfly
+// transpose once at the end; then the block's warps and the blocks are summed
+// in a fixed order (last block to finish).  One block per SM.
+constexpr int kTileRows = 128;
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+
+size_t dots_tma_smem() { return sizeof(double) * 2 * 64 * kTileRows + 64; }
+
+__global__ void __launch_bounds__(256, 1)
+    k_dots_tma(const __grid_constant__ CUtensorMap tV, int ncol, int c0, const double* xa,
+               const double* xb, int64_t Np, double* part, unsigned* counter, double* h, double* H,
+               int ldh, int j, DevStatus* st) {
+  extern __shared__ __align__(1024) double dsm[];
+  double* stage0 = dsm;
+  double* stage1 = dsm + 64 * kTileRows;
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + 2 * 64 * kTileRows);
+  __shared__ double red[8][32];
+  __shared__ bool last;
+  const int64_t rows = 2 * Np;
+  const int ntile = (int)((rows + kTileRows - 1) / kTileRows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rs = (warp & 3) * 32, hh = warp >> 2;
+  const int nbox = ncol > 32 ? 2 : 1;
+  const uint32_t bytes = (uint32_t)(nbox * 32 * kTileRows * sizeof(double));
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntile) {
+    mbar_expect_tx(&full[0], bytes);
+    for (int b = 0; b < nbox; ++b)
+      tma_load_2d(stage0 + b * 32 * kTileRows, &tV, (int)blockIdx.x * kTileRows, c0 + 32 * b,
+                  &full[0]);
+  }
+  double acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  bool failed = false;
+  int it = 0;
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    double* cur = s ? stage1 : stage0;
+    double* nxt = s ? stage0 : stage1;
+    // the other stage was last read in the previous iteration, which ended
+    // with a block barrier
+    const int tn = t + gridDim.x;
+    if (threadIdx.x == 0 && tn < ntile) {
+      mbar_expect_tx(&full[s ^ 1], bytes);
+      for (int b = 0; b < nbox; ++b)
+        tma_load_2d(nxt + b * 32 * kTileRows, &tV, tn * kTileRows, c0 + 32 * b, &full[s ^ 1]);
+    }
+    const int64_t i = (int64_t)t * kTileRows + rs + lane;
+    const double x = i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0);
+    const bool ok = mbar_wait(&full[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
+    if (ok && hh < nbox) {
+      const double* tile = cur + hh * 32 * kTileRows + rs + lane;   // column q at tile[q * 128]
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc[q] += tile[q * kTileRows] * x;
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      if (threadIdx.x == 0) {
+        atomicExch(&st->internal, 3);
+        // let a copy still in flight into this block's shared memory land
+        if (tn < ntile) mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitLimit);
+      }
+      __syncthreads();
+      break;
+    }
+  }
+  if (failed) return;
+  // lane l <- the warp's sum for column hh * 32 + l
+#pragma unroll
+  for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
+    bool up = (lane & o) != 0;
+#pragma unroll
+    for (int q = 0; q < len / 2; ++q) {
+      double send = up ? acc[q] : acc[q + len / 2];
+      double keep = up ? acc[q + len / 2] : acc[q];
+      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  red[warp][lane] = acc[0];
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int half = threadIdx.x >> 5, l = threadIdx.x & 31;
+    double sm = (red[4 * half][l] + red[4 * half + 1][l]) + (red[4 * half + 2][l] + red[4 * half + 3][l]);
+    part[blockIdx.x * 64 + threadIdx.x] = sm;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // 256 threads: column c = tid & 63, quarter = tid >> 6 sums every fourth block
+  const int c = threadIdx.x & 63, qtr = threadIdx.x >> 6;
+  double sm = 0.0;
+  for (int b = qtr; b < (int)gridDim.x; b += 4) sm += ((volatile double*)part)[b * 64 + c];
+  __syncthreads();
+  double* red2 = &red[0][0];    // 4 x 64
+  red2[qtr * 64 + c] = sm;
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double v = (red2[threadIdx.x] + red2[64 + threadIdx.x]) +
+               (red2[128 + threadIdx.x] + red2[192 + threadIdx.x]);
+    h[c0 + threadIdx.x] = v;
+    H[c0 + threadIdx.x + (int64_t)ldh * j] += v;
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
@@ -491,6 +610,8 @@ struct Work {
   double fb_ms = 0.0;
   cudaEvent_t rz[2] = {nullptr, nullptr};   // around each Ritz step
   double ritz_ms = 0.0;
+  CUtensorMap tV{};  // the Krylov basis V for the TMA-fed kernels
+  int nsm = 0;       // SMs of the device (one TMA block each)
   ~Work() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : rz)
@@ -518,8 +639,8 @@ struct Work {
   void dots(int j, const double* xa, const double* xb) {
     for (int c0 = 0; c0 <= j; c0 += 64) {
       int nc = std::min(64, j + 1 - c0);
-      k_dots<<<nblk, 128, 0, s>>>(P.V.p + ld * c0, ld, nc, xa, xb, Np, P.part.p, P.counter.p,
-                                  P.hvec.p, P.H.p, m + 1, j, c0);
+      k_dots_tma<<<nsm, 256, dots_tma_smem(), s>>>(tV, nc, c0, xa, xb, Np, P.part.p, P.counter.p,
+                                                    P.hvec.p, P.H.p, m + 1, j, P.status.p);
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
@@ -588,6 +709,13 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   W.nblk = 2 * 152;
   int64_t ld = W.ld, Np = W.Np, N = L.N;
   P.V.alloc(ld * (m + 1));
+  make_tmap_f64(&W.tV, P.V.p, (uint64_t)ld, (uint64_t)(m + 1), (uint64_t)ld, kTileRows, 32);
+  {
+    int dev = 0;
+    RQ_CUDA(cudaGetDevice(&dev));
+    RQ_CUDA(cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, dev));
+    smem_at_least((const void*)k_dots_tma, dots_tma_smem());
+  }
   P.Vtmp.alloc(ld * m);
   P.H.alloc((m + 1) * m);
   P.part.alloc(64 * (size_t)std::max(W.nblk, 4 * 1024) + (size_t)(L.N * 8 + 255) / 256);
@@ -618,7 +746,9 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   RQ_CUDA(cudaGetLastError());
   W.normalise(0, false);
 
-  int kwant = nks + (m - nks) / 2;
+  // kept at a restart: the candidates plus two (measured: fewer operator
+  // applications and Ritz steps than keeping half of the extra vectors)
+  int kwant = std::min(nks + 2, std::max(nks, m - 2));
   int k = 0;
   int lock = 0;   // leading Schur columns locked (converged, decoupled)
   RitzOut h_out{};
@@ -678,6 +808,36 @@ bool same_candidates(const EigsParams& a, const EigsParams& b) {
 }
 
 }  // namespace
+
+void make_tmap_f64(CUtensorMap* map, const double* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                   uint32_t box_rows, uint32_t box_cols) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      RQ_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                               cudaEnableDefault, &q));
+      if (q != cudaDriverEntryPointSuccess || !fn)
+        throw Error(RIGAQEP_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+      encode = (Encode)fn;
+    }
+  }
+  cuuint64_t dims[2] = {rows, cols};
+  cuuint64_t strides[1] = {ld * sizeof(double)};
+  cuuint32_t box[2] = {box_rows, box_cols};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(RIGAQEP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
 
 void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
               double* eta, int* n_conv) {
@@ -771,7 +931,11 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaGetLastError());
   P.launches += 5;
   RQ_CUDA(cudaEventRecord(P.ev1, s));
+  DevStatus dst{};
+  RQ_CUDA(cudaMemcpyAsync(&dst, P.status.p, sizeof(dst), cudaMemcpyDeviceToHost, s));
   RQ_CUDA(cudaStreamSynchronize(s));
+  if (dst.internal)
+    throw Error(RIGAQEP_ERR_INTERNAL, "a bounded wait for a tensor-memory copy ran out");
   float ms = 0.f;
   RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
   P.info.eigs_ms = ms;

@@ -28,7 +28,7 @@ from . import rigaqep, workloads
 
 # in-region eigensolve options of each workload: (Krylov dimension, shift, candidates)
 EIGS_OPTS = {
-    "p3_256_b16": dict(m=88, shift=0.0, ncand=56),
+    "p3_256_b16": dict(m=96, shift=0.0, ncand=56),
     "p3_64_b16": dict(m=96, shift=0.0, ncand=80),
 }
 
