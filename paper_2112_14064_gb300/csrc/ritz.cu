@@ -277,7 +277,9 @@ __device__ double block_sum(double v, double* red, int lane) {
   __syncthreads();
   if ((lane & 31) == 0) red[lane >> 5] = v;
   __syncthreads();
-  double s = (red[0] + red[1]) + (red[2] + red[3]);
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
   __syncthreads();
   return s;
 }
@@ -357,6 +359,7 @@ __device__ __forceinline__ void refl_row(double* A, int m, const Refl& r, int i)
 // it, applied in (round, bulge) order to the columns right of the window,
 // the rows above it and Z, one column or row per thread, without barriers.
 constexpr int kBulges = NT / 32;
+constexpr int kVecWarps = NT / 32 < 4 ? NT / 32 : 4;   // warps computing eigenvectors
 constexpr int kBulgeGap = 4;
 
 __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
@@ -386,7 +389,7 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
     if (++total > 40 * m) { sweeps = total; return false; }
     ++its;
     const int nw = hi - l + 1;
-    const int nb = nw >= kBulges * (kBulgeGap + 2) ? kBulges : 1;
+    const int nb = max(1, min(kBulges, nw / (kBulgeGap + 2)));
     // this warp's shift pair (sum sh, product th): every bulge takes the
     // eigenvalues of the trailing 2 x 2 block (measured: fewer sweeps and
     // less time than shifts from the 2 x 2 blocks above it); bulge 0 takes
@@ -608,15 +611,16 @@ __global__ void k_ritz(RitzArgs R) {
   S.wr = S.v + m;
   S.wi = S.wr + m;
   S.red = S.wi + m;
-  S.rank = (int*)(S.red + 4);
+  S.rank = (int*)(S.red + NT / 32);
   S.sel = S.rank + m;
   S.cflag = S.sel + m;
   S.refl = (Refl*)(((uintptr_t)(S.cflag + m) + 15) & ~(uintptr_t)15);
-  double* wbuf = (double*)(S.refl + (NT / 32) * (m + 16));
-  int* wlist = (int*)(wbuf + 6 * (NT / 32) * m);
+  double* wbuf = (double*)(S.refl + kBulges * (m + 4 * kBulges));
+  int* wlist = (int*)(wbuf + 6 * kVecWarps * m);
   const int warp = lane >> 5, wl = lane & 31;
-  WarpVec B{wbuf + 6 * m * warp,         wbuf + 6 * m * warp + m, wbuf + 6 * m * warp + 2 * m,
-            wbuf + 6 * m * warp + 3 * m, wbuf + 6 * m * warp + 4 * m, wbuf + 6 * m * warp + 5 * m};
+  const int vw = warp < kVecWarps ? warp : 0;
+  WarpVec B{wbuf + 6 * m * vw,         wbuf + 6 * m * vw + m, wbuf + 6 * m * vw + 2 * m,
+            wbuf + 6 * m * vw + 3 * m, wbuf + 6 * m * vw + 4 * m, wbuf + 6 * m * vw + 5 * m};
   __shared__ int wcount[NT / 32];
 
   for (int i = lane; i < m * m; i += NT) {
@@ -688,7 +692,7 @@ __global__ void k_ritz(RitzArgs R) {
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
     int myconv = 0;
-    for (int e = warp; e < nwant; e += NT / 32) {
+    for (int e = warp; warp < kVecWarps && e < nwant; e += kVecWarps) {
       const int pos = wlist[e];
       const int rk = S.rank[pos];
       if (!fin && pos < R.lock) {
@@ -743,7 +747,7 @@ __global__ void k_ritz(RitzArgs R) {
     if (wl == 0) wcount[warp] = myconv;
     __syncthreads();
     nconv = 0;
-    for (int w = 0; w < NT / 32; ++w) nconv += wcount[w];
+    for (int w = 0; w < kVecWarps; ++w) nconv += wcount[w];
     __syncthreads();
     if (fin || R.final_pass != 2 || nconv < R.neig) break;
     fin = true;
@@ -859,9 +863,9 @@ __global__ void k_ritz(RitzArgs R) {
 }  // namespace
 
 size_t ritz_smem(int m) {
-  return sizeof(double) * (2 * (size_t)m * m + 4 * (size_t)m + 4) + 3 * sizeof(int) * m + 16 +
-         sizeof(Refl) * (size_t)(NT / 32) * (size_t)(m + 16) +
-         sizeof(double) * 6 * (NT / 32) * (size_t)m + sizeof(int) * (size_t)m;
+  return sizeof(double) * (2 * (size_t)m * m + 4 * (size_t)m + NT / 32) + 3 * sizeof(int) * m + 16 +
+         sizeof(Refl) * (size_t)kBulges * (size_t)(m + 4 * kBulges) +
+         sizeof(double) * 6 * kVecWarps * (size_t)m + sizeof(int) * (size_t)m;
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
