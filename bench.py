@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     return ap.parse_args()
 
 
@@ -334,6 +335,44 @@ def run_ours(args):
 
     batch = None if args.no_batch else batch_leg(rank, world, barrier)
 
+    # mixed precision: the same step with FP32 fronts and FP64-refined solves,
+    # its eigenvalues against the FP64 step's
+    mixed = None
+    if not args.no_mixed:
+        lam64 = lam.cpu().numpy()
+
+        def step_mixed():
+            pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
+            lm, Xm, em, nc, st = pr.eigs(neig, target, v1=v1_d, raise_on_noconv=False,
+                                         precision=rigaqep.FP32_IR, **TARGET_KW)
+            im = pr.info()
+            gm = (em <= ETA_MAX).sum() if im["certified"] == 1 else torch.zeros((), device=dev)
+            pr.close()
+            return lm, gm, im
+
+        step_mixed()
+        barrier()
+        mt, mp, minf, lmx = [], 0, None, None
+        for i in range(2):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lmx, gm, minf = step_mixed()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mt.append(e0.elapsed_time(e1))
+            mp += int(gm.item())
+        lm_h = lmx.cpu().numpy()
+        diff = max(float(np.min(np.abs(lam64 - v)) / abs(v)) for v in lm_h)
+        mixed = {"precision": "FP32 fronts and sweeps, FP64-refined solves",
+                 "value": 1e3 * mp / sum(mt), "unit": UNIT, "ms_per_step": sum(mt) / len(mt),
+                 "factor_ms": minf["factor_ms"],
+                 "factor_tflops": minf["factor_flops"] / (minf["factor_ms"] * 1e-3) / 1e12,
+                 "refinement_steps": minf["n_ir"], "probe_residual": minf["ir_residual"],
+                 "fb_ms": minf["fb_ms"], "n_apply": minf["n_apply"],
+                 "max_rel_eigenvalue_diff_vs_fp64": diff, "steps": len(mt)}
+
     # max over ranks
     t = torch.tensor([total_ms, float(sum(e2e_ms))], dtype=torch.float64, device=dev)
     pr_t = torch.tensor([float(pairs), float(e2e_pairs)], dtype=torch.float64, device=dev)
@@ -378,6 +417,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": 16 * neig + 16 * N * neig + 8 * neig},
         "gpu_launches": int(sum(i["n_launches"] + 4 for i in infos)),
     }
+    if mixed is not None:
+        line["mixed"] = mixed
     if batch is not None:
         bt = torch.tensor([batch["seconds"], batch["jobs"], batch["pairs_converged"],
                            batch["pairs_certified"], batch["problems"]], dtype=torch.float64,

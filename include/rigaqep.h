@@ -67,7 +67,11 @@ typedef struct {
   int32_t ne_x, ne_y, p, block_x, block_y, n_quad, leaf_min;
 } rigaqep_mesh_desc;
 
-typedef enum { RIGAQEP_FP64 = 0 } rigaqep_precision;
+/* Factor precision.  RIGAQEP_FP64: FP64 fronts and solves.  RIGAQEP_FP32_IR:
+ * FP32 fronts and FP32 forward/backward sweeps, every solve refined in FP64
+ * (x += Q32^{-1}(y - Q x) with the FP64 residual of the assembled K, M, C) for
+ * a number of steps chosen when the factor is made (info.n_ir). */
+typedef enum { RIGAQEP_FP64 = 0, RIGAQEP_FP32_IR = 2 } rigaqep_precision;
 
 /* Krylov-Schur options.  krylov_dim = m (neig < m <= 96), max_restarts
  * (0 selects 1000), tol = Ritz-estimate tolerance |h_{m+1,m} y_m|/|theta|
@@ -127,6 +131,8 @@ typedef struct {
   double ritz_phase_cycles[6];  /* SM cycles of those steps by phase: Hessenberg reduction,
                                    QR sweeps, eigenvalues and ranks, Ritz vectors and
                                    estimates, reordering, locking */
+  int64_t n_ir;           /* FP64 refinement steps per solve (0 with the FP64 factor) */
+  double ir_residual;     /* relative residual reached by those steps on the probe */
   int64_t reused_candidates;  /* 1: the last eigs reused the converged candidates of the
                                  previous in-region call (same factor, shift, ncand,
                                  krylov_dim, tol, max_restarts, seed; seeded start) and
@@ -152,8 +158,12 @@ rigaqep_status rigaqep_assemble(const rigaqep_mesh_desc* mesh, const double* sig
 rigaqep_status rigaqep_analyze(rigaqep_problem* prob);
 
 /* Numeric multifrontal LDL^T of Q(sigma) = sigma^2 M + sigma C + K, fronts
- * batched per tree level.  Requires analyze.  A non-positive pivot returns
- * RIGAQEP_ERR_PIVOT (Q(sigma) is SPD for real sigma > 0).
+ * batched per tree level, in the given rigaqep_precision.  Requires analyze.
+ * A non-positive pivot returns RIGAQEP_ERR_PIVOT (Q(sigma) is SPD for real
+ * sigma > 0).  With RIGAQEP_FP32_IR the call also chooses the number of FP64
+ * refinement steps per solve: the smallest count (at most 40) after which a
+ * seeded right-hand side reaches a relative residual of 1e-14 or stops
+ * improving; RIGAQEP_ERR_REFINEMENT if the refinement does not contract.
  * Defined by: Algorithm 2 ("Factorize Q(s)"), Section 4.2.1. */
 rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t precision);
 

@@ -214,13 +214,15 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     rq::Problem& P = prob->impl;
     rq::StreamScope scope(P.stream);
     need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_factor");
-    need(precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG, "only RIGAQEP_FP64 is available");
+    need(precision == RIGAQEP_FP64 || precision == RIGAQEP_FP32_IR, RIGAQEP_ERR_ARG,
+         "precision must be RIGAQEP_FP64 or RIGAQEP_FP32_IR");
     need(sigma == sigma, RIGAQEP_ERR_ARG, "sigma is NaN");
+    const bool fp32 = precision == RIGAQEP_FP32_IR;
     P.factored = false;
     P.cand_valid = false;
     RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
     RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
-    rq::launch_factor(P, sigma);
+    rq::launch_factor(P, sigma, fp32);
     RQ_CUDA(cudaEventRecord(P.ev1, P.stream));
     rq::DevStatus st;
     RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
@@ -232,6 +234,28 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
       throw rq::Error(RIGAQEP_ERR_PIVOT, "non-positive pivot in supernode " +
                                              std::to_string(st.pivot_fail - 1) +
                                              ": Q(sigma) is not positive definite");
+    P.fact_fp32 = fp32;
+    P.n_ir = 0;
+    P.info.n_ir = 0;
+    P.info.ir_residual = 0.0;
+    if (fp32) {
+      // refinement steps: the fewest that reach 1e-14 on a seeded right-hand
+      // side, or the step after which the residual stops halving (at most 40)
+      std::vector<double> h = rq::ir_history(P, sigma, 40, 1e-14, 0x5eedull);
+      int best = 0;
+      double best_res = 1.0;
+      for (size_t k = 0; k < h.size(); ++k)
+        if (h[k] < best_res) {
+          best_res = h[k];
+          best = (int)k + 1;
+        }
+      if (best == 0 || !(best_res < 1e-6))
+        throw rq::Error(RIGAQEP_ERR_REFINEMENT, "FP64 refinement with the FP32 factor does not "
+                                                "contract (residual " + std::to_string(best_res) + ")");
+      P.n_ir = best;
+      P.info.n_ir = best;
+      P.info.ir_residual = best_res;
+    }
     P.factored = true;
     P.fact_sigma = sigma;
   });
@@ -281,15 +305,17 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     E.max_restarts = opts && opts->max_restarts > 0 ? opts->max_restarts : 1000;
     E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
     E.seed = opts ? opts->seed : 1;
-    need(!opts || opts->precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG, "only RIGAQEP_FP64 is available");
+    const int32_t prec = opts ? opts->precision : RIGAQEP_FP64;
+    need(prec == RIGAQEP_FP64 || prec == RIGAQEP_FP32_IR, RIGAQEP_ERR_ARG,
+         "precision must be RIGAQEP_FP64 or RIGAQEP_FP32_IR");
     need(neig >= 1 && neig <= E.ncand, RIGAQEP_ERR_ARG, "need 1 <= neig <= ncand");
     need(E.ncand < E.m && E.m <= rq::kMaxKrylov, RIGAQEP_ERR_ARG, "need ncand < krylov_dim <= 96");
     need(E.m <= 2 * P.plan.N, RIGAQEP_ERR_ARG, "krylov_dim exceeds 2N");
     need(sigma > 0.0, RIGAQEP_ERR_ARG, "the target must be real and positive");
     need(!E.in_region || E.shift == E.shift, RIGAQEP_ERR_ARG, "shift is NaN");
     P.launches = 0;
-    if (!P.factored || P.fact_sigma != E.shift) {
-      rigaqep_status fs = rigaqep_factor(prob, E.shift, RIGAQEP_FP64);
+    if (!P.factored || P.fact_sigma != E.shift || P.fact_fp32 != (prec == RIGAQEP_FP32_IR)) {
+      rigaqep_status fs = rigaqep_factor(prob, E.shift, prec);
       if (fs != RIGAQEP_OK) throw rq::Error(fs, g_last_error);
       P.launches = 2 * P.plan.nlevels;
     }

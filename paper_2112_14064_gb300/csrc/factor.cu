@@ -31,9 +31,12 @@
 // items of 32 pivot columns form x_s = inv(L11)^T D^{-1}z - W^T x_struct.
 #include "internal.h"
 
+#include <cmath>
+
 namespace rq {
 namespace {
 
+template <class T>
 struct FrontArgs {
   const int32_t* sptr;
   const int32_t* upd_ptr;
@@ -44,37 +47,47 @@ struct FrontArgs {
   const int32_t* lvl_nodes;
   const int64_t* loff;
   const int64_t* uoff;
-  double* Lval;
-  double* Uval;
-  double* Dinv;
-  double* Dval;
+  T* Lval;
+  T* Uval;
+  T* Dinv;
+  T* Dval;
   DevStatus* status;
 };
 
-FrontArgs front_args(Problem& P) {
-  return FrontArgs{P.sptr.p,   P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
-                   P.child_idx.p, P.lvl_nodes.p, P.loff.p, P.uoff.p, P.Lval.p,
-                   P.Uval.p,   P.Dinv.p,    P.Dval.p,    P.status.p};
+template <class T>
+FrontArgs<T> front_args(Problem& P);
+template <>
+FrontArgs<double> front_args<double>(Problem& P) {
+  return FrontArgs<double>{P.sptr.p,      P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
+                           P.child_idx.p, P.lvl_nodes.p, P.loff.p,  P.uoff.p,   P.Lval.p,
+                           P.Uval.p,      P.Dinv.p,    P.Dval.p,    P.status.p};
+}
+template <>
+FrontArgs<float> front_args<float>(Problem& P) {
+  return FrontArgs<float>{P.sptr.p,      P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
+                          P.child_idx.p, P.lvl_nodes.p, P.loff.p,  P.uoff.p,   P.Lval32.p,
+                          P.Uval32.p,    P.Dinv32.p,  P.Dval32.p,  P.status.p};
 }
 
-__global__ void k_front_assemble(FrontArgs A, int lvl_begin, const int32_t* rowptr_n,
+template <class T>
+__global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, const int32_t* rowptr_n,
                                  const int32_t* fpos, const double* Kn, const double* Mn,
                                  const double* Cn, double s2, double s1) {
   int s = A.lvl_nodes[lvl_begin + blockIdx.x];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  double* L = A.Lval + A.loff[s];
-  double* U = A.Uval + A.uoff[s];
-  for (int64_t i = threadIdx.x; i < F * k; i += blockDim.x) L[i] = 0.0;
-  for (int64_t i = threadIdx.x; i < (int64_t)u * u; i += blockDim.x) U[i] = 0.0;
+  T* L = A.Lval + A.loff[s];
+  T* U = A.Uval + A.uoff[s];
+  for (int64_t i = threadIdx.x; i < F * k; i += blockDim.x) L[i] = T(0);
+  for (int64_t i = threadIdx.x; i < (int64_t)u * u; i += blockDim.x) U[i] = T(0);
   __syncthreads();
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = warp; t < k; t += nw) {
     int j = a + t;
     for (int32_t q = rowptr_n[j] + lane; q < rowptr_n[j + 1]; q += 32) {
       int pos = fpos[q];
-      if (pos >= 0) L[pos + F * t] = s2 * Mn[q] + s1 * Cn[q] + Kn[q];
+      if (pos >= 0) L[pos + F * t] = (T)(s2 * Mn[q] + s1 * Cn[q] + Kn[q]);
     }
   }
   __syncthreads();
@@ -82,12 +95,12 @@ __global__ void k_front_assemble(FrontArgs A, int lvl_begin, const int32_t* rowp
     int c = A.child_idx[ci];
     int uc = A.upd_ptr[c + 1] - A.upd_ptr[c];
     const int32_t* rm = A.relmap + A.upd_ptr[c];
-    const double* Uc = A.Uval + A.uoff[c];
+    const T* Uc = A.Uval + A.uoff[c];
     for (int q = warp; q < uc; q += nw) {
       int pc = rm[q];
       for (int r = q + lane; r < uc; r += 32) {
         int pr = rm[r];
-        double v = Uc[r + (int64_t)uc * q];
+        T v = Uc[r + (int64_t)uc * q];
         if (pc < k) L[pr + F * pc] += v;
         else U[(pr - k) + (int64_t)u * (pc - k)] += v;
       }
@@ -100,45 +113,47 @@ __global__ void k_front_assemble(FrontArgs A, int lvl_begin, const int32_t* rowp
 // pivot block (rows < k only), D and D^{-1} stored, then inv(L11) in place
 // (unit lower; column j from the already inverted trailing block, last
 // column first, staged in shared memory).
-__global__ void k_pivot_factor(FrontArgs A, int lvl_begin) {
-  extern __shared__ double lb[];
-  __shared__ double dsh;
+template <class T>
+__global__ void k_pivot_factor(FrontArgs<T> A, int lvl_begin) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* lb = reinterpret_cast<T*>(dyn_smem);
+  __shared__ T dsh;
   int s = A.lvl_nodes[lvl_begin + blockIdx.x];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  double* L = A.Lval + A.loff[s];
+  T* L = A.Lval + A.loff[s];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int t = 0; t < k; ++t) {
     if (threadIdx.x == 0) {
-      double d = L[t + F * t];
-      if (!(d > 0.0)) {
+      T d = L[t + F * t];
+      if (!(d > T(0))) {
         atomicCAS(&A.status->pivot_fail, 0, s + 1);
-        d = 1.0;  // keep going with a harmless value; the host reports the failure
+        d = T(1);  // keep going with a harmless value; the host reports the failure
       }
       dsh = d;
-      L[t + F * t] = 1.0;
-      A.Dinv[a + t] = 1.0 / d;
+      L[t + F * t] = T(1);
+      A.Dinv[a + t] = T(1) / d;
       A.Dval[a + t] = d;
     }
     __syncthreads();
-    double d = dsh;
-    double rd = 1.0 / d;
+    T d = dsh;
+    T rd = T(1) / d;
     for (int i = t + 1 + threadIdx.x; i < k; i += blockDim.x) {
-      double l = L[i + F * t] * rd;
+      T l = L[i + F * t] * rd;
       lb[i] = l;
       L[i + F * t] = l;
     }
     __syncthreads();
     for (int c = t + 1 + warp; c < k; c += nw) {
-      double lc = d * lb[c];
+      T lc = d * lb[c];
       for (int i = c + lane; i < k; i += 32) L[i + F * c] -= lb[i] * lc;
     }
     __syncthreads();
   }
   for (int j = k - 2; j >= 0; --j) {
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) {
-      double v0 = 0.0, v1 = 0.0;
+      T v0 = 0.0, v1 = T(0);
       int c = j + 1;
       for (; c + 1 < i; c += 2) {
         v0 -= L[i + F * c] * L[c + F * j];
@@ -159,43 +174,45 @@ __global__ void k_pivot_factor(FrontArgs A, int lvl_begin) {
 // in place: the chunk's outputs are staged in shared memory and written back
 // after every read of the original rows.  32 x 32 tiles of inv(L11) and
 // 16 x 32 tiles of the rows are staged in shared memory (coalesced loads).
-__global__ void __launch_bounds__(256) k_panel_rows(FrontArgs A, const int4* items, int item_begin,
+template <class T>
+__global__ void __launch_bounds__(256) k_panel_rows(FrontArgs<T> A, const int4* items, int item_begin,
                                                     int mode) {
-  extern __shared__ double out[];          // 16 x k, row-major
-  __shared__ double ta[16][33];            // rows x c
-  __shared__ double tb[32][33];            // c x j  (or j x c)
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* out = reinterpret_cast<T*>(dyn_smem);   // 16 x k, row-major
+  __shared__ T ta[16][33];            // rows x c
+  __shared__ T tb[32][33];            // c x j  (or j x c)
   int4 it = items[item_begin + blockIdx.x];
   int s = it.x, r0 = it.y, nr = it.z;
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  double* L = A.Lval + A.loff[s];
-  double* R = L + k + r0;                  // first row of the chunk (column stride F)
+  T* L = A.Lval + A.loff[s];
+  T* R = L + k + r0;                  // first row of the chunk (column stride F)
   int tid = threadIdx.x;
   int orow = tid >> 4;                     // 0..15: output row
   int ocol = (tid & 15) * 2;               // two output columns within the j tile
   for (int j0 = 0; j0 < k; j0 += 32) {
-    double acc0 = 0.0, acc1 = 0.0;
+    T acc0 = 0.0, acc1 = T(0);
     int cb = mode == 0 ? 0 : j0;           // inner range (triangle of inv(L11))
     int ce = mode == 0 ? min(k, j0 + 32) : k;
     for (int c0 = cb; c0 < ce; c0 += 32) {
       for (int q = tid; q < 16 * 32; q += 256) {
         int r = q & 15, c = q >> 4;
-        ta[r][c] = (r < nr && c0 + c < k) ? R[r + F * (c0 + c)] : 0.0;
+        ta[r][c] = (r < nr && c0 + c < k) ? R[r + F * (c0 + c)] : T(0);
       }
       for (int q = tid; q < 32 * 32; q += 256) {
         int x = q & 31, y = q >> 5;
         // mode 0 needs inv(L11)[j, c]: x = j offset (rows contiguous), y = c offset
         // mode 1 needs inv(L11)[c, j]: x = c offset (rows contiguous), y = j offset
         if (mode == 0)
-          tb[y][x] = (j0 + x < k && c0 + y < k) ? L[(j0 + x) + F * (c0 + y)] : 0.0;
+          tb[y][x] = (j0 + x < k && c0 + y < k) ? L[(j0 + x) + F * (c0 + y)] : T(0);
         else
-          tb[x][y] = (c0 + x < k && j0 + y < k) ? L[(c0 + x) + F * (j0 + y)] : 0.0;
+          tb[x][y] = (c0 + x < k && j0 + y < k) ? L[(c0 + x) + F * (j0 + y)] : T(0);
       }
       __syncthreads();
 #pragma unroll 8
       for (int c = 0; c < 32; ++c) {
-        double av = ta[orow][c];
+        T av = ta[orow][c];
         acc0 += av * tb[c][ocol];
         acc1 += av * tb[c][ocol + 1];
       }
@@ -219,31 +236,32 @@ __global__ void __launch_bounds__(256) k_panel_rows(FrontArgs A, const int4* ite
 
 // Schur complement, one 32 x 32 tile (I >= J) of the update block per CTA:
 // U[I, J] -= L21[I, :] D L21[J, :]^T, 32-column slabs staged in shared memory.
-__global__ void __launch_bounds__(256) k_schur_tile(FrontArgs A, const int4* items, int item_begin) {
-  __shared__ double ta[32][33];
-  __shared__ double tb[32][33];
+template <class T>
+__global__ void __launch_bounds__(256) k_schur_tile(FrontArgs<T> A, const int4* items, int item_begin) {
+  __shared__ T ta[32][33];
+  __shared__ T tb[32][33];
   int4 it = items[item_begin + blockIdx.x];
   int s = it.x, I0 = it.y, J0 = it.z;
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
-  const double* L21 = A.Lval + A.loff[s] + k;   // row i of L21 at L21[i + F c]
-  double* U = A.Uval + A.uoff[s];
+  const T* L21 = A.Lval + A.loff[s] + k;   // row i of L21 at L21[i + F c]
+  T* U = A.Uval + A.uoff[s];
   int tid = threadIdx.x;
   int ty = tid >> 4, tx = tid & 15;              // 16 x 16 threads, 2 x 2 outputs each
-  double c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = 0.0;
+  T c00 = 0.0, c01 = 0.0, c10 = 0.0, c11 = T(0);
   for (int c0 = 0; c0 < k; c0 += 32) {
     for (int q = tid; q < 32 * 32; q += 256) {
       int r = q & 31, c = q >> 5;
       bool okc = c0 + c < k;
-      ta[r][c] = (I0 + r < u && okc) ? L21[(I0 + r) + F * (c0 + c)] : 0.0;
-      tb[r][c] = (J0 + r < u && okc) ? L21[(J0 + r) + F * (c0 + c)] * A.Dval[a + c0 + c] : 0.0;
+      ta[r][c] = (I0 + r < u && okc) ? L21[(I0 + r) + F * (c0 + c)] : T(0);
+      tb[r][c] = (J0 + r < u && okc) ? L21[(J0 + r) + F * (c0 + c)] * A.Dval[a + c0 + c] : T(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int c = 0; c < 32; ++c) {
-      double a0 = ta[2 * ty][c], a1 = ta[2 * ty + 1][c];
-      double b0 = tb[2 * tx][c], b1 = tb[2 * tx + 1][c];
+      T a0 = ta[2 * ty][c], a1 = ta[2 * ty + 1][c];
+      T b0 = tb[2 * tx][c], b1 = tb[2 * tx + 1][c];
       c00 += a0 * b0;
       c01 += a0 * b1;
       c10 += a1 * b0;
@@ -262,21 +280,30 @@ __global__ void __launch_bounds__(256) k_schur_tile(FrontArgs A, const int4* ite
 //   {front, first row/column, count <= 32, first pivot a,
 //    k, u, gather base (forward) / upd_ptr (backward), upd_ptr (forward),
 //    panel offset low, panel offset high, children's entries (forward), 0}
+template <class T>
 struct FBArgs {
   const int32_t* upd_idx;
   const int32_t* gptr;     // per front position: its children's update entries (CSR)
   const int32_t* gsrc;     // yvec slots of those entries, in child order
-  const double* Lval;
-  const double* Dinv;
-  double* yvec;    // update vectors of the forward sweep (one per supernode)
-  double* zbuf;    // forward result D^{-1} inv(L11) x of the pivot rows
+  const T* Lval;
+  const T* Dinv;
+  T* yvec;    // update vectors of the forward sweep (one per supernode)
+  T* zbuf;    // forward result D^{-1} inv(L11) x of the pivot rows
   const int4* fwd_items;
   const int4* bwd_items;
 };
 
-FBArgs fb_args(Problem& P) {
-  return FBArgs{P.upd_idx.p, P.fb_gptr.p, P.fb_gsrc.p, P.Lval.p, P.Dinv.p, P.yvec.p, P.zbuf.p,
-                (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
+template <class T>
+FBArgs<T> fb_args(Problem& P);
+template <>
+FBArgs<double> fb_args<double>(Problem& P) {
+  return FBArgs<double>{P.upd_idx.p, P.fb_gptr.p, P.fb_gsrc.p, P.Lval.p, P.Dinv.p, P.yvec.p,
+                        P.zbuf.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
+}
+template <>
+FBArgs<float> fb_args<float>(Problem& P) {
+  return FBArgs<float>{P.upd_idx.p, P.fb_gptr.p, P.fb_gsrc.p, P.Lval32.p, P.Dinv32.p, P.yvec32.p,
+                       P.zbuf32.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
 // Forward sweep, one work item = up to 32 consecutive rows of one front's
@@ -288,35 +315,36 @@ FBArgs fb_args(Problem& P) {
 // columns and keep eight loads in flight each; pivot rows only use the
 // columns up to the chunk's last row.  Vectors written by other work items
 // (update vectors, right-hand side) are read through L2 (__ldcg).
-__device__ __forceinline__ void fb_fwd_item(const FBArgs& A, int item, const double* xin,
-                                            double* xg) {
-  __shared__ double part[8][32];
-  __shared__ double yadd[32];
+template <class T>
+__device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const T* xin,
+                                            T* xg) {
+  __shared__ T part[8][32];
+  __shared__ T yadd[32];
   const int4* ip = A.fwd_items + 3 * (int64_t)item;
   int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
   int r0 = i0.y, nr = i0.z, a = i0.w;
   int k = i1.x, u = i1.y, gbase = i1.z;
   int64_t F = k + u;
-  const double* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32));
+  const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32));
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int row = r0 + min(lane, nr - 1);
   int cend = r0 + nr <= k ? r0 + nr : k;     // triangle: columns <= last pivot row
   int q = (cend + 7) / 8;
   int cb = warp * q, ce = min(cend, cb + q);
-  const double* pr = P + row;
+  const T* pr = P + row;
   // Columns in chunks of eight with unconditional loads (clamped to a valid
   // column, weight zero past the warp's range) so that a chunk's loads are all
   // in flight together; the first chunk does not depend on the gathered
   // vector and is issued before the gather.
   const int cl = max(cend - 1, 0);
-  double v[8];
+  T v[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) v[t] = pr[F * min(cb + t, cl)];
   // right-hand side plus the children's update vectors, summed per front
   // position in child order (deterministic, no write conflicts)
   const bool kids = i2.z != 0;   // the front has children's update entries
   for (int t = threadIdx.x; t < k; t += blockDim.x) {
-    double acc = __ldcg(xin + a + t);
+    T acc = __ldcg(xin + a + t);
     if (kids)
       for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g)
         acc += __ldcg(A.yvec + A.gsrc[g]);
@@ -324,18 +352,18 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs& A, int item, const dou
   }
   if (threadIdx.x < nr && r0 + (int)threadIdx.x >= k) {
     int pos = r0 + threadIdx.x;
-    double acc = 0.0;
+    T acc = T(0);
     if (kids)
       for (int g = A.gptr[gbase + pos]; g < A.gptr[gbase + pos + 1]; ++g)
         acc += __ldcg(A.yvec + A.gsrc[g]);
     yadd[threadIdx.x] = acc;
   }
   __syncthreads();
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  T s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = T(0);
   for (int c = cb;;) {
-    double w[8];
+    T w[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : 0.0;
+    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
     s0 += v[0] * w[0];
     s1 += v[1] * w[1];
     s2 += v[2] * w[2];
@@ -354,7 +382,7 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs& A, int item, const dou
   if (threadIdx.x < nr) {
     int i = r0 + threadIdx.x;
     const int l = threadIdx.x;
-    double dot = ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l])) +
+    T dot = ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l])) +
                  ((part[4][l] + part[5][l]) + (part[6][l] + part[7][l]));
     if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
     else A.yvec[i1.w + (i - k)] = yadd[threadIdx.x] - dot;
@@ -362,9 +390,11 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs& A, int item, const dou
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const double* xin) {
-  extern __shared__ double xg[];
-  fb_fwd_item(A, item_begin + blockIdx.x, xin, xg);
+template <class T>
+__global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, const T* xin) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* xg = reinterpret_cast<T*>(dyn_smem);
+  fb_fwd_item<T>(A, item_begin + blockIdx.x, xin, xg);
 }
 
 // Backward sweep, one work item = up to 32 pivot columns c of one front:
@@ -377,29 +407,29 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs A, int item_begin, const 
 // are added at the end in warp order.  Levels with few items (the top of the
 // tree, long panels) use eight warps per item, the others four.  Optionally
 // writes r_u = -x, r_l = sigma r_u + v_u.
-template <int NW>
-__device__ __forceinline__ void fb_bwd_item(const FBArgs& A, int item, double* x, double sigma,
-                                            const double* vu, double* ru, double* rl,
-                                            double* smem) {
-  double(*tile)[32][33] = reinterpret_cast<double(*)[32][33]>(smem);
-  __shared__ double gs[NW][32];
-  __shared__ double red[NW][32];
+template <class T, int NW>
+__device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, double sigma,
+                                            const T* vu, T* ru, T* rl,
+                                            T* smem) {
+  T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
+  __shared__ T gs[NW][32];
+  __shared__ T red[NW][32];
   const int4* ip = A.bwd_items + 3 * (int64_t)item;
   int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
   int c0 = i0.y, nc = i0.z, a = i0.w;
   int k = i1.x, u = i1.y;
   int64_t F = k + u;
-  const double* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32)) + F * c0;
+  const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32)) + F * c0;
   const int32_t* st = A.upd_idx + i1.z;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 32 * NW) {
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
-    double g = 0.0;
+    T g = T(0);
     if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
-    const double* pr = P + ic;
-    double v[32];
+    const T* pr = P + ic;
+    T v[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
     gs[warp][lane] = g;
@@ -414,25 +444,89 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs& A, int item, double* x
   __syncthreads();
   if (threadIdx.x < nc) {
     const int l = threadIdx.x;
-    double sum = 0.0;
+    T sum = T(0);
 #pragma unroll
     for (int w = 0; w < NW; ++w) sum += red[w][l];
     int cc = a + c0 + l;
     x[cc] = sum;
     if (ru) {
       ru[cc] = -sum;
-      rl[cc] = sigma * (-sum) + vu[cc];
+      rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
     }
   }
   __syncthreads();
 }
 
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs A, int item_begin, double* x,
-                                                   double sigma, const double* vu, double* ru,
-                                                   double* rl) {
-  extern __shared__ double bwd_smem[];
-  fb_bwd_item<NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
+template <class T, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs<T> A, int item_begin, T* x,
+                                                   double sigma, const T* vu, T* ru,
+                                                   T* rl) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* bwd_smem = reinterpret_cast<T*>(dyn_smem);
+  fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
+}
+
+// refinement helpers (FP64 vectors, FP32 correction)
+__global__ void k_to_f32(const double* a, float* b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_ir_accum(double* x, const float* d, int64_t n, int first) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = first ? (double)d[i] : x[i] + (double)d[i];
+}
+
+// r = y - (s2 M + s1 C + K) x in the ND order, 8 lanes per row; the FP32 copy
+// (next correction's right-hand side) or the FP64 residual
+template <class R>
+__device__ __forceinline__ void ir_residual_row(const int32_t* rowptr, const int32_t* col,
+                                                const double* K, const double* M, const double* C,
+                                                double s2, double s1, const double* x,
+                                                const double* y, R* r, int64_t N) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t row = t / 8;
+  int sub = t % 8;
+  double acc = 0.0;
+  if (row < N)
+    for (int32_t q = rowptr[row] + sub; q < rowptr[row + 1]; q += 8)
+      acc += (s2 * M[q] + s1 * C[q] + K[q]) * x[col[q]];
+  for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, 8);
+  if (row < N && sub == 0) r[row] = (R)(y[row] - acc);
+}
+
+__global__ void k_ir_residual(const int32_t* rowptr, const int32_t* col, const double* K,
+                              const double* M, const double* C, double s2, double s1,
+                              const double* x, const double* y, float* r, int64_t N) {
+  ir_residual_row<float>(rowptr, col, K, M, C, s2, s1, x, y, r, N);
+}
+
+__global__ void k_ir_residual64(const int32_t* rowptr, const int32_t* col, const double* K,
+                                const double* M, const double* C, double s2, double s1,
+                                const double* x, const double* y, double* r, int64_t N) {
+  ir_residual_row<double>(rowptr, col, K, M, C, s2, s1, x, y, r, N);
+}
+
+// operator outputs from the solution x of Q x = y: r_u = -x, r_l = s r_u + v_u
+__global__ void k_op_out(const double* x, double s, const double* vu, double* ru, double* rl,
+                         int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = -x[i];
+    ru[i] = v;
+    rl[i] = s * v + vu[i];
+  }
+}
+
+// seeded right-hand side in [-0.5, 0.5) (splitmix64 of seed + i)
+__global__ void k_probe_rhs(uint64_t seed, double* v, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t z = seed + (uint64_t)i + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  v[i] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
 }
 
 __global__ void k_gather(const int32_t* idx, const double* src, double* dst, int64_t n) {
@@ -447,12 +541,18 @@ __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, in
 
 }  // namespace
 
-constexpr size_t kBwdSmem4 = sizeof(double) * 4 * 32 * 33;
-constexpr size_t kBwdSmem8 = sizeof(double) * 8 * 32 * 33;
+template <class T>
+constexpr size_t bwd_smem(int nw) {
+  return sizeof(T) * (size_t)nw * 32 * 33;
+}
 
 void factor_configure(size_t smem_max) {
-  smem_at_least((const void*)k_fb_bwd<8>, kBwdSmem8);
-  if (smem_max > 48 * 1024) smem_at_least((const void*)k_fb_fwd, smem_max);
+  smem_at_least((const void*)k_fb_bwd<double, 8>, bwd_smem<double>(8));
+  smem_at_least((const void*)k_fb_bwd<float, 8>, bwd_smem<float>(8));
+  if (smem_max > 48 * 1024) {
+    smem_at_least((const void*)k_fb_fwd<double>, smem_max);
+    smem_at_least((const void*)k_fb_fwd<float>, smem_max / 2);
+  }
 }
 
 void factor_plan(Problem& P) {
@@ -475,43 +575,65 @@ void factor_plan(Problem& P) {
   P.tile_items.upload(tiles, P.stream);
   P.Dval.alloc(L.N);
   size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
-  if (smem > 48 * 1024) smem_at_least((const void*)k_panel_rows, smem);
-  if (sizeof(double) * (size_t)L.max_front > 48 * 1024)
-    smem_at_least((const void*)k_pivot_factor, sizeof(double) * L.max_front);
+  if (smem > 48 * 1024) smem_at_least((const void*)k_panel_rows<double>, smem);
+  if (smem / 2 > 48 * 1024) smem_at_least((const void*)k_panel_rows<float>, smem / 2);
+  size_t piv = sizeof(double) * (size_t)L.max_front;
+  if (piv > 48 * 1024) smem_at_least((const void*)k_pivot_factor<double>, piv);
+  if (piv / 2 > 48 * 1024) smem_at_least((const void*)k_pivot_factor<float>, piv / 2);
 }
 
-void launch_factor(Problem& P, double sigma) {
+template <class T>
+void launch_factor_t(Problem& P, double sigma) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
-  FrontArgs A = front_args(P);
+  FrontArgs<T> A = front_args<T>(P);
   const int4* rows = (const int4*)P.row_items.p;
   const int4* tiles = (const int4*)P.tile_items.p;
   for (int l = 0; l < L.nlevels; ++l) {
     int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
-    k_front_assemble<<<cnt, 256, 0, s>>>(A, b, P.rowptr_n.p, P.fpos.p, P.Kn.p, P.Mn.p, P.Cn.p,
-                                         sigma * sigma, sigma);
+    k_front_assemble<T><<<cnt, 256, 0, s>>>(A, b, P.rowptr_n.p, P.fpos.p, P.Kn.p, P.Mn.p, P.Cn.p,
+                                            sigma * sigma, sigma);
     RQ_CUDA(cudaGetLastError());
-    k_pivot_factor<<<cnt, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, b);
+    k_pivot_factor<T><<<cnt, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(A, b);
     RQ_CUDA(cudaGetLastError());
     P.launches += 2;
     int rb = P.row_lvl[l], rc = P.row_lvl[l + 1] - rb;
     int tb = P.tile_lvl[l], tc = P.tile_lvl[l + 1] - tb;
-    size_t smem = sizeof(double) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);
+    size_t smem = sizeof(T) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);
     if (rc > 0) {
-      k_panel_rows<<<rc, 256, smem, s>>>(A, rows, rb, 0);            // L21
+      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 0);            // L21
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
     if (tc > 0) {
-      k_schur_tile<<<tc, 256, 0, s>>>(A, tiles, tb);                 // U -= L21 D L21^T
+      k_schur_tile<T><<<tc, 256, 0, s>>>(A, tiles, tb);                 // U -= L21 D L21^T
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
     if (rc > 0) {
-      k_panel_rows<<<rc, 256, smem, s>>>(A, rows, rb, 1);            // W = L21 inv(L11)
+      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 1);            // W = L21 inv(L11)
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
+  }
+}
+
+void launch_factor(Problem& P, double sigma, bool fp32) {
+  if (fp32) {
+    Plan& L = P.plan;
+    if (P.Lval32.n < (size_t)L.l_total) {   // FP32 factor storage on first use
+      P.Lval32.alloc(L.l_total);
+      P.Uval32.alloc(L.u_total);
+      P.Dinv32.alloc(L.N);
+      P.Dval32.alloc(L.N);
+      P.yvec32.alloc(L.upd_idx.size());
+      P.zbuf32.alloc(L.N);
+      P.ir_y.alloc(L.N);
+      P.ir_r32.alloc(L.N);
+    }
+    launch_factor_t<float>(P, sigma);
+  } else {
+    launch_factor_t<double>(P, sigma);
   }
 }
 
@@ -561,25 +683,111 @@ void fb_plan(Problem& P) {
   P.wbuf.alloc(1);
 }
 
-void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
+template <class T>
+void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
-  FBArgs A = fb_args(P);
+  FBArgs<T> A = fb_args<T>(P);
   for (int l = 0; l < L.nlevels; ++l) {
     int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
-    k_fb_fwd<<<ic, 256, sizeof(double) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
+    k_fb_fwd<T><<<ic, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
     if (ic < 2 * 152)
-      k_fb_bwd<8><<<ic, 256, kBwdSmem8, s>>>(A, ib, xn, sigma, vu, ru, rl);
+      k_fb_bwd<T, 8><<<ic, 256, bwd_smem<T>(8), s>>>(A, ib, xn, sigma, vu, ru, rl);
     else
-      k_fb_bwd<4><<<ic, 128, kBwdSmem4, s>>>(A, ib, xn, sigma, vu, ru, rl);
+      k_fb_bwd<T, 4><<<ic, 128, bwd_smem<T>(4), s>>>(A, ib, xn, sigma, vu, ru, rl);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }
+}
+
+// FP64 iterative refinement with the FP32 factors: x_0 = 0, r_0 = y;
+//   d = Q32^{-1} r_i (FP32 sweeps),  x_{i+1} = x_i + d (FP64),
+//   r_{i+1} = y - Q(s) x_{i+1} (FP64 residual from the assembled K, M, C),
+// for a fixed number of steps chosen when the factor was made.
+void launch_fb_ir(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int64_t N = L.N;
+  const unsigned g = (unsigned)((N + 255) / 256);
+  RQ_CUDA(cudaMemcpyAsync(P.ir_y.p, xn, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  k_to_f32<<<g, 256, 0, s>>>(P.ir_y.p, P.ir_r32.p, N);
+  RQ_CUDA(cudaGetLastError());
+  P.launches += 1;
+  for (int it = 0; it < P.n_ir; ++it) {
+    launch_fb_t<float>(P, P.ir_r32.p, sigma, nullptr, nullptr, nullptr);
+    k_ir_accum<<<g, 256, 0, s>>>(xn, P.ir_r32.p, N, it == 0 ? 1 : 0);
+    RQ_CUDA(cudaGetLastError());
+    P.launches += 1;
+    if (it + 1 < P.n_ir) {
+      k_ir_residual<<<(unsigned)((N * 8 + 255) / 256), 256, 0, s>>>(
+          P.rowptr_n.p, P.col_n.p, P.Kn.p, P.Mn.p, P.Cn.p, sigma * sigma, sigma, xn, P.ir_y.p,
+          P.ir_r32.p, N);
+      RQ_CUDA(cudaGetLastError());
+      P.launches += 1;
+    }
+  }
+  if (ru) {
+    k_op_out<<<g, 256, 0, s>>>(xn, sigma, vu, ru, rl, N);
+    RQ_CUDA(cudaGetLastError());
+    P.launches += 1;
+  }
+}
+
+void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
+  if (P.fact_fp32)
+    launch_fb_ir(P, xn, sigma, vu, ru, rl);
+  else
+    launch_fb_t<double>(P, xn, sigma, vu, ru, rl);
+}
+
+// Relative residuals ||y - Q x_k|| / ||y|| of the refinement steps k = 1, 2,
+// ... on a seeded right-hand side (host-side norms), until the residual
+// reaches `target`, stops falling by half, or `max_steps` steps; used to
+// choose the number of refinement steps after an FP32 factorisation.
+std::vector<double> ir_history(Problem& P, double sigma, int max_steps, double target,
+                               uint64_t seed) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int64_t N = L.N;
+  DBuf<double> y, x, r;
+  y.alloc(N);
+  x.alloc(N);
+  r.alloc(N);
+  const unsigned g = (unsigned)((N + 255) / 256);
+  const unsigned gr = (unsigned)((N * 8 + 255) / 256);
+  k_probe_rhs<<<g, 256, 0, s>>>(seed, y.p, N);
+  RQ_CUDA(cudaGetLastError());
+  k_to_f32<<<g, 256, 0, s>>>(y.p, P.ir_r32.p, N);
+  RQ_CUDA(cudaGetLastError());
+  std::vector<double> hy(N), hr(N), hist;
+  RQ_CUDA(cudaMemcpyAsync(hy.data(), y.p, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  double ny = 0.0;
+  for (int64_t i = 0; i < N; ++i) ny += hy[i] * hy[i];
+  ny = std::sqrt(ny);
+  for (int k = 1; k <= max_steps; ++k) {
+    launch_fb_t<float>(P, P.ir_r32.p, sigma, nullptr, nullptr, nullptr);
+    k_ir_accum<<<g, 256, 0, s>>>(x.p, P.ir_r32.p, N, k == 1 ? 1 : 0);
+    RQ_CUDA(cudaGetLastError());
+    k_ir_residual64<<<gr, 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, P.Kn.p, P.Mn.p, P.Cn.p,
+                                        sigma * sigma, sigma, x.p, y.p, r.p, N);
+    RQ_CUDA(cudaGetLastError());
+    k_to_f32<<<g, 256, 0, s>>>(r.p, P.ir_r32.p, N);
+    RQ_CUDA(cudaGetLastError());
+    RQ_CUDA(cudaMemcpyAsync(hr.data(), r.p, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    RQ_CUDA(cudaStreamSynchronize(s));
+    double nr = 0.0;
+    for (int64_t i = 0; i < N; ++i) nr += hr[i] * hr[i];
+    hist.push_back(std::sqrt(nr) / ny);
+    if (hist.back() <= target) break;
+    if (k > 1 && !(hist.back() < 0.5 * hist[k - 2])) break;
+  }
+  return hist;
 }
 
 void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n, int32_t ld_in,

@@ -134,6 +134,11 @@ struct Problem {
   DBuf<int64_t> loff, uoff;
   // numeric factor
   DBuf<double> Lval, Uval, Dinv, Dval;
+  // FP32 factor (mixed precision: FP32 fronts, FP64 iterative refinement)
+  DBuf<float> Lval32, Uval32, Dinv32, Dval32, yvec32, zbuf32, ir_r32;
+  DBuf<double> ir_y;
+  bool fact_fp32 = false;       // the current factor is the FP32 one
+  int n_ir = 0;                 // refinement steps per solve with the FP32 factor
   DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
   std::vector<int32_t> row_lvl, tile_lvl;
   DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
@@ -166,7 +171,10 @@ struct Problem {
 void launch_assemble(Problem& P);
 void launch_permute_values(Problem& P);
 void launch_norms(Problem& P);
-void launch_factor(Problem& P, double sigma);
+void launch_factor(Problem& P, double sigma, bool fp32);
+// relative residuals of FP64 refinement steps 1, 2, ... with the FP32 factor
+std::vector<double> ir_history(Problem& P, double sigma, int max_steps, double target,
+                               uint64_t seed);
 void factor_configure(size_t smem_max);
 void fb_plan(Problem& P);
 void factor_plan(Problem& P);

@@ -28,6 +28,9 @@ EXPORTS = [
 ]
 
 
+FP64, FP32_IR = 0, 2   # rigaqep_precision
+
+
 class RigaqepError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -63,6 +66,7 @@ class Info(ctypes.Structure):
                 + [("certified", ctypes.c_int64), ("cert_margin", ctypes.c_double),
                    ("n_launches", ctypes.c_int64), ("ritz_ms", ctypes.c_double),
                    ("ritz_phase_cycles", ctypes.c_double * 6),
+                   ("n_ir", ctypes.c_int64), ("ir_residual", ctypes.c_double),
                    ("reused_candidates", ctypes.c_int64)])
 
     def as_dict(self):
@@ -215,20 +219,21 @@ class Problem:
         return x
 
     def eigs(self, neig, sigma, m=None, tol=1e-10, max_restarts=1000, seed=1, v1=None,
-             raise_on_noconv=True, shift=None, ncand=None):
+             raise_on_noconv=True, shift=None, ncand=None, precision=FP64):
         """Eigenpairs nearest the target sigma: (lambda (neig,) complex,
         X (neig, N) complex, eta (neig,), n_converged, status).
 
         shift=None places the spectral shift at sigma; a real shift selects
         the in-region mode (ncand pairs converged around the shift, the neig
-        nearest sigma returned; see info()["certified"])."""
+        nearest sigma returned; see info()["certified"]).  precision=FP32_IR
+        factorises in FP32 and refines every solve in FP64."""
         torch = self._torch
         dev = torch.device("cuda", torch.cuda.current_device())
         lam = torch.empty((neig, 2), dtype=torch.float64, device=dev)
         X = torch.empty((neig, self.N, 2), dtype=torch.float64, device=dev)
         eta = torch.empty(neig, dtype=torch.float64, device=dev)
         nconv = ctypes.c_int32(0)
-        opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand)
+        opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand, precision)
         if v1 is not None:
             v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
         st = self.lib.rigaqep_eigs(self._h, neig, float(sigma), ctypes.byref(opts), _ptr(v1),
@@ -289,11 +294,12 @@ class Problem:
         return out
 
 
-def eigs_opts(neig, m=None, tol=1e-10, max_restarts=1000, seed=1, shift=None, ncand=None):
+def eigs_opts(neig, m=None, tol=1e-10, max_restarts=1000, seed=1, shift=None, ncand=None,
+              precision=FP64):
     """rigaqep_eigs_opts with the defaults of Problem.eigs."""
     nc = neig if ncand is None else ncand
     m = m or min(96, 2 * nc + 20)
-    return EigsOpts(m, max_restarts, tol, seed, 0, 0 if shift is None else 1,
+    return EigsOpts(m, max_restarts, tol, seed, precision, 0 if shift is None else 1,
                     0.0 if shift is None else float(shift), nc)
 
 
@@ -319,7 +325,7 @@ def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):
         X = torch.empty((neig, pr.N, 2), dtype=torch.float64, device=dev)
         eta = torch.empty(neig, dtype=torch.float64, device=dev)
         opts = eigs_opts(neig, **{k: d[k] for k in ("m", "tol", "max_restarts", "seed", "shift",
-                                                   "ncand") if k in d})
+                                                   "ncand", "precision") if k in d})
         arr[j] = BatchJob(d["problem"], neig, float(d["target"]), opts, lam.data_ptr(),
                           X.data_ptr(), eta.data_ptr(), 0, 0, 0, 0, 0.0)
         outs.append((lam, X, eta))

@@ -1,0 +1,111 @@
+"""Mixed precision on the GPU: FP32 fronts and FP32 sweeps, every solve
+refined in FP64 against the assembled K, M, C (RIGAQEP_FP32_IR).
+
+Tolerances:
+* solves: 1e-12 relative to the FP64 oracle solve (the refinement runs until
+  the probe residual reaches 1e-14 or stops halving, and these Q(0) = K
+  systems have condition numbers well below 1e6);
+* eigenvalues: 1e-9 relative to the FP64 oracle (the mixed-mode accuracy the
+  method is held to), backward errors eta <= 1e-10;
+* at full size (256 x 256), the mixed eigenvalues against the FP64 GPU path:
+  1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle.assemble import assemble
+from oracle.multifrontal import factorize
+from oracle.nd import symbolic
+from oracle import qep
+from paper_2112_14064_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_14064_gb300 import build, rigaqep
+    build.build()
+    rigaqep.load()
+    return rigaqep
+
+
+def _oracle(c):
+    A = assemble(c["ne"], c["p"], c["block"], workloads.sigma_e(c))
+    sym = symbolic(A.n1, A.space.c0_dofs, c["p"], A.indptr, A.indices, use_c0=c["block"] > 0)
+    return A, sym
+
+
+def _match(ref, got):
+    return max(np.min(np.abs(ref - g)) / abs(g) for g in got)
+
+
+@pytest.mark.parametrize("name,sigma", [("tiny", 0.0), ("tiny", 20.0), ("p3_64_b16", 0.0)])
+def test_mixed_solve_matches_oracle(rq, name, sigma):
+    c = dict(workloads.CONFIGS[name])
+    A, sym = _oracle(c)
+    F = factorize(sym, A.Q(sigma))
+    b = np.random.default_rng(5).standard_normal((2, A.N))
+    ref = np.stack([F.solve(bb) for bb in b])
+    pr = rq.Problem(c["ne"], c["p"], c["block"], workloads.sigma_e(c)).analyze()
+    pr.factor(sigma, rq.FP32_IR)
+    inf = pr.info()
+    assert inf["n_ir"] >= 1 and inf["ir_residual"] <= 1e-13
+    x = pr.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    err = np.abs(x - ref).max() / np.abs(ref).max()
+    assert err <= 1e-12, err
+    pr.close()
+
+
+def test_mixed_eigs_literal_shift_matches_oracle(rq):
+    c = dict(workloads.CONFIGS["tiny"])
+    A, sym = _oracle(c)
+    v1 = workloads.start_vector(1, 2 * A.N)
+    F = factorize(sym, A.Q(c["shift"]))
+    ref = qep.eigs(A.K, A.C, A.M, c["shift"], c["neig"], c["m"], F.solve, v1)
+    pr = rq.Problem(c["ne"], c["p"], c["block"], workloads.sigma_e(c)).analyze()
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], m=c["m"],
+                                     v1=torch.from_numpy(v1).cuda(), precision=rq.FP32_IR)
+    assert st == 0 and nconv == c["neig"]
+    lam = lam.cpu().numpy()
+    assert _match(ref.lam, lam) < 1e-9 and _match(lam, ref.lam) < 1e-9
+    assert eta.max().item() <= 1e-10
+    pr.close()
+
+
+def test_mixed_eigs_in_region_matches_oracle(rq):
+    c = dict(workloads.CONFIGS["p3_64_b16"])
+    A, sym = _oracle(c)
+    sig = workloads.sigma_e(c)
+    v1 = workloads.start_vector(1, 2 * A.N)
+    F = factorize(sym, A.Q(0.0))
+    ref = qep.eigs(A.K, A.C, A.M, 0.0, c["neig"], 96, F.solve, v1, target=500.0, ncand=56,
+                   sigma_min=sig.min())
+    assert ref.certified
+    pr = rq.Problem(c["ne"], c["p"], c["block"], sig).analyze()
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], 500.0, m=96, v1=torch.from_numpy(v1).cuda(),
+                                     shift=0.0, ncand=56, precision=rq.FP32_IR)
+    assert st == 0 and pr.info()["certified"] == 1
+    lam = lam.cpu().numpy()
+    assert _match(ref.lam, lam) < 1e-9 and _match(lam, ref.lam) < 1e-9
+    assert eta.max().item() <= 1e-10
+    pr.close()
+
+
+def test_mixed_against_fp64_full_size(rq):
+    """256 x 256, p = 3, blocks of 16, target 500 (the bench workload)."""
+    c = dict(workloads.CONFIGS["p3_256_b16"])
+    sig = torch.from_numpy(workloads.sigma_e(c)).cuda()
+    kw = dict(m=96, shift=0.0, ncand=56, seed=1)
+    pr = rq.Problem(c["ne"], c["p"], c["block"], sig).analyze()
+    a = pr.eigs(c["neig"], c["shift"], **kw)[0].cpu().numpy()
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], precision=rq.FP32_IR, **kw)
+    inf = pr.info()
+    assert st == 0 and inf["certified"] == 1 and inf["n_ir"] >= 1
+    b = lam.cpu().numpy()
+    assert _match(a, b) < 1e-9 and _match(b, a) < 1e-9
+    assert eta.max().item() <= 1e-10
+    pr.close()
