@@ -31,6 +31,8 @@
 // items of 32 pivot columns form x_s = inv(L11)^T D^{-1}z - W^T x_struct.
 #include "internal.h"
 
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 namespace rq {
@@ -114,11 +116,11 @@ __global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, const int32_t* r
 // (unit lower; column j from the already inverted trailing block, last
 // column first, staged in shared memory).
 template <class T>
-__global__ void k_pivot_factor(FrontArgs<T> A, int lvl_begin) {
+__global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* lb = reinterpret_cast<T*>(dyn_smem);
   __shared__ T dsh;
-  int s = A.lvl_nodes[lvl_begin + blockIdx.x];
+  int s = fronts[blockIdx.x];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
@@ -165,6 +167,151 @@ __global__ void k_pivot_factor(FrontArgs<T> A, int lvl_begin) {
     __syncthreads();
     for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) L[i + F * j] = lb[i];
     __syncthreads();
+  }
+}
+
+// Pivot block of one large front by a cluster of CTAs (one front per
+// cluster; the block lives in global memory, L2-resident, and the cluster
+// barriers order it between the CTAs; values written by another CTA are read
+// through L2):
+//  LDL^T by 32-column panels: CTA 0 factors the panel (all rows below it) in
+//  shared memory and writes it back with D; then every CTA takes 32 x 32
+//  tiles of the trailing lower triangle, A -= L_panel D L_panel^T.
+//  inv(L11) by 32-column blocks from the last:
+//    X[rest, J] = -X[rest, rest] L[rest, J] X_JJ,   X_JJ = inv(L_JJ),
+//  with X[rest, rest] already in place; every CTA inverts the 32 x 32 block
+//  itself (forward elimination on the identity), reads L[rest, J] before any
+//  CTA overwrites it, and forms every CTA-th row of the result.
+constexpr int kClusterCTAs = 8;
+constexpr int kClusterMinK = 96;    // pivot blocks from this size use a cluster
+constexpr int kClusterMaxK = 800;   // up to this size (k x 32 panel in shared memory)
+
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int32_t* fronts) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int CS = (int)cl.num_blocks();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* Y = reinterpret_cast<T*>(dyn_smem);   // rows x 32, column-major (ld = rows)
+  __shared__ T bl[32][33];                 // L_JJ
+  __shared__ T bx[32][33];                 // inv(L_JJ)
+  __shared__ T dv[32];
+  const int s = fronts[blockIdx.x / CS];
+  const int a = A.sptr[s], k = A.sptr[s + 1] - a;
+  const int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
+  const int64_t F = k + u;
+  T* L = A.Lval + A.loff[s];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // ---- LDL^T by panels
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int jb = min(32, k - j0);
+    const int R = k - j0;
+    if (rank == 0) {
+      for (int q = tid; q < R * jb; q += 256) {
+        int r = q % R, c = q / R;
+        Y[r + R * c] = __ldcg(L + (j0 + r) + F * (j0 + c));
+      }
+      __syncthreads();
+      for (int t = 0; t < jb; ++t) {
+        if (tid == 0) {
+          T d = Y[t + R * t];
+          if (!(d > T(0))) {
+            atomicCAS(&A.status->pivot_fail, 0, s + 1);
+            d = T(1);  // keep going with a harmless value; the host reports the failure
+          }
+          dv[t] = d;
+        }
+        __syncthreads();
+        const T d = dv[t], rd = T(1) / d;
+        for (int r = t + 1 + tid; r < R; r += 256) Y[r + R * t] *= rd;
+        __syncthreads();
+        for (int c = t + 1 + warp; c < jb; c += 8) {
+          const T f = d * Y[c + R * t];
+          for (int r = c + lane; r < R; r += 32) Y[r + R * c] -= Y[r + R * t] * f;
+        }
+        __syncthreads();
+      }
+      for (int q = tid; q < R * jb; q += 256) {
+        int r = q % R, c = q / R;
+        if (r >= c) L[(j0 + r) + F * (j0 + c)] = r == c ? T(1) : Y[r + R * c];
+      }
+      for (int t = tid; t < jb; t += 256) {
+        A.Dval[a + j0 + t] = dv[t];
+        A.Dinv[a + j0 + t] = T(1) / dv[t];
+      }
+    }
+    cl.sync();
+    const int Rt = k - j0 - jb;    // trailing rows and columns
+    if (Rt > 0) {
+      for (int q = tid; q < Rt * jb; q += 256) {
+        int r = q % Rt, c = q / Rt;
+        Y[r + Rt * c] = __ldcg(L + (j0 + jb + r) + F * (j0 + c));
+      }
+      if (tid < jb) dv[tid] = __ldcg(A.Dval + a + j0 + tid);
+      __syncthreads();
+      const int nt = (Rt + 31) / 32;
+      int tile = 0;
+      for (int I = 0; I < nt; ++I)
+        for (int J = 0; J <= I; ++J, ++tile) {
+          if (tile % CS != rank) continue;
+          const int c = J * 32 + lane;
+          for (int p = 0; p < 4; ++p) {
+            const int r = I * 32 + warp + 8 * p;
+            if (r < Rt && c < Rt && r >= c) {
+              T acc = T(0);
+              for (int t = 0; t < jb; ++t) acc += Y[r + Rt * t] * (dv[t] * Y[c + Rt * t]);
+              T* dst = L + (j0 + jb + r) + F * (j0 + jb + c);
+              *dst = __ldcg(dst) - acc;
+            }
+          }
+        }
+    }
+    cl.sync();
+  }
+  // ---- inv(L11) in place, blocks from the last
+  const int nb = (k + 31) / 32;
+  for (int J = nb - 1; J >= 0; --J) {
+    const int j0 = J * 32, jb = min(32, k - j0);
+    const int Rr = k - j0 - jb;
+    for (int q = tid; q < 32 * 32; q += 256) {
+      int r = q & 31, c = q >> 5;
+      bl[r][c] = (r < jb && c < r) ? __ldcg(L + (j0 + r) + F * (j0 + c)) : T(0);
+      bx[r][c] = r == c ? T(1) : T(0);
+    }
+    for (int q = tid; q < Rr * jb; q += 256) {
+      int r = q % Rr, c = q / Rr;
+      Y[r + Rr * c] = __ldcg(L + (j0 + jb + r) + F * (j0 + c));
+    }
+    __syncthreads();
+    // forward elimination on the identity: after step t, row t of bx is final
+    for (int t = 0; t < jb; ++t) {
+      for (int q = tid; q < 32 * 32; q += 256) {
+        int r = q & 31, c = q >> 5;
+        if (r > t && r < jb && c <= t) bx[r][c] -= bl[r][t] * bx[t][c];
+      }
+      __syncthreads();
+    }
+    cl.sync();   // every CTA holds L[rest, J] before any overwrites it
+    for (int i = rank + CS * warp; i < Rr; i += CS * 8) {
+      // z = Y[i, :] + sum_{q < i} X[i, q] Y[q, :]   (lane = column)
+      T z = lane < jb ? Y[i + Rr * lane] : T(0);
+      const T* xi = L + (j0 + jb + i) + F * (int64_t)(j0 + jb);
+      for (int q = 0; q < i; ++q) z += __ldcg(xi + F * q) * (lane < jb ? Y[q + Rr * lane] : T(0));
+      // X[i, J] = -z X_JJ:  out[c] = -sum_{t >= c} z[t] bx[t][c]
+      T o = T(0);
+      for (int t = 0; t < jb; ++t) {
+        T zt = __shfl_sync(0xffffffffu, z, t);
+        if (t >= lane) o += zt * bx[t][lane];
+      }
+      if (lane < jb) L[(j0 + jb + i) + F * (j0 + lane)] = -o;
+    }
+    if (rank == 0)
+      for (int q = tid; q < jb * jb; q += 256) {
+        int r = q % jb, c = q / jb;
+        if (r > c) L[(j0 + r) + F * (j0 + c)] = bx[r][c];
+      }
+    cl.sync();
   }
 }
 
@@ -573,6 +720,26 @@ void factor_plan(Problem& P) {
   }
   P.row_items.upload(rows, P.stream);
   P.tile_items.upload(tiles, P.stream);
+  // pivot blocks of each level: small ones one CTA each, large ones a cluster
+  std::vector<int32_t> pf;
+  P.piv_lvl.assign(2 * L.nlevels + 1, 0);
+  for (int l = 0; l < L.nlevels; ++l) {
+    for (int big = 0; big < 2; ++big) {
+      for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
+        int sn = L.lvl_nodes[q];
+        int k = L.sptr[sn + 1] - L.sptr[sn];
+        bool isbig = k >= kClusterMinK && k <= kClusterMaxK;
+        if (isbig == (big == 1)) pf.push_back(sn);
+      }
+      P.piv_lvl[2 * l + big + 1] = (int32_t)pf.size();
+    }
+  }
+  P.piv_fronts.upload(pf, P.stream);
+  {
+    size_t cs = sizeof(double) * 32 * (size_t)kClusterMaxK;
+    smem_at_least((const void*)k_pivot_cluster<double>, cs);
+    smem_at_least((const void*)k_pivot_cluster<float>, cs / 2);
+  }
   P.Dval.alloc(L.N);
   size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
   if (smem > 48 * 1024) smem_at_least((const void*)k_panel_rows<double>, smem);
@@ -594,9 +761,32 @@ void launch_factor_t(Problem& P, double sigma) {
     k_front_assemble<T><<<cnt, 256, 0, s>>>(A, b, P.rowptr_n.p, P.fpos.p, P.Kn.p, P.Mn.p, P.Cn.p,
                                             sigma * sigma, sigma);
     RQ_CUDA(cudaGetLastError());
-    k_pivot_factor<T><<<cnt, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(A, b);
-    RQ_CUDA(cudaGetLastError());
-    P.launches += 2;
+    const int nsm = P.piv_lvl[2 * l + 1] - P.piv_lvl[2 * l];
+    const int nbig = P.piv_lvl[2 * l + 2] - P.piv_lvl[2 * l + 1];
+    if (nsm > 0) {
+      k_pivot_factor<T><<<nsm, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(
+          A, P.piv_fronts.p + P.piv_lvl[2 * l]);
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
+    if (nbig > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(nbig * kClusterCTAs));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = sizeof(T) * 32 * (size_t)P.lvl_maxK[l];
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kClusterCTAs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const int32_t* fl = P.piv_fronts.p + P.piv_lvl[2 * l + 1];
+      RQ_CUDA(cudaLaunchKernelEx(&cfg, k_pivot_cluster<T>, A, fl));
+      ++P.launches;
+    }
+    ++P.launches;
     int rb = P.row_lvl[l], rc = P.row_lvl[l + 1] - rb;
     int tb = P.tile_lvl[l], tc = P.tile_lvl[l + 1] - tb;
     size_t smem = sizeof(T) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);

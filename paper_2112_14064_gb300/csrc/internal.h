@@ -140,6 +140,8 @@ struct Problem {
   bool fact_fp32 = false;       // the current factor is the FP32 one
   int n_ir = 0;                 // refinement steps per solve with the FP32 factor
   DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
+  DBuf<int32_t> piv_fronts;     // per level: small pivot blocks, then cluster-sized ones
+  std::vector<int32_t> piv_lvl; // boundaries: level l small [2l, 2l+1), large [2l+1, 2l+2)
   std::vector<int32_t> row_lvl, tile_lvl;
   DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
   DBuf<double> xwork;           // FB work vector (N)

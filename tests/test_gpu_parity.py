@@ -99,6 +99,27 @@ def test_solve_matches_oracle(rq, name, over, sigma):
     pr.close()
 
 
+@pytest.mark.parametrize("ne,sigma,prec", [(128, 0.0, 0), (128, 500.0, 0), (256, 0.0, 0),
+                                           (128, 0.0, 2)])
+def test_solve_residual_large_fronts(rq, ne, sigma, prec):
+    """Meshes whose top pivot blocks (143 and 287 pivots) are factorised by a
+    cluster of CTAs: the FP64 residual of the GPU solve against the assembled
+    Q(sigma) (a property that holds at any size; these systems have condition
+    numbers below 1e7, so a backward-stable solve leaves < 1e-12)."""
+    import scipy.sparse as sp
+    c = _cfg("p3_256_b16", ne=ne)
+    pr = _problem(rq, c).factor(sigma, prec)
+    csr = pr.export_csr()
+    Q = sp.csr_matrix((sigma * sigma * csr["M"] + sigma * csr["C"] + csr["K"], csr["col"],
+                       csr["rowptr"]), shape=(pr.N, pr.N))
+    B = np.random.default_rng(11).standard_normal((2, pr.N))
+    X = pr.solve(torch.from_numpy(B).cuda()).cpu().numpy()
+    for i in range(2):
+        res = np.abs(B[i] - Q @ X[i]).max() / (np.abs(Q).max() * np.abs(X[i]).max())
+        assert res <= 1e-12, res
+    pr.close()
+
+
 def test_solve_in_place_and_zero_rhs(rq):
     c = _cfg("tiny")
     A, _ = _oracle(c)
