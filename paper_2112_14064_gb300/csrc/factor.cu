@@ -183,7 +183,7 @@ __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
 //  itself (forward elimination on the identity), reads L[rest, J] before any
 //  CTA overwrites it, and forms every CTA-th row of the result.
 constexpr int kClusterCTAs = 8;
-constexpr int kClusterMinK = 96;    // pivot blocks from this size use a cluster
+constexpr int kClusterMinK = 64;    // pivot blocks from this size use a cluster
 constexpr int kClusterMaxK = 800;   // up to this size (k x 32 panel in shared memory)
 
 template <class T>
@@ -453,20 +453,24 @@ FBArgs<float> fb_args<float>(Problem& P) {
                        P.zbuf32.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
-// Forward sweep, one work item = up to 32 consecutive rows of one front's
+// Forward sweep, one work item = up to 32 RC consecutive rows of one front's
 // panel P = [inv(L11); W], W = L21 inv(L11):
 //   xg  = x_s + (children's update vectors at the pivot rows)
 //   z   = inv(L11) xg           -> zbuf = D^{-1} z   (pivot rows)
 //   y_s = (children at the update rows) - W xg      (update rows)
-// Lanes run down the rows (coalesced columns), the eight warps split the
-// columns and keep eight loads in flight each; pivot rows only use the
-// columns up to the chunk's last row.  Vectors written by other work items
-// (update vectors, right-hand side) are read through L2 (__ldcg).
-template <class T>
+// Lanes run down the rows (coalesced columns).  Warp w takes row chunk
+// w mod RC (32 rows) and column part w / RC of 8 / RC, keeping eight loads in
+// flight; pivot rows only use the columns up to the chunk's last row.  RC = 1
+// for long panels (all eight warps split the columns of 32 rows), RC = 4 for
+// the short ones at the bottom of the tree (one item covers a small front and
+// its gather is done once).  Vectors written by other work items (update
+// vectors, right-hand side) are read through L2 (__ldcg).
+template <class T, int RC>
 __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const T* xin,
                                             T* xg) {
+  constexpr int NP = 8 / RC;          // column parts per row chunk
   __shared__ T part[8][32];
-  __shared__ T yadd[32];
+  __shared__ T yadd[32 * RC];
   const int4* ip = A.fwd_items + 3 * (int64_t)item;
   int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
   int r0 = i0.y, nr = i0.z, a = i0.w;
@@ -474,11 +478,15 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   int64_t F = k + u;
   const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32));
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int row = r0 + min(lane, nr - 1);
-  int cend = r0 + nr <= k ? r0 + nr : k;     // triangle: columns <= last pivot row
-  int q = (cend + 7) / 8;
-  int cb = warp * q, ce = min(cend, cb + q);
-  const T* pr = P + row;
+  const int rc = warp % RC, cp = warp / RC;
+  const int cr0 = r0 + 32 * rc;                       // first row of this warp's chunk
+  const int cn = max(0, min(32, nr - 32 * rc));       // rows of the chunk
+  int row = cr0 + min(lane, max(cn, 1) - 1);
+  int cend = cr0 + cn <= k ? cr0 + cn : k;            // triangle: columns <= last pivot row
+  if (cn == 0) cend = 0;
+  int q = (cend + NP - 1) / NP;
+  int cb = cp * q, ce = min(cend, cb + q);
+  const T* pr = P + min(row, (int)F - 1);
   // Columns in chunks of eight with unconditional loads (clamped to a valid
   // column, weight zero past the warp's range) so that a chunk's loads are all
   // in flight together; the first chunk does not depend on the gathered
@@ -506,7 +514,7 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
     yadd[threadIdx.x] = acc;
   }
   __syncthreads();
-  T s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = T(0);
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   for (int c = cb;;) {
     T w[8];
 #pragma unroll
@@ -527,21 +535,23 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   part[warp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (threadIdx.x < nr) {
-    int i = r0 + threadIdx.x;
     const int l = threadIdx.x;
-    T dot = ((part[0][l] + part[1][l]) + (part[2][l] + part[3][l])) +
-                 ((part[4][l] + part[5][l]) + (part[6][l] + part[7][l]));
+    int i = r0 + l;
+    const int lrc = l / 32, ll = l % 32;
+    T dot = T(0);
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) dot += part[pp * RC + lrc][ll];
     if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
-    else A.yvec[i1.w + (i - k)] = yadd[threadIdx.x] - dot;
+    else A.yvec[i1.w + (i - k)] = yadd[l] - dot;
   }
   __syncthreads();
 }
 
-template <class T>
+template <class T, int RC>
 __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, const T* xin) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* xg = reinterpret_cast<T*>(dyn_smem);
-  fb_fwd_item<T>(A, item_begin + blockIdx.x, xin, xg);
+  fb_fwd_item<T, RC>(A, item_begin + blockIdx.x, xin, xg);
 }
 
 // Backward sweep, one work item = up to 32 pivot columns c of one front:
@@ -697,8 +707,10 @@ void factor_configure(size_t smem_max) {
   smem_at_least((const void*)k_fb_bwd<double, 8>, bwd_smem<double>(8));
   smem_at_least((const void*)k_fb_bwd<float, 8>, bwd_smem<float>(8));
   if (smem_max > 48 * 1024) {
-    smem_at_least((const void*)k_fb_fwd<double>, smem_max);
-    smem_at_least((const void*)k_fb_fwd<float>, smem_max / 2);
+    smem_at_least((const void*)k_fb_fwd<double, 1>, smem_max);
+    smem_at_least((const void*)k_fb_fwd<float, 1>, smem_max / 2);
+    smem_at_least((const void*)k_fb_fwd<double, 4>, smem_max);
+    smem_at_least((const void*)k_fb_fwd<float, 4>, smem_max / 2);
   }
 }
 
@@ -850,14 +862,18 @@ void fb_plan(Problem& P) {
   std::vector<int32_t> fwd, bwd;
   P.fwd_lvl.assign(L.nlevels + 1, 0);
   P.bwd_lvl.assign(L.nlevels + 1, 0);
+  P.fwd_rc.assign(L.nlevels, 1);
   for (int l = 0; l < L.nlevels; ++l) {
+    // 128-row forward items on levels whose pivot blocks are all small
+    P.fwd_rc[l] = P.lvl_maxK[l] <= 64 ? 4 : 1;
+    const int rows = 32 * P.fwd_rc[l];
     for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
       int s = L.lvl_nodes[q];
       int a = L.sptr[s], k = L.sptr[s + 1] - a, u = L.upd_ptr[s + 1] - L.upd_ptr[s];
       int32_t lo = (int32_t)(uint32_t)(L.loff[s] & 0xffffffffll), hi = (int32_t)(L.loff[s] >> 32);
       int nkid = gptr[gbase[s + 1]] - gptr[gbase[s]];   // children's update entries
-      for (int r = 0; r < k + u; r += 32)
-        fwd.insert(fwd.end(), {s, r, std::min(32, k + u - r), a, k, u, gbase[s], L.upd_ptr[s],
+      for (int r = 0; r < k + u; r += rows)
+        fwd.insert(fwd.end(), {s, r, std::min(rows, k + u - r), a, k, u, gbase[s], L.upd_ptr[s],
                                lo, hi, nkid, 0});
       for (int c = 0; c < k; c += 32)
         bwd.insert(bwd.end(), {s, c, std::min(32, k - c), a, k, u, L.upd_ptr[s], 0, lo, hi, 0, 0});
@@ -880,7 +896,11 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
   FBArgs<T> A = fb_args<T>(P);
   for (int l = 0; l < L.nlevels; ++l) {
     int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
-    k_fb_fwd<T><<<ic, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(A, ib, xn);
+    const size_t sm = sizeof(T) * (size_t)P.lvl_maxK[l];
+    if (P.fwd_rc[l] == 4)
+      k_fb_fwd<T, 4><<<ic, 256, sm, s>>>(A, ib, xn);
+    else
+      k_fb_fwd<T, 1><<<ic, 256, sm, s>>>(A, ib, xn);
     RQ_CUDA(cudaGetLastError());
     ++P.launches;
   }

@@ -149,6 +149,7 @@ struct Problem {
   DBuf<int32_t> fwd_items, bwd_items;   // FB work items (12 int32 each, see factor.cu)
   DBuf<int32_t> fb_gptr, fb_gsrc;       // per front position: children's update entries
   std::vector<int32_t> fwd_lvl, bwd_lvl;  // work items of each level
+  std::vector<int32_t> fwd_rc;            // 32-row chunks per forward item, per level
   // Krylov workspace
   DBuf<double> V, Vtmp, H, part, hvec, wvec, yop, scal, Y;
   DBuf<RitzOut> ritz;
