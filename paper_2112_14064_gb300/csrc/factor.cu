@@ -297,7 +297,17 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
       // z = Y[i, :] + sum_{q < i} X[i, q] Y[q, :]   (lane = column)
       T z = lane < jb ? Y[i + Rr * lane] : T(0);
       const T* xi = L + (j0 + jb + i) + F * (int64_t)(j0 + jb);
-      for (int q = 0; q < i; ++q) z += __ldcg(xi + F * q) * (lane < jb ? Y[q + Rr * lane] : T(0));
+      const int lc = lane < jb ? lane : 0;
+      const T lm = lane < jb ? T(1) : T(0);
+      int q = 0;
+      for (; q + 8 <= i; q += 8) {   // eight row entries of X in flight
+        T xv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) xv[t] = __ldcg(xi + F * (q + t));
+#pragma unroll
+        for (int t = 0; t < 8; ++t) z += xv[t] * (lm * Y[(q + t) + Rr * lc]);
+      }
+      for (; q < i; ++q) z += __ldcg(xi + F * q) * (lm * Y[q + Rr * lc]);
       // X[i, J] = -z X_JJ:  out[c] = -sum_{t >= c} z[t] bx[t][c]
       T o = T(0);
       for (int t = 0; t < jb; ++t) {
