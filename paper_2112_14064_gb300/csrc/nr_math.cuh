@@ -8,12 +8,15 @@ namespace rq {
 // GPU every FP64 instruction occupies an SM sub-partition's FP64 pipe for 64
 // cycles and a square root plus a divide measured ~1,350 cycles, so both
 // start from the FP32 hardware approximation and apply Newton-Raphson steps in
-// FP64 (quadratic convergence: two steps from 24 bits exceed 53 bits), plus
-// one residual correction.  Outside the FP32 exponent range they fall back to
-// the FP64 operators.
+// FP64 (quadratic convergence): two steps for the reciprocal, one step plus a
+// residual correction for the square root.  Outside the FP32 exponent range
+// they fall back to the FP64 operators.
+
+// |x| in [2^-99, 2^100): an integer test on the exponent field of the high
+// word (no FP64 instruction), so that the FP32 seeds below stay normal.
 __device__ __forceinline__ bool f32_range(double x) {
-  double a = fabs(x);
-  return a > 1e-30 && a < 1e30;
+  const int e = (__double2hiint(x) >> 20) & 0x7ff;
+  return e > 1023 - 100 && e < 1023 + 100;
 }
 __device__ __forceinline__ double rcp_nr(double x) {
   if (!f32_range(x)) return 1.0 / x;
@@ -28,12 +31,14 @@ __device__ __forceinline__ double div_nr(double a, double b) {
   double q = a * r;
   return fma(r, fma(-b, q, a), q);   // one residual correction
 }
+// One Newton step on the FP32 reciprocal square root (relative error about
+// 1.5 e0^2 < 2^-41 from e0 < 2^-21), then sqrt(x) = x y with one residual
+// correction s + (y/2)(x - s^2), which squares the error again.
 __device__ __forceinline__ double sqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return sqrt(x);
+  if (!(x > 0.0) || !f32_range(x)) return sqrt(x);
   double y = (double)rsqrtf((float)x);         // ~ 1/sqrt(x)
   y = y * fma(-0.5 * x * y, y, 1.5);           // y <- y (3 - x y^2) / 2
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  double s = x * y;                            // sqrt(x), then one residual correction
+  double s = x * y;
   return fma(0.5 * y, fma(-s, s, x), s);
 }
 
