@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <iterator>
 #include <stdexcept>
 #include <thread>
 
@@ -178,32 +179,43 @@ void Plan::build_symbolic() {
   for (int s = 0; s < nsuper; ++s)
     for (int j = sptr[s]; j < sptr[s + 1]; ++j) owner[j] = s;
 
-  // exact supernodal structures, processed in post-order
+  // exact supernodal structures: the later-ordered neighbours of each
+  // supernode's own rows (independent per supernode, host threads), then in
+  // post-order the union with the children's structures (sorted merges)
   parent.assign(nsuper, -1);
   level.assign(nsuper, 0);
   std::vector<std::vector<int32_t>> kids(nsuper);
   std::vector<std::vector<int32_t>> st(nsuper);
-  std::vector<int32_t> mark(N, -1);
-  for (int s = 0; s < nsuper; ++s) {
-    int a = sptr[s], e = sptr[s + 1];
-    std::vector<int32_t>& S = st[s];
-    for (int j = a; j < e; ++j) {
-      int32_t o = perm[j];
-      for (int32_t q = rowptr[o]; q < rowptr[o + 1]; ++q) {
-        int32_t i = iperm[col[q]];
-        if (i >= e && mark[i] != s) { mark[i] = s; S.push_back(i); }
+  parallel_ranges(nsuper, 64, [&](int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s) {
+      int a = sptr[s], e = sptr[s + 1];
+      std::vector<int32_t>& S = st[s];
+      for (int j = a; j < e; ++j) {
+        int32_t o = perm[j];
+        for (int32_t q = rowptr[o]; q < rowptr[o + 1]; ++q) {
+          int32_t i = iperm[col[q]];
+          if (i >= e) S.push_back(i);
+        }
       }
+      std::sort(S.begin(), S.end());
+      S.erase(std::unique(S.begin(), S.end()), S.end());
     }
+  });
+  std::vector<int32_t> merged;
+  for (int s = 0; s < nsuper; ++s) {
+    int e = sptr[s + 1];
     int lv = 0;
     for (int32_t c : kids[s]) {
-      for (int32_t i : st[c])
-        if (i >= e && mark[i] != s) { mark[i] = s; S.push_back(i); }
+      const std::vector<int32_t>& C = st[c];
+      auto from = std::lower_bound(C.begin(), C.end(), e);
+      merged.clear();
+      std::set_union(st[s].begin(), st[s].end(), from, C.end(), std::back_inserter(merged));
+      st[s].swap(merged);
       lv = std::max(lv, level[c] + 1);
     }
     level[s] = lv;
-    std::sort(S.begin(), S.end());
-    if (!S.empty()) {
-      parent[s] = owner[S[0]];
+    if (!st[s].empty()) {
+      parent[s] = owner[st[s][0]];
       kids[parent[s]].push_back(s);
     }
   }
