@@ -505,6 +505,9 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   T v[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) v[t] = pr[F * min(cb + t, cl)];
+  // the panels and item descriptors were written before this sweep; the
+  // vectors below come from the previous kernels of the stream
+  pdl_wait();
   // right-hand side plus the children's update vectors, summed per front
   // position in child order (deterministic, no write conflicts)
   const bool kids = i2.z != 0;   // the front has children's update entries
@@ -559,6 +562,7 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
 
 template <class T, int RC>
 __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, const T* xin) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* xg = reinterpret_cast<T*>(dyn_smem);
   fb_fwd_item<T, RC>(A, item_begin + blockIdx.x, xin, xg);
@@ -590,6 +594,7 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
   const int32_t* st = A.upd_idx + i1.z;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T acc = T(0);
+  pdl_wait();   // zbuf and x come from the previous kernels of the stream
   for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 32 * NW) {
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
@@ -628,6 +633,7 @@ template <class T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs<T> A, int item_begin, T* x,
                                                    double sigma, const T* vu, T* ru,
                                                    T* rl) {
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* bwd_smem = reinterpret_cast<T*>(dyn_smem);
   fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
@@ -908,19 +914,19 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
     int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
     const size_t sm = sizeof(T) * (size_t)P.lvl_maxK[l];
     if (P.fwd_rc[l] == 4)
-      k_fb_fwd<T, 4><<<ic, 256, sm, s>>>(A, ib, xn);
+      launch_pdl(k_fb_fwd<T, 4>, dim3(ic), dim3(256), sm, s, A, ib, (const T*)xn);
     else
-      k_fb_fwd<T, 1><<<ic, 256, sm, s>>>(A, ib, xn);
-    RQ_CUDA(cudaGetLastError());
+      launch_pdl(k_fb_fwd<T, 1>, dim3(ic), dim3(256), sm, s, A, ib, (const T*)xn);
     ++P.launches;
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
     if (ic < 2 * 152)
-      k_fb_bwd<T, 8><<<ic, 256, bwd_smem<T>(8), s>>>(A, ib, xn, sigma, vu, ru, rl);
+      launch_pdl(k_fb_bwd<T, 8>, dim3(ic), dim3(256), bwd_smem<T>(8), s, A, ib, xn, sigma, vu, ru,
+                 rl);
     else
-      k_fb_bwd<T, 4><<<ic, 128, bwd_smem<T>(4), s>>>(A, ib, xn, sigma, vu, ru, rl);
-    RQ_CUDA(cudaGetLastError());
+      launch_pdl(k_fb_bwd<T, 4>, dim3(ic), dim3(128), bwd_smem<T>(4), s, A, ib, xn, sigma, vu, ru,
+                 rl);
     ++P.launches;
   }
 }

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/rigaqep.h"
@@ -43,6 +44,35 @@ struct StreamScope {
   explicit StreamScope(cudaStream_t s) : old(t_stream) { t_stream = s; }
   ~StreamScope() { t_stream = old; }
 };
+
+// Programmatic dependent launch for the kernels of the operator and
+// Gram-Schmidt chain: a kernel launched this way may start while the previous
+// kernel of the stream drains.  Such a kernel calls pdl_trigger() first (its
+// own dependents may then launch once all its blocks have started) and
+// pdl_wait() before it reads anything an earlier kernel of the stream wrote
+// (the wait returns when the previous kernel has completed and its memory is
+// visible; it is a no-op for an ordinary launch).
+template <class... KArgs, class... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RQ_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
 
 // Raises a kernel's dynamic shared memory limit to at least `bytes` (never
 // lowers it, so concurrent callers with different sizes cannot race a launch

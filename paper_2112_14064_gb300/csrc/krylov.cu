@@ -33,6 +33,8 @@ constexpr int kSub = 8;  // lanes per CSR row
 __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const double* Mv,
                           const double* Cv, const double* vu, const double* vl, double s,
                           double* y, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
@@ -50,6 +52,8 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
 
 __global__ void k_spmv(const int32_t* rowptr, const int32_t* col, const double* A, const double* x,
                        double* y, int64_t N) {
+  pdl_trigger();
+  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
@@ -159,12 +163,14 @@ __global__ void __launch_bounds__(256, 1)
   const int rs = (warp & 3) * 32, hh = warp >> 2;
   const int nbox = ncol > 32 ? 2 : 1;
   const uint32_t bytes = (uint32_t)(nbox * 32 * kTileRows * sizeof(double));
+  pdl_trigger();
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
+  pdl_wait();
   if (threadIdx.x == 0 && (int)blockIdx.x < ntile) {
     mbar_expect_tx(&full[0], bytes);
     for (int b = 0; b < nbox; ++b)
@@ -255,6 +261,8 @@ __global__ void __launch_bounds__(256, 1)
 __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double* Mv,
                         const double* zu, const double* zl, int64_t N, double* part,
                         unsigned* counter, double* H, int ldh, int j, double* scal) {
+  pdl_trigger();
+  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
@@ -300,6 +308,8 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
 // z[i] -= sum_c V[i, c] h[c] over the 2 Np rows of column z (ld stride in V)
 __global__ void k_update(const double* V, int64_t ld, int ncol, const double* h, double* z,
                          int64_t rows) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double hs[kMaxKrylov + 1];
   for (int t = threadIdx.x; t <= kMaxKrylov; t += blockDim.x) hs[t] = t < ncol ? h[t] : 0.0;
   __syncthreads();
@@ -320,6 +330,8 @@ __global__ void k_update(const double* V, int64_t ld, int ncol, const double* h,
 }
 
 __global__ void k_scale(double* z, const double* scal, int64_t n) {
+  pdl_trigger();
+  pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) z[i] *= scal[0];
 }
@@ -639,16 +651,15 @@ struct Work {
   void dots(int j, const double* xa, const double* xb) {
     for (int c0 = 0; c0 <= j; c0 += 64) {
       int nc = std::min(64, j + 1 - c0);
-      k_dots_tma<<<nsm, 256, dots_tma_smem(), s>>>(tV, nc, c0, xa, xb, Np, P.part.p, P.counter.p,
-                                                    P.hvec.p, P.H.p, m + 1, j, P.status.p);
-      RQ_CUDA(cudaGetLastError());
+      launch_pdl(k_dots_tma, dim3(nsm), dim3(256), dots_tma_smem(), s, tV, nc, c0, xa, xb, Np,
+                 P.part.p, P.counter.p, P.hvec.p, P.H.p, m + 1, j, P.status.p);
       ++P.launches;
     }
   }
   void spmv(const double* A, const double* x, double* y) {
     int64_t thr = N * kSub;
-    k_spmv<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, A, x, y, N);
-    RQ_CUDA(cudaGetLastError());
+    launch_pdl(k_spmv, dim3((unsigned)((thr + 255) / 256)), dim3(256), 0, s, P.rowptr_n.p,
+               P.col_n.p, A, x, y, N);
     ++n_spmv;
     ++P.launches;
   }
@@ -657,22 +668,22 @@ struct Work {
     double* z = col(c);
     int64_t thr = N * kSub;
     unsigned nb = (unsigned)((thr + 255) / 256);
-    k_bnorm<<<nb, 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, P.Mn.p, z, z + Np, N, P.part.p,
-                               P.counter.p + 1, setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p);
-    RQ_CUDA(cudaGetLastError());
+    launch_pdl(k_bnorm, dim3(nb), dim3(256), 0, s, P.rowptr_n.p, P.col_n.p, P.Mn.p, z,
+               (const double*)(z + Np), N, P.part.p, P.counter.p + 1, setH ? P.H.p : nullptr, m + 1,
+               c - 1, P.scal.p);
     ++n_spmv;
     P.launches += 2;
-    k_scale<<<(unsigned)((2 * Np + 255) / 256), 256, 0, s>>>(z, P.scal.p, 2 * Np);
-    RQ_CUDA(cudaGetLastError());
+    launch_pdl(k_scale, dim3((unsigned)((2 * Np + 255) / 256)), dim3(256), 0, s, z,
+               (const double*)P.scal.p, 2 * Np);
     n_vv += 2;
   }
   void step(int j) {
     double* v = col(j);
     double* r = col(j + 1);
     int64_t thr = N * kSub;
-    k_spmv_op<<<(unsigned)((thr + 255) / 256), 256, 0, s>>>(P.rowptr_n.p, P.col_n.p, P.Mn.p, P.Cn.p,
-                                                            v, v + Np, sigma, P.yop.p, N);
-    RQ_CUDA(cudaGetLastError());
+    launch_pdl(k_spmv_op, dim3((unsigned)((thr + 255) / 256)), dim3(256), 0, s, P.rowptr_n.p,
+               P.col_n.p, P.Mn.p, P.Cn.p, (const double*)v, (const double*)(v + Np), sigma, P.yop.p,
+               N);
     n_spmv += 3;
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     launch_fb(P, P.yop.p, sigma, v, r, r + Np);
@@ -681,8 +692,8 @@ struct Work {
     for (int pass = 0; pass < 2; ++pass) {
       spmv(P.Mn.p, r + Np, P.wvec.p);
       dots(j, r, P.wvec.p);
-      k_update<<<(unsigned)((2 * Np + 255) / 256), 256, 0, s>>>(P.V.p, ld, j + 1, P.hvec.p, r, 2 * Np);
-      RQ_CUDA(cudaGetLastError());
+      launch_pdl(k_update, dim3((unsigned)((2 * Np + 255) / 256)), dim3(256), 0, s,
+                 (const double*)P.V.p, ld, j + 1, (const double*)P.hvec.p, r, 2 * Np);
       ++P.launches;
       n_vv += 4 * (j + 1);
     }
