@@ -594,16 +594,28 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
   const int32_t* st = A.upd_idx + i1.z;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T acc = T(0);
-  pdl_wait();   // zbuf and x come from the previous kernels of the stream
+  // the first block's panel entries were written before this sweep: load them
+  // before waiting for the previous kernels (zbuf and x come from those)
+  T v[32];
+  {
+    const int64_t i = c0 + 32 * warp + lane;
+    const T* pr = P + (i < F ? i : F - 1);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
+  }
+  pdl_wait();
+  bool first = true;
   for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 32 * NW) {
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
     T g = T(0);
     if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
     const T* pr = P + ic;
-    T v[32];
+    if (!first) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
+      for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
+    }
+    first = false;
     gs[warp][lane] = g;
 #pragma unroll
     for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[q];

@@ -34,13 +34,15 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
                           const double* Cv, const double* vu, const double* vl, double s,
                           double* y, int64_t N) {
   pdl_trigger();
-  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
   double acc = 0.0;
+  // the pattern is fixed before the chain starts; the vectors are not
+  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
+  pdl_wait();
   if (r < N) {
-    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) {
+    for (int32_t q = q0 + sub; q < q1; q += kSub) {
       int32_t c = col[q];
       double u = vu[c];
       acc += Mv[q] * (s * u + vl[c]) + Cv[q] * u;
@@ -53,13 +55,14 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
 __global__ void k_spmv(const int32_t* rowptr, const int32_t* col, const double* A, const double* x,
                        double* y, int64_t N) {
   pdl_trigger();
-  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
   double acc = 0.0;
+  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
+  pdl_wait();
   if (r < N) {
-    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) acc += A[q] * x[col[q]];
+    for (int32_t q = q0 + sub; q < q1; q += kSub) acc += A[q] * x[col[q]];
   }
   for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
   if (r < N && sub == 0) y[r] = acc;
@@ -262,13 +265,14 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
                         const double* zu, const double* zl, int64_t N, double* part,
                         unsigned* counter, double* H, int ldh, int j, double* scal) {
   pdl_trigger();
-  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
   int sub = t % kSub;
   double acc = 0.0;
+  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
+  pdl_wait();
   if (r < N) {
-    for (int32_t q = rowptr[r] + sub; q < rowptr[r + 1]; q += kSub) acc += Mv[q] * zl[col[q]];
+    for (int32_t q = q0 + sub; q < q1; q += kSub) acc += Mv[q] * zl[col[q]];
   }
   for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
   double v = 0.0;
