@@ -29,10 +29,11 @@ namespace {
 
 constexpr int kSub = 8;  // lanes per CSR row
 
-// y_i = sum_q M_iq (s vu_q + vl_q) + C_iq vu_q  (fused s M v_u + C v_u + M v_l)
+// y_i = sum_q M_iq w_q + C_iq vu_q with w = s vu + vl (formed by k_scale when
+// the basis vector was normalised): the fused s M v_u + C v_u + M v_l
 __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const double* Mv,
-                          const double* Cv, const double* vu, const double* vl, double s,
-                          double* y, int64_t N) {
+                          const double* Cv, const double* vu, const double* w, double* y,
+                          int64_t N) {
   pdl_trigger();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = t / kSub;
@@ -44,8 +45,7 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
   if (r < N) {
     for (int32_t q = q0 + sub; q < q1; q += kSub) {
       int32_t c = col[q];
-      double u = vu[c];
-      acc += Mv[q] * (s * u + vl[c]) + Cv[q] * u;
+      acc += Mv[q] * w[c] + Cv[q] * vu[c];
     }
   }
   for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
@@ -298,9 +298,12 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sm += ((volatile double*)part)[b];
   r2[threadIdx.x] = sm;
   __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {   // fixed-order tree over the 256 partial sums
+    if (threadIdx.x < o) r2[threadIdx.x] += r2[threadIdx.x + o];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)blockDim.x; ++w) tot += r2[w];
+    double tot = r2[0];
     double nr = sqrt(tot);
     if (H) H[(j + 1) + (int64_t)ldh * j] = nr;
     scal[0] = 1.0 / nr;
@@ -333,11 +336,19 @@ __global__ void k_update(const double* V, int64_t ld, int ncol, const double* h,
   z[i] -= (a0 + a1) + (a2 + a3);
 }
 
-__global__ void k_scale(double* z, const double* scal, int64_t n) {
+// z *= 1 / ||z||_B over the 2 Np rows; also w = s z_u + z_l (rows < Np) for
+// the next operator product
+__global__ void k_scale(double* z, const double* scal, int64_t Np, double s, double* w) {
   pdl_trigger();
   pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) z[i] *= scal[0];
+  if (i < Np) {
+    const double f = scal[0];
+    const double u = z[i] * f, l = z[Np + i] * f;
+    z[i] = u;
+    z[Np + i] = l;
+    w[i] = s * u + l;
+  }
 }
 
 // out[i, t] = sum_{c < m} V[i, c] Q[c, t] (restart / basis change); each
@@ -677,8 +688,8 @@ struct Work {
                c - 1, P.scal.p);
     ++n_spmv;
     P.launches += 2;
-    launch_pdl(k_scale, dim3((unsigned)((2 * Np + 255) / 256)), dim3(256), 0, s, z,
-               (const double*)P.scal.p, 2 * Np);
+    launch_pdl(k_scale, dim3((unsigned)((Np + 255) / 256)), dim3(256), 0, s, z,
+               (const double*)P.scal.p, Np, sigma, P.wop.p);
     n_vv += 2;
   }
   void step(int j) {
@@ -686,8 +697,7 @@ struct Work {
     double* r = col(j + 1);
     int64_t thr = N * kSub;
     launch_pdl(k_spmv_op, dim3((unsigned)((thr + 255) / 256)), dim3(256), 0, s, P.rowptr_n.p,
-               P.col_n.p, P.Mn.p, P.Cn.p, (const double*)v, (const double*)(v + Np), sigma, P.yop.p,
-               N);
+               P.col_n.p, P.Mn.p, P.Cn.p, (const double*)v, (const double*)P.wop.p, P.yop.p, N);
     n_spmv += 3;
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     launch_fb(P, P.yop.p, sigma, v, r, r + Np);
@@ -739,6 +749,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   P.hvec.alloc(kMaxKrylov + 1);
   P.wvec.alloc(Np);
   P.yop.alloc(Np);
+  P.wop.alloc(Np);
   P.scal.alloc(4);
   P.Y.alloc(2 * (size_t)m * kMaxKrylov);
   P.ritz.alloc(1);
