@@ -44,8 +44,9 @@ struct RitzArgs {
 };
 
 struct Smem {
-  double* T;   // m x m, column-major
-  double* Z;   // m x m
+  double* T;   // m x m, column-major, leading dimension ld
+  double* Z;   // m x m, leading dimension ld
+  int ld;      // m rounded up to odd: row-wise lane access hits distinct banks
   double* v;   // Householder vector (m)
   double* wr;  // Ritz values (Schur order)
   double* wi;
@@ -56,8 +57,8 @@ struct Smem {
   struct Refl* refl;  // reflectors of the current QR sweep
 };
 
-#define TT(r, c) S.T[(r) + m * (c)]
-#define ZZ(r, c) S.Z[(r) + m * (c)]
+#define TT(r, c) S.T[(r) + S.ld * (c)]
+#define ZZ(r, c) S.Z[(r) + S.ld * (c)]
 
 // Householder reflector for x[0..n): (I - tau v v^T) x = beta e_0, v[0] = 1.
 // All threads compute it redundantly from the same data.
@@ -81,29 +82,30 @@ __device__ void house(const double* x, int n, double* v, double& tau, double& be
 
 // T columns c0..c0+n-1 (rows r0..r1-1) and Z columns c0..c0+n-1 (all m rows)
 // <- cols P in one pass, one row per thread: keeps all four warps busy.
-__device__ void apply_right_tz(double* T, double* Z, int m, const double* v, double tau, int n,
-                               int c0, int r0, int r1, int lane) {
+__device__ void apply_right_tz(double* T, double* Z, int m, int ld, const double* v, double tau,
+                               int n, int c0, int r0, int r1, int lane) {
   if (tau == 0.0) return;
   int nt = r1 - r0;
   for (int q = lane; q < nt + m; q += NT) {
     double* A = q < nt ? T : Z;
     int r = q < nt ? r0 + q : q - nt;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += v[i] * A[r + m * (c0 + i)];
+    for (int i = 0; i < n; ++i) s += v[i] * A[r + ld * (c0 + i)];
     s *= tau;
-    for (int i = 0; i < n; ++i) A[r + m * (c0 + i)] -= s * v[i];
+    for (int i = 0; i < n; ++i) A[r + ld * (c0 + i)] -= s * v[i];
   }
 }
 
-// rows r0..r0+n-1 of A (ld m) <- P rows, columns c0..c1-1, threads over columns
-__device__ void apply_left(double* A, int m, const double* v, double tau, int n, int r0, int c0,
+// rows r0..r0+n-1 of A (leading dimension ld) <- P rows, columns c0..c1-1,
+// threads over columns
+__device__ void apply_left(double* A, int ld, const double* v, double tau, int n, int r0, int c0,
                            int c1, int lane) {
   if (tau == 0.0) return;
   for (int c = c0 + lane; c < c1; c += NT) {
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += v[i] * A[(r0 + i) + m * c];
+    for (int i = 0; i < n; ++i) s += v[i] * A[(r0 + i) + ld * c];
     s *= tau;
-    for (int i = 0; i < n; ++i) A[(r0 + i) + m * c] -= s * v[i];
+    for (int i = 0; i < n; ++i) A[(r0 + i) + ld * c] -= s * v[i];
   }
 }
 
@@ -258,9 +260,9 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
   }
   __syncthreads();
   for (int q = 0; q < n2; ++q) {
-    apply_left(S.T, m, vh[q], tau[q], n, j, j, m, lane);
+    apply_left(S.T, S.ld, vh[q], tau[q], n, j, j, m, lane);
     __syncthreads();
-    apply_right_tz(S.T, S.Z, m, vh[q], tau[q], n, j, 0, j + n, lane);
+    apply_right_tz(S.T, S.Z, m, S.ld, vh[q], tau[q], n, j, 0, j + n, lane);
     __syncthreads();
   }
   if (lane == 0)
@@ -286,15 +288,14 @@ __device__ double block_sum(double v, double* red, int lane) {
 
 __device__ double frob(Smem& S, int m, int lane) {
   double s = 0.0;
-  for (int i = lane; i < m * m; i += NT) s += S.T[i] * S.T[i];
+  for (int i = lane; i < S.ld * m; i += NT) s += S.T[i] * S.T[i];   // padding rows are 0
   return sqrt(block_sum(s, S.red, lane));
 }
 
-// Real Schur form of the Hessenberg T by Francis double-shift steps.
 // Reflector P = I - tau u u^T with P x = beta e_0 for x of length n (2 or 3):
 // u = x - beta e_0, beta = -sign(x_0) ||x||, and u^T u = 2 beta (beta - x_0),
 // so tau = 2 / u^T u = 1 / (beta (beta - x_0)): one square root, one reciprocal.
-struct Refl {
+struct alignas(16) Refl {
   double u0, u1, u2, tau;
   int pos, n;
 };
@@ -314,9 +315,9 @@ __device__ __forceinline__ void make_refl(double x0, double x1, double x2, int n
   r.tau = rcp_nr(beta * (beta - x0));
 }
 
-// rows pos..pos+n-1 of column c of A (ld m) <- P (rows)
-__device__ __forceinline__ void refl_col(double* A, int m, const Refl& r, int c) {
-  double* a = A + r.pos + m * c;
+// rows pos..pos+n-1 of column c of A (leading dimension ld) <- P (rows)
+__device__ __forceinline__ void refl_col(double* A, int ld, const Refl& r, int c) {
+  double* a = A + r.pos + ld * c;
   double s = r.u0 * a[0] + r.u1 * a[1];
   if (r.n == 3) s += r.u2 * a[2];
   s *= r.tau;
@@ -326,14 +327,14 @@ __device__ __forceinline__ void refl_col(double* A, int m, const Refl& r, int c)
 }
 
 // columns pos..pos+n-1 of row i of A <- (cols) P
-__device__ __forceinline__ void refl_row(double* A, int m, const Refl& r, int i) {
-  double* a = A + i + m * r.pos;
-  double s = r.u0 * a[0] + r.u1 * a[m];
-  if (r.n == 3) s += r.u2 * a[2 * m];
+__device__ __forceinline__ void refl_row(double* A, int ld, const Refl& r, int i) {
+  double* a = A + i + ld * r.pos;
+  double s = r.u0 * a[0] + r.u1 * a[ld];
+  if (r.n == 3) s += r.u2 * a[2 * ld];
   s *= r.tau;
   a[0] -= s * r.u0;
-  a[m] -= s * r.u1;
-  if (r.n == 3) a[2 * m] -= s * r.u2;
+  a[ld] -= s * r.u1;
+  if (r.n == 3) a[2 * ld] -= s * r.u2;
 }
 
 // Real Schur form of the Hessenberg T by Francis double-shift sweeps.
@@ -430,14 +431,14 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
         make_refl(x, y, z, n, r);
         r.pos = kq;
         if (r.tau != 0.0)
-          for (int i = l + wl; i <= min(kq + 3, hi); i += 32) refl_row(S.T, m, r, i);
+          for (int i = l + wl; i <= min(kq + 3, hi); i += 32) refl_row(S.T, S.ld, r, i);
       }
       if (warp < nb && wl == 0) rl[t * nb + warp] = r;
       __syncthreads();
       if (act) {
         int c0 = kq > l ? kq - 1 : l;
         if (r.tau != 0.0)
-          for (int c = c0 + wl; c <= hi; c += 32) refl_col(S.T, m, r, c);
+          for (int c = c0 + wl; c <= hi; c += 32) refl_col(S.T, S.ld, r, c);
         if (kq > l && wl == 0) {
           TT(kq + 1, kq - 1) = 0.0;
           if (r.n == 3) TT(kq + 2, kq - 1) = 0.0;
@@ -453,15 +454,15 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
       if (q < ncol) {
         int c = hi + 1 + q;
         for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_col(S.T, m, rl[t], c);
+          if (rl[t].tau != 0.0) refl_col(S.T, S.ld, rl[t], c);
       } else if (q < ncol + nrow) {
         int i = q - ncol;
         for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_row(S.T, m, rl[t], i);
+          if (rl[t].tau != 0.0) refl_row(S.T, S.ld, rl[t], i);
       } else {
         int i = q - ncol - nrow;
         for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_row(S.Z, m, rl[t], i);
+          if (rl[t].tau != 0.0) refl_row(S.Z, S.ld, rl[t], i);
       }
     }
     __syncthreads();
@@ -486,9 +487,9 @@ __device__ void hessenberg(Smem& S, int m, int lane, int lock) {
     __syncthreads();
     for (int i = lane; i < n; i += NT) S.v[i] = i == 0 ? 1.0 : TT(c + 1 + i, c) * rd;
     __syncthreads();
-    apply_left(S.T, m, S.v, tau, n, c + 1, c, m, lane);
+    apply_left(S.T, S.ld, S.v, tau, n, c + 1, c, m, lane);
     __syncthreads();
-    apply_right_tz(S.T, S.Z, m, S.v, tau, n, c + 1, 0, m, lane);
+    apply_right_tz(S.T, S.Z, m, S.ld, S.v, tau, n, c + 1, 0, m, lane);
     __syncthreads();
     if (lane == 0)
       for (int i = 1; i < n; ++i) TT(c + 1 + i, c) = 0.0;
@@ -521,8 +522,8 @@ struct WarpVec {
 // diagonal 1 x 1 shifts T_ii - lambda and of the 2 x 2 block determinants
 // formed first, in parallel over the lanes, so that the sequential chain per
 // row is a complex multiply and a residual update.
-__device__ void trevc_warp(const double* T, int m, int j, double lr, double li, double smin,
-                           const double* wi, int wl, WarpVec& B) {
+__device__ void trevc_warp(const double* T, int m, int ld, int j, double lr, double li,
+                           double smin, const double* wi, int wl, WarpVec& B) {
   const bool pair = (li != 0.0);
   for (int i = wl; i < m; i += 32) { B.yr[i] = 0.0; B.yi[i] = 0.0; }
   __syncwarp();
@@ -532,9 +533,9 @@ __device__ void trevc_warp(const double* T, int m, int j, double lr, double li, 
     top = j;
   } else {
     if (wl == 0) {
-      B.yr[j] = T[j + m * (j + 1)];
+      B.yr[j] = T[j + ld * (j + 1)];
       B.yi[j] = 0.0;
-      B.yr[j + 1] = lr - T[j + m * j];
+      B.yr[j + 1] = lr - T[j + ld * j];
       B.yi[j + 1] = li;
     }
     top = j + 1;
@@ -542,19 +543,19 @@ __device__ void trevc_warp(const double* T, int m, int j, double lr, double li, 
   __syncwarp();
   for (int r = wl; r < j; r += 32) {
     double ar = 0.0, ai = 0.0;
-    for (int l = j; l <= top; ++l) { ar -= T[r + m * l] * B.yr[l]; ai -= T[r + m * l] * B.yi[l]; }
+    for (int l = j; l <= top; ++l) { ar -= T[r + ld * l] * B.yr[l]; ai -= T[r + ld * l] * B.yi[l]; }
     B.sr[r] = ar;
     B.si[r] = ai;
     // reciprocal of the shifted diagonal (1 x 1 rows) or of the determinant of
     // the shifted 2 x 2 block (stored at its first row)
     if (wi[r] == 0.0) {
-      double dr = T[r + m * r] - lr, di = -li;
+      double dr = T[r + ld * r] - lr, di = -li;
       if (fabs(dr) + fabs(di) < smin) dr = smin;
       cdiv(1.0, 0.0, dr, di, B.dr[r], B.di[r]);
     } else if (wi[r] > 0.0) {
       int i0 = r, i1 = r + 1;
-      double ar2 = T[i0 + m * i0] - lr, ai2 = -li, br = T[i0 + m * i1], cr = T[i1 + m * i0];
-      double dr = T[i1 + m * i1] - lr, di = -li;
+      double ar2 = T[i0 + ld * i0] - lr, ai2 = -li, br = T[i0 + ld * i1], cr = T[i1 + ld * i0];
+      double dr = T[i1 + ld * i1] - lr, di = -li;
       double detr = ar2 * dr - ai2 * di - br * cr, deti = ar2 * di + ai2 * dr;
       if (fabs(detr) + fabs(deti) < smin) detr = smin;
       cdiv(1.0, 0.0, detr, deti, B.dr[r], B.di[r]);
@@ -568,15 +569,15 @@ __device__ void trevc_warp(const double* T, int m, int j, double lr, double li, 
       double yr = s_r * pr - s_i * pi, yi = s_r * pi + s_i * pr;
       if (wl == 0) { B.yr[i] = yr; B.yi[i] = yi; }
       for (int r = wl; r < i; r += 32) {
-        B.sr[r] -= T[r + m * i] * yr;
-        B.si[r] -= T[r + m * i] * yi;
+        B.sr[r] -= T[r + ld * i] * yr;
+        B.si[r] -= T[r + ld * i] * yi;
       }
       __syncwarp();
       i -= 1;
     } else {              // rows i-1, i form a 2 x 2 block
       int i0 = i - 1;
-      double ar = T[i0 + m * i0] - lr, ai = -li, br = T[i0 + m * i], cr = T[i + m * i0];
-      double dr = T[i + m * i] - lr, di = -li;
+      double ar = T[i0 + ld * i0] - lr, ai = -li, br = T[i0 + ld * i], cr = T[i + ld * i0];
+      double dr = T[i + ld * i] - lr, di = -li;
       double s0r = B.sr[i0], s0i = B.si[i0], s1r = B.sr[i], s1i = B.si[i];
       double n0r = s0r * dr - s0i * di - br * s1r, n0i = s0r * di + s0i * dr - br * s1i;
       double n1r = ar * s1r - ai * s1i - cr * s0r, n1i = ar * s1i + ai * s1r - cr * s0i;
@@ -585,8 +586,8 @@ __device__ void trevc_warp(const double* T, int m, int j, double lr, double li, 
       double y1r = n1r * pr - n1i * pi, y1i = n1r * pi + n1i * pr;
       if (wl == 0) { B.yr[i0] = y0r; B.yi[i0] = y0i; B.yr[i] = y1r; B.yi[i] = y1i; }
       for (int r = wl; r < i0; r += 32) {
-        B.sr[r] -= T[r + m * i0] * y0r + T[r + m * i] * y1r;
-        B.si[r] -= T[r + m * i0] * y0i + T[r + m * i] * y1i;
+        B.sr[r] -= T[r + ld * i0] * y0r + T[r + ld * i] * y1r;
+        B.si[r] -= T[r + ld * i0] * y0i + T[r + ld * i] * y1i;
       }
       __syncwarp();
       i -= 2;
@@ -605,9 +606,10 @@ __global__ void k_ritz(RitzArgs R) {
   const int m = R.m;
   const int lane = threadIdx.x;  // thread index in the CTA
   Smem S;
+  S.ld = m | 1;
   S.T = sm;
-  S.Z = S.T + m * m;
-  S.v = S.Z + m * m;
+  S.Z = S.T + S.ld * m;
+  S.v = S.Z + S.ld * m;
   S.wr = S.v + m;
   S.wi = S.wr + m;
   S.red = S.wi + m;
@@ -623,9 +625,9 @@ __global__ void k_ritz(RitzArgs R) {
             wbuf + 6 * m * vw + 3 * m, wbuf + 6 * m * vw + 4 * m, wbuf + 6 * m * vw + 5 * m};
   __shared__ int wcount[NT / 32];
 
-  for (int i = lane; i < m * m; i += NT) {
-    int r = i % m, c = i / m;
-    S.T[i] = R.H[r + (m + 1) * c];
+  for (int i = lane; i < S.ld * m; i += NT) {
+    int r = i % S.ld, c = i / S.ld;
+    S.T[i] = r < m ? R.H[r + (m + 1) * c] : 0.0;
     S.Z[i] = (r == c) ? 1.0 : 0.0;
   }
   const double beta = R.H[m + (m + 1) * (m - 1)];
@@ -710,7 +712,7 @@ __global__ void k_ritz(RitzArgs R) {
       }
       double lr = S.wr[pos], li = S.wi[pos];
       int jstart = (li < 0.0) ? pos - 1 : pos;   // conjugate: start of its block
-      trevc_warp(S.T, m, jstart, lr, fabs(li), smin, S.wi, wl, B);
+      trevc_warp(S.T, m, S.ld, jstart, lr, fabs(li), smin, S.wi, wl, B);
       // y_H = Z y ; estimate uses the last row; norm of y equals norm of Z y
       double nrm = 0.0, lastr = 0.0, lasti = 0.0;
       for (int l = wl; l < m; l += 32) {
@@ -851,7 +853,7 @@ __global__ void k_ritz(RitzArgs R) {
     }
     R.Hnew[i] = v;
   }
-  for (int i = lane; i < m * k; i += NT) R.Q[i] = S.Z[i];
+  for (int i = lane; i < m * k; i += NT) R.Q[i] = ZZ(i % m, i / m);
   if (lane == 0) {
     R.out->k = k;
     R.out->n_lock = nl;
@@ -863,7 +865,7 @@ __global__ void k_ritz(RitzArgs R) {
 }  // namespace
 
 size_t ritz_smem(int m) {
-  return sizeof(double) * (2 * (size_t)m * m + 4 * (size_t)m + NT / 32) + 3 * sizeof(int) * m + 16 +
+  return sizeof(double) * (2 * (size_t)(m | 1) * m + 4 * (size_t)m + NT / 32) + 3 * sizeof(int) * m + 16 +
          sizeof(Refl) * (size_t)kBulges * (size_t)(m + 4 * kBulges) +
          sizeof(double) * 6 * kVecWarps * (size_t)m + sizeof(int) * (size_t)m;
 }
