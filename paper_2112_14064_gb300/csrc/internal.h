@@ -120,7 +120,7 @@ struct DevStatus {
 struct RitzOut {
   int32_t n_conv;       // wanted pairs (first neig) with estimate <= tol
   int32_t k;            // kept dimension after reordering (restart)
-  int32_t fail;         // QR did not converge
+  int32_t fail;         // 1: QR did not converge, 2: a bounded wait between the CTAs ran out
   int32_t sweeps;       // Francis double-shift sweeps of this step
   int32_t n_lock;       // leading Schur columns locked after this restart
   int32_t finished;     // eigenvectors written, no restart data

@@ -797,6 +797,8 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
       RQ_CUDA(cudaEventElapsedTime(&ms, W.rz[0], W.rz[1]));
       W.ritz_ms += ms;
     }
+    if (h_out.fail == 2)
+      throw Error(RIGAQEP_ERR_INTERNAL, "a bounded wait between the Ritz-step CTAs ran out");
     if (h_out.fail) throw Error(RIGAQEP_ERR_INTERNAL, "QR iteration on the projected matrix did not converge");
     qr_sweeps += h_out.sweeps;
     for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] += (double)h_out.phase_cycles[q];

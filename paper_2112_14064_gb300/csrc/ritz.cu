@@ -8,8 +8,9 @@
 // restart keeps the invariant subspace of the wanted Ritz values (Krylov-Schur,
 // Section 4.1.3, which the paper cites without details).
 //
-// One CTA of four warps (one per SM sub-partition, so the FP64 row and column
-// updates use all four FP64 pipes) does the whole step in shared memory:
+// A cluster of three CTAs of four warps each (one warp per SM sub-partition,
+// so the FP64 row and column updates use all four FP64 pipes of an SM).  The
+// first CTA does the whole step in its shared memory:
 //   1. Householder reduction of H_m to Hessenberg form, Z accumulated;
 //   2. Francis double-shift QR to real Schur form T = Z^T H_m Z, 2x2 blocks
 //      standardised (equal diagonal for complex pairs, split when real);
@@ -24,14 +25,27 @@
 //      the spike row are set to zero, so the projected matrix stays block
 //      upper triangular and later steps reduce and iterate only on the
 //      trailing active block (the locked Schur part is left as it is).
+// During step 2 the other two CTAs apply, one sweep behind, the updates that
+// lie outside the active window: the second CTA accumulates Z in its own
+// shared memory, the third updates the rows above and the columns right of
+// the window in the first CTA's T through distributed shared memory.  The
+// first CTA hands each sweep over in a double-buffered batch (its reflectors
+// and the rotations of the 2 x 2 blocks deflated before it) and goes on with
+// the next sweep.
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "nr_math.cuh"
+#include "tma.cuh"
 
 namespace rq {
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
-constexpr int NT = 128;   // threads of the Ritz CTA
+constexpr int NT = 128;   // threads of each Ritz CTA
+constexpr int kRitzCTAs = 3;   // cluster: the Ritz CTA, the Z CTA and the off-window T CTA
+constexpr int kMaxRot = 48;    // rotations per batch (2 x 2 deflations between sweeps)
+constexpr uint32_t kQueueWaitLimit = 1u << 22;   // polls of a batch barrier before giving up
 
 struct RitzArgs {
   const double* H;   // (m+1) x m, column-major, ld = m+1
@@ -54,7 +68,7 @@ struct Smem {
   int* sel;
   int* cflag;  // converged flag of each Schur position
   double* red; // 4 partial sums
-  struct Refl* refl;  // reflectors of the current QR sweep
+  char* batch; // two batches of deferred QR work (BatchHdr, Rot[kMaxRot], Refl[])
 };
 
 #define TT(r, c) S.T[(r) + S.ld * (c)]
@@ -109,6 +123,93 @@ __device__ void apply_left(double* A, int ld, const double* v, double tau, int n
   }
 }
 
+// Deferred QR work handed from the Ritz CTA to the helper CTAs, one batch per
+// sweep: the rotations of the 2 x 2 blocks standardised since the last sweep
+// (applied first, in order), then the sweep's reflectors in (round, bulge)
+// order.
+struct Refl;
+struct BatchHdr {
+  int nrot;          // rotations
+  int sweep;         // 1: reflectors of a sweep on the window [l, hi] follow
+  int l, hi, nb, rounds;
+  int end;           // last batch of the QR iteration
+  int pad;
+};
+struct Rot {         // G = [[c, -s], [s, c]] on rows/columns j, j+1
+  double c, s;
+  int j, pad;
+};
+constexpr size_t kReflOff = (sizeof(BatchHdr) + kMaxRot * sizeof(Rot) + 15) / 16 * 16;
+
+// The Ritz CTA's side of the batch queue.  Two batch buffers live in its
+// shared memory; `full` barriers (one arrival) in each helper CTA, `empty`
+// barriers (one arrival per helper) and `done` in the Ritz CTA.  Every thread
+// keeps the same copy of the counters.
+struct Queue {
+  char* buf;         // batch 0; batch 1 follows at bbytes
+  size_t bbytes;
+  uint64_t* bars;    // [0..1] full, [2..3] empty, [4] done (same offsets in every CTA)
+  int* err;          // shared flag: a bounded wait ran out
+  int bq;            // batch being filled
+  int nrot;          // its rotations so far
+  bool open;         // its buffer has been released by the helpers
+  __device__ BatchHdr* hdr(int b) const { return (BatchHdr*)(buf + (size_t)(b & 1) * bbytes); }
+  __device__ Rot* rot(int b) const { return (Rot*)(buf + (size_t)(b & 1) * bbytes + sizeof(BatchHdr)); }
+  __device__ Refl* refl(int b) const { return (Refl*)(buf + (size_t)(b & 1) * bbytes + kReflOff); }
+};
+
+// Makes the buffer of batch bq writable: its previous batch (bq - 2) has been
+// copied by both helpers.
+__device__ void q_acquire(Queue& Q, int lane) {
+  if (Q.open) return;
+  if (Q.bq >= 2 && lane == 0 &&
+      !mbar_wait_cluster(&Q.bars[2 + (Q.bq & 1)], (uint32_t)(((Q.bq >> 1) - 1) & 1), kQueueWaitLimit))
+    *Q.err = 1;
+  __syncthreads();
+  Q.open = true;
+  Q.nrot = 0;
+}
+
+// Completes batch bq (every thread's writes to it are done) and signals both
+// helpers.
+__device__ void q_publish(Queue& Q, int lane, int sweep, int l, int hi, int nb, int rounds, int end) {
+  __syncthreads();
+  if (lane == 0) {
+    BatchHdr* h = Q.hdr(Q.bq);
+    h->nrot = Q.nrot;
+    h->sweep = sweep;
+    h->l = l;
+    h->hi = hi;
+    h->nb = nb;
+    h->rounds = rounds;
+    h->end = end;
+    h->pad = 0;
+    fence_acq_rel_cluster();
+    for (int r = 1; r < kRitzCTAs; ++r) mbar_arrive_remote(&Q.bars[Q.bq & 1], (uint32_t)r);
+  }
+  ++Q.bq;
+  Q.open = false;
+}
+
+// G applied to the 2 x 2 block at j alone (T_jj..T_j+1,j+1 <- G^T T G); the
+// rows right of it, the columns above it and Z are left to the helpers.
+__device__ void rotate_block(Smem& S, int m, int j, double c, double s, int lane) {
+  __syncthreads();
+  if (lane == 0) {
+    for (int col = j; col <= j + 1; ++col) {
+      double a = TT(j, col), b = TT(j + 1, col);
+      TT(j, col) = c * a + s * b;
+      TT(j + 1, col) = -s * a + c * b;
+    }
+    for (int r = j; r <= j + 1; ++r) {
+      double a = TT(r, j), b = TT(r, j + 1);
+      TT(r, j) = c * a + s * b;
+      TT(r, j + 1) = -s * a + c * b;
+    }
+  }
+  __syncthreads();
+}
+
 // Plane rotation G = [[c, -s], [s, c]] on rows/cols j, j+1: T <- G^T T G, Z <- Z G
 __device__ void rotate(Smem& S, int m, int j, double c, double s, int lane) {
   __syncthreads();
@@ -133,8 +234,10 @@ __device__ void rotate(Smem& S, int m, int j, double c, double s, int lane) {
 
 // Standardise the 2x2 diagonal block at j: split it (exact zero below the
 // diagonal) when its eigenvalues are real, else make its diagonal equal.
-// Returns true when the block stays a complex pair.
-__device__ bool standardize2(Smem& S, int m, int j, int lane) {
+// Returns true when the block stays a complex pair.  With a queue (during the
+// QR iteration) only the block itself is rotated here and the rotation is
+// appended to the open batch for the rest of T and for Z.
+__device__ bool standardize2(Smem& S, int m, int j, int lane, Queue* q = nullptr) {
   double a = TT(j, j), b = TT(j, j + 1), e = TT(j + 1, j), d = TT(j + 1, j + 1);
   if (e == 0.0) return false;
   double hp = 0.5 * (a - d);
@@ -175,7 +278,19 @@ __device__ bool standardize2(Smem& S, int m, int j, int lane) {
     }
     cplx = true;
   }
-  rotate(S, m, j, c, s, lane);
+  if (q) {
+    rotate_block(S, m, j, c, s, lane);
+    if (lane == 0) {
+      Rot* rt = q->rot(q->bq) + q->nrot;
+      rt->c = c;
+      rt->s = s;
+      rt->j = j;
+      rt->pad = 0;
+    }
+    ++q->nrot;
+  } else {
+    rotate(S, m, j, c, s, lane);
+  }
   if (!cplx) {
     if (lane == 0) TT(j + 1, j) = 0.0;
   } else if (lane == 0) {
@@ -355,19 +470,29 @@ __device__ __forceinline__ void refl_row(double* A, int ld, const Refl& r, int i
 // only overlap between bulges (the rows of a bulge behind against the
 // columns of the bulge ahead) sees the ahead bulge's right-hand update before
 // the behind bulge's left-hand update, as in the one-bulge-at-a-time order.
-// A left and a right application of one reflector commute.  Only window
-// entries are updated during the sweep; its reflectors are kept and, after
-// it, applied in (round, bulge) order to the columns right of the window,
-// the rows above it and Z, one column or row per thread, without barriers.
+// A left and a right application of one reflector commute.
+//
+// Only window entries are updated here.  The sweep's reflectors go to the
+// helper CTAs, which apply them, in (round, bulge) order, to the columns
+// right of the window, the rows above it and Z while this CTA runs the next
+// sweep.  That is safe because an entry outside the window of one sweep is
+// outside the window of every later sweep (later windows lie inside it or
+// wholly above it), and the deflation tests read only diagonal and
+// subdiagonal entries, which the helpers never write.
+// Returns 0 when converged, 1 when the sweep limit was reached, 2 when a
+// bounded wait on the helpers ran out.
 constexpr int kBulges = NT / 32;
 constexpr int kVecWarps = NT / 32 < 4 ? NT / 32 : 4;   // warps computing eigenvectors
 constexpr int kBulgeGap = 4;
 
-__device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
+__host__ __device__ inline size_t batch_bytes(int m) {
+  return kReflOff + sizeof(Refl) * (size_t)kBulges * (size_t)(m + 4 * kBulges);
+}
+
+__device__ int francis(Smem& S, int m, int lane, int& sweeps, int lock, Queue& Q) {
   double tn = frob(S, m, lane);
   if (tn == 0.0) tn = 1.0;
-  int hi = m - 1, its = 0, total = 0;
-  Refl* rl = S.refl;
+  int hi = m - 1, its = 0, total = 0, status = 0;
   const int warp = lane >> 5, wl = lane & 31;
   while (hi >= lock) {
     int l = hi;
@@ -382,12 +507,15 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
     __syncthreads();
     if (l == hi) { --hi; its = 0; continue; }
     if (l == hi - 1) {
-      standardize2(S, m, hi - 1, lane);
+      if (Q.open && Q.nrot == kMaxRot) q_publish(Q, lane, 0, 0, 0, 0, 0, 0);
+      q_acquire(Q, lane);
+      if (*Q.err) { status = 2; break; }
+      standardize2(S, m, hi - 1, lane, &Q);
       hi -= 2;
       its = 0;
       continue;
     }
-    if (++total > 40 * m) { sweeps = total; return false; }
+    if (++total > 40 * m) { status = 1; break; }
     ++its;
     const int nw = hi - l + 1;
     const int nb = max(1, min(kBulges, nw / (kBulgeGap + 2)));
@@ -408,6 +536,9 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
         th = TT(p, p) * TT(p + 1, p + 1) - TT(p, p + 1) * TT(p + 1, p);
       }
     }
+    q_acquire(Q, lane);
+    if (*Q.err) { status = 2; break; }
+    Refl* rl = Q.refl(Q.bq);
     const int rounds = (hi - 1 - l) + kBulgeGap * (nb - 1) + 1;
     for (int t = 0; t < rounds; ++t) {
       const int kq = l + t - kBulgeGap * warp;
@@ -446,29 +577,123 @@ __device__ bool francis(Smem& S, int m, int lane, int& sweeps, int lock) {
       }
       __syncthreads();
     }
-    // deferred off-window updates: columns hi+1..m-1 of T (left), rows
-    // 0..l-1 of T and all rows of Z (right), reflectors in (round, bulge) order
-    const int nref = rounds * nb;
-    int ncol = m - 1 - hi, nrow = l;
-    for (int q = lane; q < ncol + nrow + m; q += NT) {
-      if (q < ncol) {
-        int c = hi + 1 + q;
+    q_publish(Q, lane, 1, l, hi, nb, rounds, 0);
+  }
+  // last batch (with any pending rotations), then wait until both helpers
+  // have applied everything and written Z back
+  q_acquire(Q, lane);
+  q_publish(Q, lane, 0, 0, 0, 0, 0, 1);
+  if (lane == 0 && !mbar_wait_cluster(&Q.bars[4], 0, kQueueWaitLimit)) *Q.err = 1;
+  __syncthreads();
+  if (*Q.err) status = 2;
+  sweeps = total;
+  return status;
+}
+
+// Helper CTA (cluster rank 1: Z, rank 2: T outside the window) of the QR
+// iteration: takes the batches in order, copies each into its own shared
+// memory (releasing the buffer), and applies it.  Rank 1 copies Z from the
+// Ritz CTA before the first batch and writes it back after the last.
+__device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int m = R.m, ld = S.ld, lane = threadIdx.x;
+  const int maxref = kBulges * (m + 4 * kBulges);
+  const char* rbuf = cl.map_shared_rank(Q.buf, 0);
+  double* T0 = cl.map_shared_rank(S.T, 0);
+  double* Z0 = cl.map_shared_rank(S.Z, 0);
+  Rot* lrot = Q.rot(0);     // this CTA's copy of the current batch
+  Refl* lrl = Q.refl(0);
+  int err = 0;
+  for (int b = 0;; ++b) {
+    if (lane == 0)
+      *Q.err = mbar_wait_cluster(&Q.bars[b & 1], (uint32_t)((b >> 1) & 1), kQueueWaitLimit) ? 0 : 1;
+    __syncthreads();
+    if (*Q.err) { err = 1; break; }
+    fence_acq_rel_cluster();
+    const char* src = rbuf + (size_t)(b & 1) * Q.bbytes;
+    const BatchHdr h = *(const BatchHdr*)src;
+    // entries are checked against the matrix so that no access can leave it
+    const int nrot = min(max(h.nrot, 0), kMaxRot);
+    const int nref = h.sweep ? min(max(h.rounds * h.nb, 0), maxref) : 0;
+    const int l = min(max(h.l, 0), m - 1), hi = min(max(h.hi, l), m - 1);
+    for (int q = lane; q < nrot; q += NT) {
+      Rot rt = ((const Rot*)(src + sizeof(BatchHdr)))[q];
+      if (rt.j < 0 || rt.j > m - 2) { rt.c = 1.0; rt.s = 0.0; rt.j = 0; }
+      lrot[q] = rt;
+    }
+    for (int q = lane; q < nref; q += NT) {
+      Refl r = ((const Refl*)(src + kReflOff))[q];
+      if (r.n < 2 || r.n > 3 || r.pos < 0 || r.pos + r.n > m) { r.tau = 0.0; r.n = 2; r.pos = 0; }
+      lrl[q] = r;
+    }
+    if (rank == 1 && b == 0)
+      for (int i = lane; i < ld * m; i += NT) S.Z[i] = Z0[i];
+    __syncthreads();
+    if (lane == 0) mbar_arrive_remote(&Q.bars[2 + (b & 1)], 0);
+    if (rank == 1) {
+      // Z <- Z G for each rotation, then Z <- Z P for each reflector; one row per thread
+      for (int i = lane; i < m; i += NT) {
+        for (int q = 0; q < nrot; ++q) {
+          const int j = lrot[q].j;
+          const double c = lrot[q].c, sn = lrot[q].s;
+          double a = S.Z[i + ld * j], bb = S.Z[i + ld * (j + 1)];
+          S.Z[i + ld * j] = c * a + sn * bb;
+          S.Z[i + ld * (j + 1)] = -sn * a + c * bb;
+        }
         for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_col(S.T, S.ld, rl[t], c);
-      } else if (q < ncol + nrow) {
-        int i = q - ncol;
-        for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_row(S.T, S.ld, rl[t], i);
-      } else {
-        int i = q - ncol - nrow;
-        for (int t = 0; t < nref; ++t)
-          if (rl[t].tau != 0.0) refl_row(S.Z, S.ld, rl[t], i);
+          if (lrl[t].tau != 0.0) refl_row(S.Z, ld, lrl[t], i);
+      }
+    } else {
+      // rotations: rows j, j+1 right of the block (from the left), columns
+      // j, j+1 above it (from the right)
+      for (int q = 0; q < nrot; ++q) {
+        const int j = lrot[q].j;
+        const double c = lrot[q].c, sn = lrot[q].s;
+        const int nc = m - j - 2;
+        for (int u = lane; u < nc + j; u += NT) {
+          double *pa, *pb;
+          if (u < nc) {
+            const int col = j + 2 + u;
+            pa = T0 + j + ld * col;
+            pb = pa + 1;
+          } else {
+            pa = T0 + (u - nc) + ld * j;
+            pb = pa + ld;
+          }
+          double a = *pa, bb = *pb;
+          *pa = c * a + sn * bb;
+          *pb = -sn * a + c * bb;
+        }
+        __syncthreads();
+      }
+      // the sweep: columns right of the window (rows l..hi, from the left)
+      // and rows above it (columns l..hi, from the right)
+      const int ncol = m - 1 - hi, nrow = l;
+      for (int u = lane; u < ncol + nrow; u += NT) {
+        if (u < ncol) {
+          const int c = hi + 1 + u;
+          for (int t = 0; t < nref; ++t)
+            if (lrl[t].tau != 0.0) refl_col(T0, ld, lrl[t], c);
+        } else {
+          const int i = u - ncol;
+          for (int t = 0; t < nref; ++t)
+            if (lrl[t].tau != 0.0) refl_row(T0, ld, lrl[t], i);
+        }
       }
     }
     __syncthreads();
+    if (h.end) break;
   }
-  sweeps = total;
-  return true;
+  if (rank == 1 && !err)
+    for (int i = lane; i < ld * m; i += NT) Z0[i] = S.Z[i];
+  fence_acq_rel_cluster();
+  __syncthreads();
+  if (lane == 0) {
+    if (err) *cl.map_shared_rank(Q.err, 0) = 1;
+    fence_acq_rel_cluster();
+    mbar_arrive_remote(&Q.bars[4], 0);
+  }
 }
 
 __device__ void hessenberg(Smem& S, int m, int lane, int lock) {
@@ -601,11 +826,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__global__ void k_ritz(RitzArgs R) {
-  extern __shared__ double sm[];
-  const int m = R.m;
-  const int lane = threadIdx.x;  // thread index in the CTA
-  Smem S;
+// Shared-memory layout, the same in every CTA of the cluster (the helpers
+// address the Ritz CTA's T, Z and batches at their own offsets).
+__device__ void ritz_layout(double* sm, int m, Smem& S, double*& wbuf, int*& wlist) {
   S.ld = m | 1;
   S.T = sm;
   S.Z = S.T + S.ld * m;
@@ -616,9 +839,15 @@ __global__ void k_ritz(RitzArgs R) {
   S.rank = (int*)(S.red + NT / 32);
   S.sel = S.rank + m;
   S.cflag = S.sel + m;
-  S.refl = (Refl*)(((uintptr_t)(S.cflag + m) + 15) & ~(uintptr_t)15);
-  double* wbuf = (double*)(S.refl + kBulges * (m + 4 * kBulges));
-  int* wlist = (int*)(wbuf + 6 * kVecWarps * m);
+  S.batch = (char*)(((uintptr_t)(S.cflag + m) + 15) & ~(uintptr_t)15);
+  wbuf = (double*)(S.batch + 2 * batch_bytes(m));
+  wlist = (int*)(wbuf + 6 * kVecWarps * m);
+}
+
+// The Ritz CTA (cluster rank 0): steps 1-6.
+__device__ void ritz_main(const RitzArgs& R, Smem& S, Queue& Q, double* wbuf, int* wlist) {
+  const int m = R.m;
+  const int lane = threadIdx.x;  // thread index in the CTA
   const int warp = lane >> 5, wl = lane & 31;
   const int vw = warp < kVecWarps ? warp : 0;
   WarpVec B{wbuf + 6 * m * vw,         wbuf + 6 * m * vw + m, wbuf + 6 * m * vw + 2 * m,
@@ -637,9 +866,18 @@ __global__ void k_ritz(RitzArgs R) {
   hessenberg(S, m, lane, R.lock);
   t_ph[1] = clock64();
   int sweeps = 0;
-  bool ok = francis(S, m, lane, sweeps, R.lock);
+  const int qr_status = francis(S, m, lane, sweeps, R.lock, Q);
   t_ph[2] = clock64();
   __syncthreads();
+  if (qr_status == 2) {   // the helpers' results are incomplete: report and stop
+    if (lane == 0) {
+      R.out->fail = 2;
+      R.out->finished = 1;
+      R.out->sweeps = sweeps;
+    }
+    return;
+  }
+  const bool ok = qr_status == 0;
   // eigenvalues in Schur order
   if (lane == 0) {
     int pos = 0;
@@ -862,12 +1100,40 @@ __global__ void k_ritz(RitzArgs R) {
   }
 }
 
+// One cluster of kRitzCTAs CTAs.  Every wait inside is bounded except the
+// two cluster barriers, which every CTA reaches on every path.
+__global__ void __launch_bounds__(NT) k_ritz(RitzArgs R) {
+  extern __shared__ double sm[];
+  __shared__ uint64_t qbar[5];
+  __shared__ int qerr;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  if (threadIdx.x == 0) {
+    qerr = 0;
+    mbar_init(&qbar[0], 1);                 // full: the Ritz CTA arrives
+    mbar_init(&qbar[1], 1);
+    for (int i = 2; i < 5; ++i) mbar_init(&qbar[i], kRitzCTAs - 1);   // empty, done: each helper
+    mbar_fence_init();
+  }
+  cl.sync();   // every barrier is initialised before any CTA arrives on it
+  Smem S;
+  double* wbuf;
+  int* wlist;
+  ritz_layout(sm, R.m, S, wbuf, wlist);
+  Queue Q{S.batch, batch_bytes(R.m), qbar, &qerr, 0, 0, false};
+  if (rank == 0)
+    ritz_main(R, S, Q, wbuf, wlist);
+  else
+    ritz_helper(R, rank, S, Q);
+  cl.sync();   // no CTA leaves while another may still address its shared memory
+}
+
 }  // namespace
 
 size_t ritz_smem(int m) {
   return sizeof(double) * (2 * (size_t)(m | 1) * m + 4 * (size_t)m + NT / 32) + 3 * sizeof(int) * m + 16 +
-         sizeof(Refl) * (size_t)kBulges * (size_t)(m + 4 * kBulges) +
-         sizeof(double) * 6 * kVecWarps * (size_t)m + sizeof(int) * (size_t)m;
+         2 * batch_bytes(m) + sizeof(double) * 6 * kVecWarps * (size_t)m + sizeof(int) * (size_t)m;
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
@@ -875,8 +1141,19 @@ void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* o
   RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol};
   size_t smem = ritz_smem(m);
   smem_at_least((const void*)k_ritz, smem);
-  k_ritz<<<1, NT, smem, s>>>(R);
-  RQ_CUDA(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kRitzCTAs);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kRitzCTAs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RQ_CUDA(cudaLaunchKernelEx(&cfg, k_ritz, R));
 }
 
 }  // namespace rq

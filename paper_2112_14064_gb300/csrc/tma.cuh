@@ -1,6 +1,7 @@
 // Tensor Memory Access (TMA) tiles for the tall-skinny Krylov-basis kernels:
 // a 2-D tensor map over a column-major FP64 matrix, bulk tensor copies into
-// shared memory that complete on an mbarrier, and bounded waits.
+// shared memory that complete on an mbarrier, and bounded waits; barriers
+// that the CTAs of a cluster arrive on across their shared memories.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -53,6 +54,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// --- barriers between the CTAs of a cluster ------------------------------
+
+// Orders this thread's earlier shared and global accesses, and those it has
+// observed, before its later ones for every thread of the cluster.
+__device__ __forceinline__ void fence_acq_rel_cluster() {
+  asm volatile("fence.acq_rel.cluster;" ::: "memory");
+}
+
+// Arrives (release, cluster scope) on the barrier at the same shared-memory
+// offset as `bar` in the CTA of cluster rank `rank`.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(bar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+
+// Waits (acquire, cluster scope) for phase `parity` of a barrier of this CTA
+// that other CTAs of the cluster arrive on; gives up after `limit` polls and
+// returns false.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < limit; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
         : "r"(smem_addr(bar)), "r"(parity)
