@@ -590,6 +590,66 @@ __device__ int francis(Smem& S, int m, int lane, int& sweeps, int lock, Queue& Q
   return status;
 }
 
+// A helper's copy of a reflector, rescaled to a unit leading entry:
+// P = I - tau u u^T = I - tv v v^T with v = u / u_0, tv = tau u_0^2, and
+// w = tv v, so that applying P to a 3-vector a is s = a_0 + v_1 a_1 + v_2 a_2,
+// a -= s [tv, w_1, w_2]: five FP64 instructions instead of seven.  (The Ritz
+// CTA keeps the u form: there the product u^T a can start before tau is
+// known, which shortens the latency chain of each bulge-chase round.)
+struct alignas(16) HRefl {
+  double v1, v2, tv, w1, w2;
+  int pos, n;   // n = 0: skip
+};
+static_assert(sizeof(HRefl) == sizeof(Refl), "a helper's copy reuses the batch layout");
+
+// Applies the reflectors rl[0..nref) in order to the strided vector x[k st]
+// (a row of a column-major matrix when st = ld, a column when st = 1), each
+// to its entries pos..pos+n-1; entries with n = 0 are skipped.  The next
+// reflector's entries are loaded before the current one is applied, so that
+// the load latency (distributed shared memory for the T helper) overlaps the
+// FP64 chain; an entry that both touch is taken from the registers.
+__device__ void apply_seq(double* x, int st, const HRefl* rl, int nref) {
+  int t = 0;
+  while (t < nref && rl[t].n == 0) ++t;
+  if (t >= nref) return;
+  HRefl r = rl[t];
+  double a0 = x[r.pos * st], a1 = x[(r.pos + 1) * st], a2 = r.n == 3 ? x[(r.pos + 2) * st] : 0.0;
+  for (;;) {
+    int tn = t + 1;
+    while (tn < nref && rl[tn].n == 0) ++tn;
+    const bool more = tn < nref;
+    HRefl q;
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+    if (more) {
+      q = rl[tn];
+      b0 = x[q.pos * st];
+      b1 = x[(q.pos + 1) * st];
+      if (q.n == 3) b2 = x[(q.pos + 2) * st];
+    }
+    double sd = fma(r.v1, a1, a0);
+    if (r.n == 3) sd = fma(r.v2, a2, sd);
+    a0 = fma(-r.tv, sd, a0);
+    a1 = fma(-r.w1, sd, a1);
+    x[r.pos * st] = a0;
+    x[(r.pos + 1) * st] = a1;
+    if (r.n == 3) {
+      a2 = fma(-r.w2, sd, a2);
+      x[(r.pos + 2) * st] = a2;
+    }
+    if (!more) return;
+    // q's entry k is r's entry k + d
+    const int d = q.pos - r.pos;
+    b0 = d == 0 ? a0 : d == 1 ? a1 : (d == 2 && r.n == 3) ? a2 : b0;
+    b1 = d == -1 ? a0 : d == 0 ? a1 : (d == 1 && r.n == 3) ? a2 : b1;
+    b2 = d == -2 ? a0 : d == -1 ? a1 : (d == 0 && r.n == 3) ? a2 : b2;
+    a0 = b0;
+    a1 = b1;
+    a2 = b2;
+    r = q;
+    t = tn;
+  }
+}
+
 // Helper CTA (cluster rank 1: Z, rank 2: T outside the window) of the QR
 // iteration: takes the batches in order, copies each into its own shared
 // memory (releasing the buffer), and applies it.  Rank 1 copies Z from the
@@ -603,7 +663,7 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
   double* T0 = cl.map_shared_rank(S.T, 0);
   double* Z0 = cl.map_shared_rank(S.Z, 0);
   Rot* lrot = Q.rot(0);     // this CTA's copy of the current batch
-  Refl* lrl = Q.refl(0);
+  HRefl* lrl = (HRefl*)Q.refl(0);   // same size as Refl
   int err = 0;
   for (int b = 0;; ++b) {
     if (lane == 0)
@@ -623,9 +683,26 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
       lrot[q] = rt;
     }
     for (int q = lane; q < nref; q += NT) {
-      Refl r = ((const Refl*)(src + kReflOff))[q];
-      if (r.n < 2 || r.n > 3 || r.pos < 0 || r.pos + r.n > m) { r.tau = 0.0; r.n = 2; r.pos = 0; }
-      lrl[q] = r;
+      const Refl r = ((const Refl*)(src + kReflOff))[q];
+      HRefl hr;
+      // n = 0 marks an entry to skip: an inactive bulge, a zero reflector,
+      // or (never in a correct batch) one that would leave the matrix.
+      // A nonzero reflector has |u_0| = |x_0| + ||x|| > 0.
+      if (r.n < 2 || r.n > 3 || r.pos < 0 || r.pos + r.n > m || !(r.tau != 0.0) || !(r.u0 != 0.0)) {
+        hr.v1 = hr.v2 = hr.tv = hr.w1 = hr.w2 = 0.0;
+        hr.n = 0;
+        hr.pos = 0;
+      } else {
+        const double ru = 1.0 / r.u0;
+        hr.v1 = r.u1 * ru;
+        hr.v2 = r.n == 3 ? r.u2 * ru : 0.0;
+        hr.tv = r.tau * r.u0 * r.u0;
+        hr.w1 = hr.tv * hr.v1;
+        hr.w2 = hr.tv * hr.v2;
+        hr.n = r.n;
+        hr.pos = r.pos;
+      }
+      lrl[q] = hr;
     }
     if (rank == 1 && b == 0)
       for (int i = lane; i < ld * m; i += NT) S.Z[i] = Z0[i];
@@ -641,8 +718,7 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
           S.Z[i + ld * j] = c * a + sn * bb;
           S.Z[i + ld * (j + 1)] = -sn * a + c * bb;
         }
-        for (int t = 0; t < nref; ++t)
-          if (lrl[t].tau != 0.0) refl_row(S.Z, ld, lrl[t], i);
+        apply_seq(S.Z + i, ld, lrl, nref);
       }
     } else {
       // rotations: rows j, j+1 right of the block (from the left), columns
@@ -671,15 +747,10 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
       // and rows above it (columns l..hi, from the right)
       const int ncol = m - 1 - hi, nrow = l;
       for (int u = lane; u < ncol + nrow; u += NT) {
-        if (u < ncol) {
-          const int c = hi + 1 + u;
-          for (int t = 0; t < nref; ++t)
-            if (lrl[t].tau != 0.0) refl_col(T0, ld, lrl[t], c);
-        } else {
-          const int i = u - ncol;
-          for (int t = 0; t < nref; ++t)
-            if (lrl[t].tau != 0.0) refl_row(T0, ld, lrl[t], i);
-        }
+        if (u < ncol)
+          apply_seq(T0 + ld * (hi + 1 + u), 1, lrl, nref);
+        else
+          apply_seq(T0 + (u - ncol), ld, lrl, nref);
       }
     }
     __syncthreads();
