@@ -664,6 +664,13 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
   double* Z0 = cl.map_shared_rank(S.Z, 0);
   Rot* lrot = Q.rot(0);     // this CTA's copy of the current batch
   HRefl* lrl = (HRefl*)Q.refl(0);   // same size as Refl
+  // rank 2 works on its own copy of the entries outside the window: taken
+  // from the Ritz CTA when a batch first touches them (own = 1), written
+  // back at the end; its T and Z areas hold the copy and the flags
+  double* Tl = S.T;
+  unsigned char* own = (unsigned char*)S.Z;
+  if (rank == 2)
+    for (int e = lane; e < ld * m; e += NT) own[e] = 0;
   int err = 0;
   for (int b = 0;; ++b) {
     if (lane == 0)
@@ -721,6 +728,27 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
         apply_seq(S.Z + i, ld, lrl, nref);
       }
     } else {
+      // take over the entries this batch touches that the Ritz CTA has not
+      // handed over yet (they never return to its window)
+      for (int q = 0; q < nrot; ++q) {
+        const int j = lrot[q].j, nc = m - j - 2;
+        for (int u = lane; u < nc + j; u += NT) {
+          const int e = u < nc ? j + ld * (j + 2 + u) : (u - nc) + ld * j;
+          const int e2 = u < nc ? e + 1 : e + ld;
+          if (!own[e]) { Tl[e] = T0[e]; own[e] = 1; }
+          if (!own[e2]) { Tl[e2] = T0[e2]; own[e2] = 1; }
+        }
+      }
+      if (h.sweep) {
+        const int nw = hi - l + 1;
+        const int cr = l * nw, cc = nw * (m - 1 - hi);
+        for (int u = lane; u < cr + cc; u += NT) {
+          const int e = u < cr ? (u % l) + ld * (l + u / l)
+                               : (l + (u - cr) % nw) + ld * (hi + 1 + (u - cr) / nw);
+          if (!own[e]) { Tl[e] = T0[e]; own[e] = 1; }
+        }
+      }
+      __syncthreads();
       // rotations: rows j, j+1 right of the block (from the left), columns
       // j, j+1 above it (from the right)
       for (int q = 0; q < nrot; ++q) {
@@ -731,10 +759,10 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
           double *pa, *pb;
           if (u < nc) {
             const int col = j + 2 + u;
-            pa = T0 + j + ld * col;
+            pa = Tl + j + ld * col;
             pb = pa + 1;
           } else {
-            pa = T0 + (u - nc) + ld * j;
+            pa = Tl + (u - nc) + ld * j;
             pb = pa + ld;
           }
           double a = *pa, bb = *pb;
@@ -748,9 +776,9 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
       const int ncol = m - 1 - hi, nrow = l;
       for (int u = lane; u < ncol + nrow; u += NT) {
         if (u < ncol)
-          apply_seq(T0 + ld * (hi + 1 + u), 1, lrl, nref);
+          apply_seq(Tl + ld * (hi + 1 + u), 1, lrl, nref);
         else
-          apply_seq(T0 + (u - ncol), ld, lrl, nref);
+          apply_seq(Tl + (u - ncol), ld, lrl, nref);
       }
     }
     __syncthreads();
@@ -758,6 +786,9 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
   }
   if (rank == 1 && !err)
     for (int i = lane; i < ld * m; i += NT) Z0[i] = S.Z[i];
+  if (rank == 2 && !err)
+    for (int e = lane; e < ld * m; e += NT)
+      if (own[e]) T0[e] = Tl[e];
   fence_acq_rel_cluster();
   __syncthreads();
   if (lane == 0) {
