@@ -415,19 +415,26 @@ struct alignas(16) Refl {
   int pos, n;
 };
 
+// The tests and the sign choice are integer operations on the bits (an FP64
+// compare would cost a 64-cycle FP64 instruction on the round's critical
+// chain).  n = 0 marks the identity (x_1 = x_2 = 0).
 __device__ __forceinline__ void make_refl(double x0, double x1, double x2, int n, Refl& r) {
-  double sg = x1 * x1 + (n == 3 ? x2 * x2 : 0.0);
-  r.n = n;
-  if (sg == 0.0) {
-    r.u0 = 1.0; r.u1 = 0.0; r.u2 = 0.0; r.tau = 0.0;
+  if (n == 2) x2 = 0.0;
+  const double q = fma(x0, x0, fma(x2, x2, x1 * x1));
+  const long long b1 = __double_as_longlong(x1) << 1, b2 = __double_as_longlong(x2) << 1;
+  if ((b1 | b2) == 0 || (__double_as_longlong(q) << 1) == 0) {
+    r.u0 = 1.0; r.u1 = 0.0; r.u2 = 0.0; r.tau = 0.0; r.n = 0;
     return;
   }
-  double nr = sqrt_nr(x0 * x0 + sg);
-  double beta = x0 <= 0.0 ? nr : -nr;
+  r.n = n;
+  const double nr = sqrt_nr(q);
+  // beta = -sign(x0) ||x|| (beta = ||x|| for x0 = +-0)
+  const long long flip = __double_as_longlong(x0) > 0 ? (long long)0x8000000000000000ULL : 0LL;
+  const double beta = __longlong_as_double(__double_as_longlong(nr) ^ flip);
   r.u0 = x0 - beta;
   r.u1 = x1;
-  r.u2 = n == 3 ? x2 : 0.0;
-  r.tau = rcp_nr(beta * (beta - x0));
+  r.u2 = x2;
+  r.tau = rcp_nr(-beta * r.u0);   // 1 / (beta (beta - x0))
 }
 
 // rows pos..pos+n-1 of column c of A (leading dimension ld) <- P (rows)
@@ -561,14 +568,14 @@ __device__ int francis(Smem& S, int m, int lane, int& sweeps, int lock, Queue& Q
         }
         make_refl(x, y, z, n, r);
         r.pos = kq;
-        if (r.tau != 0.0)
+        if (r.n != 0)
           for (int i = l + wl; i <= min(kq + 3, hi); i += 32) refl_row(S.T, S.ld, r, i);
       }
       if (warp < nb && wl == 0) rl[t * nb + warp] = r;
       __syncthreads();
       if (act) {
         int c0 = kq > l ? kq - 1 : l;
-        if (r.tau != 0.0)
+        if (r.n != 0)
           for (int c = c0 + wl; c <= hi; c += 32) refl_col(S.T, S.ld, r, c);
         if (kq > l && wl == 0) {
           TT(kq + 1, kq - 1) = 0.0;
