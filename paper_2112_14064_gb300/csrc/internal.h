@@ -181,7 +181,7 @@ struct Problem {
   std::vector<int32_t> fwd_lvl, bwd_lvl;  // work items of each level
   std::vector<int32_t> fwd_rc;            // 32-row chunks per forward item, per level
   // Krylov workspace
-  DBuf<double> V, Vtmp, H, part, hvec, wvec, yop, wop, scal, Y;
+  DBuf<double> V, Vtmp, H, part, hvec, yop, wop, scal, Y;
   DBuf<RitzOut> ritz;
   DBuf<unsigned> counter;       // last-block-done counters of the fused reductions
   DBuf<DevStatus> status;

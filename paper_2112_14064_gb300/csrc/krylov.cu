@@ -9,8 +9,12 @@
 // v_{j+1} = r / h_{j+1,j}.  Ritz step and truncation: ritz.cu.
 //
 // The Krylov basis lives in the nested-dissection order of the factor, so
-// no permutation is needed per step: V is (2 Np) x (m+1), column-major,
-// column c = [v_u (Np); v_l (Np)] with Np = N rounded up to 32 (zero pad).
+// no permutation is needed per step: V is (3 Np) x (m+1), column-major,
+// column c = [v_u (Np); v_l (Np); w = M v_l (Np)] with Np = N rounded up to
+// a whole TMA tile of rows (zero pad).  Keeping the B-image w of every basis
+// vector (formed by the B-norm kernel, which computes M v_l anyway) turns the
+// projections into h = V_u^T r_u + W^T r_l (M is symmetric), so that neither
+// Gram-Schmidt pass needs a sparse product; the restart rotates W with V.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -52,93 +56,9 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
   if (r < N && sub == 0) y[r] = acc;
 }
 
-__global__ void k_spmv(const int32_t* rowptr, const int32_t* col, const double* A, const double* x,
-                       double* y, int64_t N) {
-  pdl_trigger();
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t r = t / kSub;
-  int sub = t % kSub;
-  double acc = 0.0;
-  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
-  pdl_wait();
-  if (r < N) {
-    for (int32_t q = q0 + sub; q < q1; q += kSub) acc += A[q] * x[col[q]];
-  }
-  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
-  if (r < N && sub == 0) y[r] = acc;
-}
-
-// h[c] = sum_i V[i, c] x(i) over the 2 Np rows, x(i) = xa[i] (i < Np) or
-// xb[i - Np]; then H[c, j] += h[c].  Per-thread accumulators for all 64
-// columns, a butterfly transpose-reduction inside each warp (lane l ends with
-// columns 2l, 2l+1), a sum over the block's warps, and a fixed-order sum over
-// blocks by the last block to finish (counter in global memory).
-__global__ void __launch_bounds__(128) k_dots(const double* V, int64_t ld, int ncol,
-                                               const double* xa, const double* xb, int64_t Np,
-                                               double* part, unsigned* counter, double* h,
-                                               double* H, int ldh, int j, int c_off) {
-  double acc[64];
-#pragma unroll
-  for (int c = 0; c < 64; ++c) acc[c] = 0.0;
-  int64_t rows = 2 * Np;
-  // columns in warp-uniform chunks of 8 with unconditional (clamped) loads
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double x = i < Np ? xa[i] : xb[i - Np];
-    const double* vr = V + i;
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 8) {
-      if (c0 < ncol) {
-        double v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = vr[ld * min(c0 + q, ncol - 1)];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[c0 + q] += (c0 + q < ncol ? v[q] : 0.0) * x;
-      }
-    }
-  }
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16, len = 64; o > 0; o >>= 1, len >>= 1) {
-    bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < len / 2; ++i) {
-      double send = up ? acc[i] : acc[i + len / 2];
-      double keep = up ? acc[i + len / 2] : acc[i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  __shared__ double red[4][64];
-  __shared__ bool last;
-  red[warp][2 * lane] = acc[0];
-  red[warp][2 * lane + 1] = acc[1];
-  __syncthreads();
-  if (threadIdx.x < 64) {
-    double sm = red[0][threadIdx.x] + red[1][threadIdx.x] + red[2][threadIdx.x] + red[3][threadIdx.x];
-    part[blockIdx.x * 64 + threadIdx.x] = sm;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  // 128 threads: column c = tid & 63, half = tid >> 6 sums every other block
-  int c = threadIdx.x & 63, half = threadIdx.x >> 6;
-  double sm = 0.0;
-  for (int b = half; b < (int)gridDim.x; b += 2) sm += ((volatile double*)part)[b * 64 + c];
-  __syncthreads();
-  red[half][c] = sm;
-  __syncthreads();
-  if (threadIdx.x < ncol) {
-    double v = red[0][threadIdx.x] + red[1][threadIdx.x];
-    h[c_off + threadIdx.x] = v;
-    H[c_off + threadIdx.x + (int64_t)ldh * j] += v;
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
-
-// The same dot products with the basis streamed through shared memory by
+// h[c] = sum_i B(i, c) x(i) over the 2 Np rows of [V_u; W] (B-images of the
+// basis vectors), x(i) = xa[i] (i < Np) or xb[i - Np]; then H[c, j] += h[c].
+// The basis is streamed through shared memory by
 // TMA: tiles of 128 rows x up to 64 columns (two 128 x 32 boxes), two stages,
 // the next tile's copy in flight while the current one is used.  Warp w
 // takes rows 32 (w mod 4) .. +31 of a tile and column half w / 4; each lane
@@ -174,11 +94,12 @@ __global__ void __launch_bounds__(256, 1)
   }
   __syncthreads();
   pdl_wait();
+  // tile t covers rows t*128.. of [V_u; W]: V rows 0..Np-1, then 2Np..3Np-1
+  auto vrow = [Np](int t) { const int64_t r = (int64_t)t * kTileRows; return (int)(r < Np ? r : r + Np); };
   if (threadIdx.x == 0 && (int)blockIdx.x < ntile) {
     mbar_expect_tx(&full[0], bytes);
     for (int b = 0; b < nbox; ++b)
-      tma_load_2d(stage0 + b * 32 * kTileRows, &tV, (int)blockIdx.x * kTileRows, c0 + 32 * b,
-                  &full[0]);
+      tma_load_2d(stage0 + b * 32 * kTileRows, &tV, vrow((int)blockIdx.x), c0 + 32 * b, &full[0]);
   }
   double acc[32];
 #pragma unroll
@@ -195,7 +116,7 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0 && tn < ntile) {
       mbar_expect_tx(&full[s ^ 1], bytes);
       for (int b = 0; b < nbox; ++b)
-        tma_load_2d(nxt + b * 32 * kTileRows, &tV, tn * kTileRows, c0 + 32 * b, &full[s ^ 1]);
+        tma_load_2d(nxt + b * 32 * kTileRows, &tV, vrow(tn), c0 + 32 * b, &full[s ^ 1]);
     }
     const int64_t i = (int64_t)t * kTileRows + rs + lane;
     const double x = i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0);
@@ -262,7 +183,7 @@ __global__ void __launch_bounds__(256, 1)
 // per row); the last block sets nrm = sqrt(sum), H[j+1, j] = nrm (if H),
 // scal = {1/nrm, nrm}.
 __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double* Mv,
-                        const double* zu, const double* zl, int64_t N, double* part,
+                        const double* zu, const double* zl, double* wz, int64_t N, double* part,
                         unsigned* counter, double* H, int ldh, int j, double* scal) {
   pdl_trigger();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -276,7 +197,10 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
   }
   for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
   double v = 0.0;
-  if (r < N && sub == 0) v = zl[r] * acc + zu[r] * zu[r];
+  if (r < N && sub == 0) {
+    wz[r] = acc;   // (M z_l)_r, the B-image kept with the basis vector
+    v = zl[r] * acc + zu[r] * zu[r];
+  }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __shared__ double red[8];
   __shared__ double r2[256];
@@ -336,8 +260,8 @@ __global__ void k_update(const double* V, int64_t ld, int ncol, const double* h,
   z[i] -= (a0 + a1) + (a2 + a3);
 }
 
-// z *= 1 / ||z||_B over the 2 Np rows; also w = s z_u + z_l (rows < Np) for
-// the next operator product
+// z *= 1 / ||z||_B over its 3 Np rows (v_u, v_l and the B-image M v_l);
+// also w = s z_u + z_l (rows < Np) for the next operator product
 __global__ void k_scale(double* z, const double* scal, int64_t Np, double s, double* w) {
   pdl_trigger();
   pdl_wait();
@@ -347,6 +271,7 @@ __global__ void k_scale(double* z, const double* scal, int64_t Np, double s, dou
     const double u = z[i] * f, l = z[Np + i] * f;
     z[i] = u;
     z[Np + i] = l;
+    z[2 * Np + i] *= f;
     w[i] = s * u + l;
   }
 }
@@ -623,6 +548,10 @@ __global__ void k_grad(const double* X, const double* lam, const double* den, co
   G[2 * (e + ne2 * t) + 1] = (ni * dr - nr * di) / dd;
 }
 
+// basis layout: rows per half (a multiple of the TMA tile) and column stride
+int64_t basis_np(int64_t N) { return (N + kTileRows - 1) / kTileRows * kTileRows; }
+int64_t basis_ld(int64_t N) { return 3 * basis_np(N); }
+
 struct Work {
   Problem& P;
   int m;
@@ -671,21 +600,14 @@ struct Work {
       ++P.launches;
     }
   }
-  void spmv(const double* A, const double* x, double* y) {
-    int64_t thr = N * kSub;
-    launch_pdl(k_spmv, dim3((unsigned)((thr + 255) / 256)), dim3(256), 0, s, P.rowptr_n.p,
-               P.col_n.p, A, x, y, N);
-    ++n_spmv;
-    ++P.launches;
-  }
   // B-norm of column c -> H[c, c-1] (if setH) and V[:, c] normalised
   void normalise(int c, bool setH) {
     double* z = col(c);
     int64_t thr = N * kSub;
     unsigned nb = (unsigned)((thr + 255) / 256);
     launch_pdl(k_bnorm, dim3(nb), dim3(256), 0, s, P.rowptr_n.p, P.col_n.p, P.Mn.p, z,
-               (const double*)(z + Np), N, P.part.p, P.counter.p + 1, setH ? P.H.p : nullptr, m + 1,
-               c - 1, P.scal.p);
+               (const double*)(z + Np), z + 2 * Np, N, P.part.p, P.counter.p + 1,
+               setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p);
     ++n_spmv;
     P.launches += 2;
     launch_pdl(k_scale, dim3((unsigned)((Np + 255) / 256)), dim3(256), 0, s, z,
@@ -704,8 +626,7 @@ struct Work {
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     ++n_apply;
     for (int pass = 0; pass < 2; ++pass) {
-      spmv(P.Mn.p, r + Np, P.wvec.p);
-      dots(j, r, P.wvec.p);
+      dots(j, r, r + Np);   // V_u^T r_u + W^T r_l
       launch_pdl(k_update, dim3((unsigned)((2 * Np + 255) / 256)), dim3(256), 0, s,
                  (const double*)P.V.p, ld, j + 1, (const double*)P.hvec.p, r, 2 * Np);
       ++P.launches;
@@ -729,8 +650,8 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   W.fb_events(m + 1);
   RQ_CUDA(cudaEventCreate(&W.rz[0]));
   RQ_CUDA(cudaEventCreate(&W.rz[1]));
-  W.Np = (L.N + 31) / 32 * 32;
-  W.ld = 2 * W.Np;
+  W.Np = basis_np(L.N);
+  W.ld = basis_ld(L.N);
   W.nblk = 2 * 152;
   int64_t ld = W.ld, Np = W.Np, N = L.N;
   P.V.alloc(ld * (m + 1));
@@ -747,7 +668,6 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   P.counter.alloc(4);
   RQ_CUDA(cudaMemsetAsync(P.counter.p, 0, 4 * sizeof(unsigned), s));
   P.hvec.alloc(kMaxKrylov + 1);
-  P.wvec.alloc(Np);
   P.yop.alloc(Np);
   P.wop.alloc(Np);
   P.scal.alloc(4);
@@ -759,7 +679,6 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   RQ_CUDA(cudaMemsetAsync(P.V.p, 0, sizeof(double) * ld * (m + 1), s));
   RQ_CUDA(cudaMemsetAsync(P.Vtmp.p, 0, sizeof(double) * ld * m, s));
   RQ_CUDA(cudaMemsetAsync(P.H.p, 0, sizeof(double) * (m + 1) * m, s));
-  RQ_CUDA(cudaMemsetAsync(P.wvec.p, 0, sizeof(double) * Np, s));
 
   const double* start = v1;
   if (!start) {
@@ -873,7 +792,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   cudaStream_t s = P.stream;
   const int m = E.m, nks = E.ncand;
   const double tol = E.tol;
-  const int64_t N = L.N, ld = 2 * ((L.N + 31) / 32 * 32);
+  const int64_t N = L.N, ld = basis_ld(L.N);
   RQ_CUDA(cudaEventRecord(P.ev0, s));
   // in-region calls that differ only in the target (and neig) share the
   // converged candidates of the previous call on the same factor
