@@ -57,35 +57,50 @@ __global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const doubl
 }
 
 // h[c] = sum_i B(i, c) x(i) over the 2 Np rows of [V_u; W] (B-images of the
-// basis vectors), x(i) = xa[i] (i < Np) or xb[i - Np]; then H[c, j] += h[c].
-// The basis is streamed through shared memory by
-// TMA: tiles of 128 rows x up to 64 columns (two 128 x 32 boxes), two stages,
-// the next tile's copy in flight while the current one is used.  Warp w
-// takes rows 32 (w mod 4) .. +31 of a tile and column half w / 4; each lane
-// keeps 32 column sums for its rows, reduced over the warp by a butterfly
-// transpose once at the end; then the block's warps and the blocks are summed
-// in a fixed order (last block to finish).  One block per SM.
+// basis vectors), x(i) = xa[i] (i < Np) or xb[i - Np]; then H[c, j] += h[c],
+// for all ncol <= 96 columns in one launch.  The basis is streamed through
+// shared memory by TMA: tiles of 128 rows x ncol columns rounded up to 8
+// (boxes of 128 x 8), two stages, the next tile's copy in flight while the
+// current one is used.  Warp w takes rows 32 (w mod 4) .. +31 of a tile and
+// columns 32 (w / 4) .. +31; each lane keeps up to 32 column sums for its
+// rows (only the loaded 8-column groups are accumulated, so that the FP64
+// work follows ncol), reduced over the warp by a butterfly transpose once at
+// the end; then the block's warps and the blocks are summed in a fixed order
+// (last block to finish).  One block per SM.
 constexpr int kTileRows = 128;
+constexpr int kDotsCols = 96;    // columns per launch (the largest Krylov dimension)
+constexpr int kDotsThreads = 384;
+constexpr int kBoxCols = 8;
+static_assert(kDotsCols >= kMaxKrylov, "one launch covers every basis column");
 constexpr uint32_t kTmaWaitLimit = 1u << 22;
 
-size_t dots_tma_smem() { return sizeof(double) * 2 * 64 * kTileRows + 64; }
+size_t dots_tma_smem() { return sizeof(double) * 2 * kDotsCols * kTileRows + 64; }
 
-__global__ void __launch_bounds__(256, 1)
-    k_dots_tma(const __grid_constant__ CUtensorMap tV, int ncol, int c0, const double* xa,
+// acc[q] += tile[q * 128] * x for q < 8 G (G warp-uniform, 1..4)
+template <int G>
+__device__ __forceinline__ void dots_acc(double (&acc)[32], const double* tile, double x) {
+#pragma unroll
+  for (int q = 0; q < 8 * G; ++q) acc[q] = fma(tile[q * kTileRows], x, acc[q]);
+}
+
+__global__ void __launch_bounds__(kDotsThreads, 1)
+    k_dots_tma(const __grid_constant__ CUtensorMap tV, int ncol, const double* xa,
                const double* xb, int64_t Np, double* part, unsigned* counter, double* h, double* H,
                int ldh, int j, DevStatus* st) {
   extern __shared__ __align__(1024) double dsm[];
   double* stage0 = dsm;
-  double* stage1 = dsm + 64 * kTileRows;
-  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + 2 * 64 * kTileRows);
-  __shared__ double red[8][32];
+  double* stage1 = dsm + kDotsCols * kTileRows;
+  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + 2 * kDotsCols * kTileRows);
+  __shared__ double red[kDotsThreads / 32][32];
   __shared__ bool last;
   const int64_t rows = 2 * Np;
   const int ntile = (int)((rows + kTileRows - 1) / kTileRows);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rs = (warp & 3) * 32, hh = warp >> 2;
-  const int nbox = ncol > 32 ? 2 : 1;
-  const uint32_t bytes = (uint32_t)(nbox * 32 * kTileRows * sizeof(double));
+  const int rs = (warp & 3) * 32, cg = warp >> 2;
+  const int nbox = (ncol + kBoxCols - 1) / kBoxCols;
+  // this warp's loaded 8-column groups (0..4)
+  const int g = min(4, max(0, nbox - 4 * cg));
+  const uint32_t bytes = (uint32_t)(nbox * kBoxCols * kTileRows * sizeof(double));
   pdl_trigger();
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -99,7 +114,7 @@ __global__ void __launch_bounds__(256, 1)
   if (threadIdx.x == 0 && (int)blockIdx.x < ntile) {
     mbar_expect_tx(&full[0], bytes);
     for (int b = 0; b < nbox; ++b)
-      tma_load_2d(stage0 + b * 32 * kTileRows, &tV, vrow((int)blockIdx.x), c0 + 32 * b, &full[0]);
+      tma_load_2d(stage0 + b * kBoxCols * kTileRows, &tV, vrow((int)blockIdx.x), kBoxCols * b, &full[0]);
   }
   double acc[32];
 #pragma unroll
@@ -116,15 +131,17 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0 && tn < ntile) {
       mbar_expect_tx(&full[s ^ 1], bytes);
       for (int b = 0; b < nbox; ++b)
-        tma_load_2d(nxt + b * 32 * kTileRows, &tV, vrow(tn), c0 + 32 * b, &full[s ^ 1]);
+        tma_load_2d(nxt + b * kBoxCols * kTileRows, &tV, vrow(tn), kBoxCols * b, &full[s ^ 1]);
     }
     const int64_t i = (int64_t)t * kTileRows + rs + lane;
     const double x = i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0);
     const bool ok = mbar_wait(&full[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
-    if (ok && hh < nbox) {
-      const double* tile = cur + hh * 32 * kTileRows + rs + lane;   // column q at tile[q * 128]
-#pragma unroll
-      for (int q = 0; q < 32; ++q) acc[q] += tile[q * kTileRows] * x;
+    if (ok) {
+      const double* tile = cur + cg * 32 * kTileRows + rs + lane;   // column q at tile[q * 128]
+      if (g == 4) dots_acc<4>(acc, tile, x);
+      else if (g == 3) dots_acc<3>(acc, tile, x);
+      else if (g == 2) dots_acc<2>(acc, tile, x);
+      else if (g == 1) dots_acc<1>(acc, tile, x);
     }
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -138,23 +155,25 @@ __global__ void __launch_bounds__(256, 1)
     }
   }
   if (failed) return;
-  // lane l <- the warp's sum for column hh * 32 + l
+  // lane l <- the warp's sum for column 32 cg + l
+  if (g > 0) {
 #pragma unroll
-  for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
-    bool up = (lane & o) != 0;
+    for (int o = 16, len = 32; o > 0; o >>= 1, len >>= 1) {
+      bool up = (lane & o) != 0;
 #pragma unroll
-    for (int q = 0; q < len / 2; ++q) {
-      double send = up ? acc[q] : acc[q + len / 2];
-      double keep = up ? acc[q + len / 2] : acc[q];
-      acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      for (int q = 0; q < len / 2; ++q) {
+        double send = up ? acc[q] : acc[q + len / 2];
+        double keep = up ? acc[q + len / 2] : acc[q];
+        acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
     }
   }
   red[warp][lane] = acc[0];
   __syncthreads();
-  if (threadIdx.x < 64) {
-    const int half = threadIdx.x >> 5, l = threadIdx.x & 31;
-    double sm = (red[4 * half][l] + red[4 * half + 1][l]) + (red[4 * half + 2][l] + red[4 * half + 3][l]);
-    part[blockIdx.x * 64 + threadIdx.x] = sm;
+  if (threadIdx.x < kDotsCols) {
+    const int cgr = threadIdx.x >> 5, l = threadIdx.x & 31;
+    double sm = (red[4 * cgr][l] + red[4 * cgr + 1][l]) + (red[4 * cgr + 2][l] + red[4 * cgr + 3][l]);
+    part[blockIdx.x * kDotsCols + threadIdx.x] = sm;
   }
   __threadfence();
   __syncthreads();
@@ -162,19 +181,21 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // 256 threads: column c = tid & 63, quarter = tid >> 6 sums every fourth block
-  const int c = threadIdx.x & 63, qtr = threadIdx.x >> 6;
+  // 384 threads: column c = tid mod 96, quarter = tid / 96 sums every fourth
+  // block (L2 loads, unrolled so that several are in flight; fixed order)
+  const int c = threadIdx.x % kDotsCols, qtr = threadIdx.x / kDotsCols;
   double sm = 0.0;
-  for (int b = qtr; b < (int)gridDim.x; b += 4) sm += ((volatile double*)part)[b * 64 + c];
+#pragma unroll 8
+  for (int b = qtr; b < (int)gridDim.x; b += 4) sm += __ldcg(part + b * kDotsCols + c);
   __syncthreads();
-  double* red2 = &red[0][0];    // 4 x 64
-  red2[qtr * 64 + c] = sm;
+  double* red2 = &red[0][0];    // 4 x 96
+  red2[qtr * kDotsCols + c] = sm;
   __syncthreads();
   if (threadIdx.x < ncol) {
-    double v = (red2[threadIdx.x] + red2[64 + threadIdx.x]) +
-               (red2[128 + threadIdx.x] + red2[192 + threadIdx.x]);
-    h[c0 + threadIdx.x] = v;
-    H[c0 + threadIdx.x + (int64_t)ldh * j] += v;
+    double v = (red2[threadIdx.x] + red2[kDotsCols + threadIdx.x]) +
+               (red2[2 * kDotsCols + threadIdx.x] + red2[3 * kDotsCols + threadIdx.x]);
+    h[threadIdx.x] = v;
+    H[threadIdx.x + (int64_t)ldh * j] += v;
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
@@ -219,7 +240,8 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
   if (!last) return;
   __threadfence();
   double sm = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sm += ((volatile double*)part)[b];
+#pragma unroll 4
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sm += __ldcg(part + b);
   r2[threadIdx.x] = sm;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {   // fixed-order tree over the 256 partial sums
@@ -279,9 +301,9 @@ __global__ void k_scale(double* z, const double* scal, int64_t Np, double s, dou
 // out[i, t] = sum_{c < m} V[i, c] Q[c, t] (restart / basis change); each
 // thread owns one row and 16 output columns t0 .. t0+15 (blockIdx.y).
 __global__ void k_basis_gemm(const double* V, int64_t ld, int m, const double* Q, int k,
-                             double* out, int64_t rows) {
+                             double* out, int64_t rows, int lo) {
   extern __shared__ double qs[];
-  int t0 = blockIdx.y * 16;
+  int t0 = lo + blockIdx.y * 16;
   int nt = min(16, k - t0);
   for (int i = threadIdx.x; i < m * 16; i += blockDim.x) {
     int c = i % m, q = i / m;
@@ -294,7 +316,7 @@ __global__ void k_basis_gemm(const double* V, int64_t ld, int m, const double* Q
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = 0.0;
   const double* vr = V + i;
-  for (int c = 0; c < m; ++c) {
+  for (int c = lo; c < m; ++c) {
     double v = vr[ld * c];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] += v * qs[c + m * q];
@@ -593,12 +615,9 @@ struct Work {
   double* col(int c) { return P.V.p + ld * c; }
 
   void dots(int j, const double* xa, const double* xb) {
-    for (int c0 = 0; c0 <= j; c0 += 64) {
-      int nc = std::min(64, j + 1 - c0);
-      launch_pdl(k_dots_tma, dim3(nsm), dim3(256), dots_tma_smem(), s, tV, nc, c0, xa, xb, Np,
-                 P.part.p, P.counter.p, P.hvec.p, P.H.p, m + 1, j, P.status.p);
-      ++P.launches;
-    }
+    launch_pdl(k_dots_tma, dim3(nsm), dim3(kDotsThreads), dots_tma_smem(), s, tV, j + 1, xa, xb, Np,
+               P.part.p, P.counter.p, P.hvec.p, P.H.p, m + 1, j, P.status.p);
+    ++P.launches;
   }
   // B-norm of column c -> H[c, c-1] (if setH) and V[:, c] normalised
   void normalise(int c, bool setH) {
@@ -655,7 +674,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   W.nblk = 2 * 152;
   int64_t ld = W.ld, Np = W.Np, N = L.N;
   P.V.alloc(ld * (m + 1));
-  make_tmap_f64(&W.tV, P.V.p, (uint64_t)ld, (uint64_t)(m + 1), (uint64_t)ld, kTileRows, 32);
+  make_tmap_f64(&W.tV, P.V.p, (uint64_t)ld, (uint64_t)(m + 1), (uint64_t)ld, kTileRows, kBoxCols);
   {
     int dev = 0;
     RQ_CUDA(cudaGetDevice(&dev));
@@ -723,14 +742,21 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
     for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] += (double)h_out.phase_cycles[q];
     if (h_out.finished) break;
     k = h_out.k;
+    // the columns locked before this Ritz step are untouched by it: their
+    // Schur vectors are unit vectors (Q[:lk, :lk] = I, Q[:lk, lk:] = 0), so
+    // only V[:, lk:k] = V[:, lk:m] Q[lk:m, lk:k] is formed
+    const int lk = lock;
     lock = h_out.n_lock;
     // V[:, :k] = V[:, :m] Q ; V[:, k] = V[:, m] ; H = Hnew
     size_t smem = sizeof(double) * (size_t)m * 16;
-    dim3 gg((unsigned)((ld + 127) / 128), (unsigned)((k + 15) / 16));
-    k_basis_gemm<<<gg, 128, smem, s>>>(P.V.p, ld, m, Qb.p, k, P.Vtmp.p, ld);
-    RQ_CUDA(cudaGetLastError());
-    ++P.launches;
-    RQ_CUDA(cudaMemcpyAsync(P.V.p, P.Vtmp.p, sizeof(double) * ld * k, cudaMemcpyDeviceToDevice, s));
+    if (k > lk) {
+      dim3 gg((unsigned)((ld + 127) / 128), (unsigned)((k - lk + 15) / 16));
+      k_basis_gemm<<<gg, 128, smem, s>>>(P.V.p, ld, m, Qb.p, k, P.Vtmp.p, ld, lk);
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+      RQ_CUDA(cudaMemcpyAsync(P.V.p + ld * lk, P.Vtmp.p + ld * lk, sizeof(double) * ld * (k - lk),
+                              cudaMemcpyDeviceToDevice, s));
+    }
     RQ_CUDA(cudaMemcpyAsync(P.V.p + ld * k, P.V.p + ld * m, sizeof(double) * ld,
                             cudaMemcpyDeviceToDevice, s));
     RQ_CUDA(cudaMemcpyAsync(P.H.p, Hn.p, sizeof(double) * (m + 1) * m, cudaMemcpyDeviceToDevice, s));
