@@ -12,8 +12,10 @@
 // forms each CSR entry by summing over the elements shared by its two
 // functions (one thread per row, no atomics, deterministic):
 //   M_ij = sum_e mx my,  K_ij = sum_e (kx my + mx ky),  C_ij = sum_e sigma_e mx my.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -243,6 +245,47 @@ void launch_permute_values(Problem& P) {
   P.Cn.alloc(n);
   k_permute<<<(unsigned)((n + 255) / 256), 256, 0, P.stream>>>(P.slot_map.p, P.K.p, P.M.p, P.C.p,
                                                                P.Kn.p, P.Mn.p, P.Cn.p, n);
+  RQ_CUDA(cudaGetLastError());
+}
+
+// SELL-32: thread (slice s, lane l) writes row 32 s + l's entries at
+// off + 32 k + l; slots past the row's end (and rows past N) get column 0 and
+// zero values.
+__global__ void k_sell_fill(const int32_t* rowptr, const int32_t* col, const double* Mn,
+                            const double* Cn, const int32_t* off, int64_t ns, int64_t N,
+                            int32_t* scol, double* sM, double* sC) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t sl = r >> 5;
+  if (sl >= ns) return;
+  const int l = (int)(r & 31);
+  const int32_t o0 = off[sl], w = (off[sl + 1] - o0) >> 5;
+  const int32_t q0 = r < N ? rowptr[r] : 0, n = r < N ? rowptr[r + 1] - q0 : 0;
+  for (int k = 0; k < w; ++k) {
+    const int64_t e = o0 + 32 * (int64_t)k + l;
+    scol[e] = k < n ? col[q0 + k] : 0;
+    sM[e] = k < n ? Mn[q0 + k] : 0.0;
+    sC[e] = k < n ? Cn[q0 + k] : 0.0;
+  }
+}
+
+void launch_sell(Problem& P) {
+  const Plan& L = P.plan;
+  const int64_t N = L.N, ns = (N + 31) / 32;
+  std::vector<int32_t>& off = P.sell_off_h;
+  off.assign(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int32_t w = 0;
+    for (int64_t r = 32 * sl; r < std::min(N, 32 * sl + 32); ++r)
+      w = std::max(w, L.rowptr_n[r + 1] - L.rowptr_n[r]);
+    off[sl + 1] = off[sl] + 32 * w;
+  }
+  P.sell_off.upload(off, P.stream);
+  P.sell_col.alloc(off[ns]);
+  P.sell_M.alloc(off[ns]);
+  P.sell_C.alloc(off[ns]);
+  k_sell_fill<<<(unsigned)((32 * ns + 255) / 256), 256, 0, P.stream>>>(
+      P.rowptr_n.p, P.col_n.p, P.Mn.p, P.Cn.p, P.sell_off.p, ns, N, P.sell_col.p, P.sell_M.p,
+      P.sell_C.p);
   RQ_CUDA(cudaGetLastError());
 }
 

@@ -177,6 +177,7 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
     P.fpos.upload(L.fpos, s);
     P.slot_map.upload(L.slot_map, s);
     rq::launch_permute_values(P);
+    rq::launch_sell(P);
     P.lvl_maxF.assign(L.nlevels, 0);
     P.lvl_maxK.assign(L.nlevels, 0);
     for (int sn = 0; sn < L.nsuper; ++sn) {

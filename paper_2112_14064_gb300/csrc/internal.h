@@ -116,7 +116,7 @@ struct DevStatus {
   int32_t pad;
 };
 
-// Output of the single-CTA Ritz kernel.
+// Output of the Ritz kernel.
 struct RitzOut {
   int32_t n_conv;       // wanted pairs (first neig) with estimate <= tol
   int32_t k;            // kept dimension after reordering (restart)
@@ -159,6 +159,11 @@ struct Problem {
   DBuf<int32_t> rowptr_n, col_n, fpos;
   DBuf<int32_t> slot_map;
   DBuf<double> Kn, Mn, Cn;
+  // the same pattern in SELL-32 (slices of 32 rows, each padded to its widest
+  // row; entry k of row 32 s + l at sell_off[s] + 32 k + l) with M and C
+  DBuf<int32_t> sell_off, sell_col;
+  DBuf<double> sell_M, sell_C;
+  std::vector<int32_t> sell_off_h;   // host copy (source of the upload)
   // symbolic on device
   DBuf<int32_t> perm, iperm, sptr, upd_ptr, upd_idx, relmap, child_ptr, child_idx, lvl_nodes;
   DBuf<int64_t> loff, uoff;
@@ -203,6 +208,8 @@ struct Problem {
 // kernels / launch helpers (each .cu file)
 void launch_assemble(Problem& P);
 void launch_permute_values(Problem& P);
+// SELL-32 copy of the ND pattern with M and C (after launch_permute_values)
+void launch_sell(Problem& P);
 void launch_norms(Problem& P);
 void launch_factor(Problem& P, double sigma, bool fp32);
 // relative residuals of FP64 refinement steps 1, 2, ... with the FP32 factor

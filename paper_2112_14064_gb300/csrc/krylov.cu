@@ -31,29 +31,63 @@ void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* o
 
 namespace {
 
-constexpr int kSub = 8;  // lanes per CSR row
+// Sparse products over the SELL-32 copy of the pattern (slot k of row
+// 32 s + l at off[s] + 32 k + l; padded slots hold column 0 and zero values).
+// kSplit warps share a slice: warp t takes slots k = t mod kSplit of all 32
+// rows, so that every load of the pattern and the values is coalesced, each
+// FP64 instruction does 32 rows' work (on this GPU every FP64 warp
+// instruction costs 64 cycles of its sub-partition's pipe whatever its active
+// lanes), and there are kSplit threads per row to keep loads in flight.  The
+// partial sums meet in shared memory.  A block of 256 threads covers two
+// slices.
+constexpr int kSplit = 4;
+constexpr int kSellBlock = 256;
+constexpr int kSlicesPerBlock = kSellBlock / 32 / kSplit;
+static_assert(kSlicesPerBlock >= 1, "a block covers whole slices");
+// sum of the kSplit partial sums of row `lane` of the slice whose first warp is w0
+__device__ __forceinline__ double sell_combine(const double (*red)[32], int w0, int lane) {
+  double a = red[w0][lane];
+#pragma unroll
+  for (int t = 1; t < kSplit; ++t) a += red[w0 + t][lane];
+  return a;
+}
+struct Sell {
+  int32_t o0, wd;   // first slot and width of the thread's slice (0 past the last slice)
+};
+__device__ __forceinline__ Sell sell_slice(const int32_t* off, int64_t ns, int64_t r) {
+  const int64_t sl = r >> 5;
+  Sell q{0, 0};
+  if (sl < ns) {
+    q.o0 = off[sl];
+    q.wd = (off[sl + 1] - q.o0) >> 5;
+  }
+  return q;
+}
 
 // y_i = sum_q M_iq w_q + C_iq vu_q with w = s vu + vl (formed by k_scale when
 // the basis vector was normalised): the fused s M v_u + C v_u + M v_l
-__global__ void k_spmv_op(const int32_t* rowptr, const int32_t* col, const double* Mv,
-                          const double* Cv, const double* vu, const double* w, double* y,
-                          int64_t N) {
+__global__ void __launch_bounds__(kSellBlock) k_spmv_op(
+    const int32_t* off, int64_t ns, const int32_t* col, const double* Ms, const double* Cs,
+    const double* vu, const double* w, double* y, int64_t N) {
   pdl_trigger();
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t r = t / kSub;
-  int sub = t % kSub;
-  double acc = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = warp % kSplit;
+  const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
   // the pattern is fixed before the chain starts; the vectors are not
-  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
+  const Sell q = sell_slice(off, ns, r);
+  const int64_t e0 = q.o0 + lane;
   pdl_wait();
-  if (r < N) {
-    for (int32_t q = q0 + sub; q < q1; q += kSub) {
-      int32_t c = col[q];
-      acc += Mv[q] * w[c] + Cv[q] * vu[c];
-    }
+  double acc = 0.0;
+#pragma unroll 2
+  for (int k = sub; k < q.wd; k += kSplit) {
+    const int64_t e = e0 + 32 * (int64_t)k;
+    const int32_t c = col[e];
+    acc = fma(Ms[e], w[c], acc);
+    acc = fma(Cs[e], vu[c], acc);
   }
-  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
-  if (r < N && sub == 0) y[r] = acc;
+  __shared__ double red[kSellBlock / 32][32];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (sub == 0 && r < N) y[r] = sell_combine(red, warp, lane);
 }
 
 // h[c] = sum_i B(i, c) x(i) over the 2 Np rows of [V_u; W] (B-images of the
@@ -203,35 +237,45 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
 // B-norm of z = [zu; zl]: sum zu^2 + zl . (M zl) with the SpMV fused (8 lanes
 // per row); the last block sets nrm = sqrt(sum), H[j+1, j] = nrm (if H),
 // scal = {1/nrm, nrm}.
-__global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double* Mv,
-                        const double* zu, const double* zl, double* wz, int64_t N, double* part,
-                        unsigned* counter, double* H, int ldh, int j, double* scal) {
+// B-norm of z = [zu; zl]: sum zu^2 + zl . (M zl) with the SpMV fused (SELL,
+// one thread per row), M zl kept as the basis vector's B-image; the last
+// block sets nrm = sqrt(sum), H[j+1, j] = nrm (if H), scal = {1/nrm, nrm}.
+__global__ void __launch_bounds__(kSellBlock) k_bnorm(
+    const int32_t* off, int64_t ns, const int32_t* col, const double* Ms, const double* zu,
+    const double* zl, double* wz, int64_t N, double* part, unsigned* counter, double* H, int ldh,
+    int j, double* scal) {
   pdl_trigger();
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t r = t / kSub;
-  int sub = t % kSub;
-  double acc = 0.0;
-  const int32_t q0 = r < N ? rowptr[r] : 0, q1 = r < N ? rowptr[r + 1] : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = warp % kSplit;
+  const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
+  const Sell q = sell_slice(off, ns, r);
+  const int64_t e0 = q.o0 + lane;
   pdl_wait();
-  if (r < N) {
-    for (int32_t q = q0 + sub; q < q1; q += kSub) acc += Mv[q] * zl[col[q]];
+  double acc = 0.0;
+#pragma unroll 2
+  for (int k = sub; k < q.wd; k += kSplit) {
+    const int64_t e = e0 + 32 * (int64_t)k;
+    acc = fma(Ms[e], zl[col[e]], acc);
   }
-  for (int o = kSub / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, kSub);
-  double v = 0.0;
-  if (r < N && sub == 0) {
-    wz[r] = acc;   // (M z_l)_r, the B-image kept with the basis vector
-    v = zl[r] * acc + zu[r] * zu[r];
-  }
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __shared__ double red[8];
-  __shared__ double r2[256];
+  __shared__ double red[kSellBlock / 32][32];
+  __shared__ double bs[kSlicesPerBlock];
   __shared__ bool last;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = v;
+  const int nw = kSellBlock / 32;
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (sub == 0) {
+    double v = 0.0;
+    if (r < N) {
+      const double a = sell_combine(red, warp, lane);
+      wz[r] = a;   // (M z_l)_r, the B-image kept with the basis vector
+      v = zl[r] * a + zu[r] * zu[r];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) bs[warp / kSplit] = v;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double sm = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sm += red[w];
+    for (int b = 0; b < kSlicesPerBlock; ++b) sm += bs[b];
     part[blockIdx.x] = sm;
     __threadfence();
     last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -239,22 +283,23 @@ __global__ void k_bnorm(const int32_t* rowptr, const int32_t* col, const double*
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // L2 loads, several in flight; fixed-order sums over the blocks
   double sm = 0.0;
 #pragma unroll 4
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) sm += __ldcg(part + b);
-  r2[threadIdx.x] = sm;
+  for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+  if (lane == 0) red[0][warp] = sm;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {   // fixed-order tree over the 256 partial sums
-    if (threadIdx.x < o) r2[threadIdx.x] += r2[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double tot = r2[0];
-    double nr = sqrt(tot);
-    if (H) H[(j + 1) + (int64_t)ldh * j] = nr;
-    scal[0] = 1.0 / nr;
-    scal[1] = nr;
-    *counter = 0u;
+  if (warp == 0) {
+    double tot = lane < nw ? red[0][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) {
+      double nr = sqrt(tot);
+      if (H) H[(j + 1) + (int64_t)ldh * j] = nr;
+      scal[0] = 1.0 / nr;
+      scal[1] = nr;
+      *counter = 0u;
+    }
   }
 }
 
@@ -622,9 +667,10 @@ struct Work {
   // B-norm of column c -> H[c, c-1] (if setH) and V[:, c] normalised
   void normalise(int c, bool setH) {
     double* z = col(c);
-    int64_t thr = N * kSub;
-    unsigned nb = (unsigned)((thr + 255) / 256);
-    launch_pdl(k_bnorm, dim3(nb), dim3(256), 0, s, P.rowptr_n.p, P.col_n.p, P.Mn.p, z,
+    const int64_t ns = (N + 31) / 32;
+    launch_pdl(k_bnorm, dim3((unsigned)((ns + kSlicesPerBlock - 1) / kSlicesPerBlock)),
+               dim3(kSellBlock), 0, s, P.sell_off.p, ns,
+               P.sell_col.p, P.sell_M.p, z,
                (const double*)(z + Np), z + 2 * Np, N, P.part.p, P.counter.p + 1,
                setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p);
     ++n_spmv;
@@ -636,9 +682,11 @@ struct Work {
   void step(int j) {
     double* v = col(j);
     double* r = col(j + 1);
-    int64_t thr = N * kSub;
-    launch_pdl(k_spmv_op, dim3((unsigned)((thr + 255) / 256)), dim3(256), 0, s, P.rowptr_n.p,
-               P.col_n.p, P.Mn.p, P.Cn.p, (const double*)v, (const double*)P.wop.p, P.yop.p, N);
+    const int64_t ns = (N + 31) / 32;
+    launch_pdl(k_spmv_op, dim3((unsigned)((ns + kSlicesPerBlock - 1) / kSlicesPerBlock)),
+               dim3(kSellBlock), 0, s, P.sell_off.p,
+               ns, P.sell_col.p, P.sell_M.p, P.sell_C.p, (const double*)v, (const double*)P.wop.p,
+               P.yop.p, N);
     n_spmv += 3;
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     launch_fb(P, P.yop.p, sigma, v, r, r + Np);

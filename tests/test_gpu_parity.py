@@ -176,8 +176,11 @@ def test_eigs_match_oracle(rq, name, over, _):
     for k in range(neig):
         x = X[k]
         assert np.linalg.norm(x) == pytest.approx(1.0, abs=1e-12)
-        i = np.argmax(np.abs(x))
-        assert abs(x[i].imag) <= 1e-14 and x[i].real > 0
+        # an entry of largest modulus is real and positive; entries whose
+        # moduli tie within rounding (symmetric modes) may each be the one
+        ax = np.abs(x)
+        top = np.flatnonzero(ax >= ax.max() * (1 - 1e-12))
+        assert any(abs(x[i].imag) <= 1e-14 and x[i].real > 0 for i in top)
         # the oracle's own backward error of the GPU pair
         assert qep.backward_error(lam[k], x, A.K, A.C, A.M) <= 1e-10
     inf = pr.info()
