@@ -124,9 +124,13 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
   extern __shared__ __align__(1024) double dsm[];
   double* stage0 = dsm;
   double* stage1 = dsm + kDotsCols * kTileRows;
+  // full[s]: the tile's copy landed (one arrival plus the bytes);
+  // empty[s]: every warp has finished reading the stage (one arrival each)
   uint64_t* full = reinterpret_cast<uint64_t*>(dsm + 2 * kDotsCols * kTileRows);
+  uint64_t* empty = full + 2;
   __shared__ double red[kDotsThreads / 32][32];
   __shared__ bool last;
+  __shared__ volatile int abort_flag;
   const int64_t rows = 2 * Np;
   const int ntile = (int)((rows + kTileRows - 1) / kTileRows);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,56 +143,75 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
+    mbar_init(&empty[0], kDotsThreads / 32);
+    mbar_init(&empty[1], kDotsThreads / 32);
+    abort_flag = 0;
     mbar_fence_init();
   }
   __syncthreads();
   pdl_wait();
   // tile t covers rows t*128.. of [V_u; W]: V rows 0..Np-1, then 2Np..3Np-1
   auto vrow = [Np](int t) { const int64_t r = (int64_t)t * kTileRows; return (int)(r < Np ? r : r + Np); };
-  if (threadIdx.x == 0 && (int)blockIdx.x < ntile) {
-    mbar_expect_tx(&full[0], bytes);
-    for (int b = 0; b < nbox; ++b)
-      tma_load_2d(stage0 + b * kBoxCols * kTileRows, &tV, vrow((int)blockIdx.x), kBoxCols * b, &full[0]);
-  }
+  // producer (thread 0): the block's first two tiles now, then each stage
+  // again once every warp has released it
+  int issued[2] = {-1, -1};   // last iteration whose copy went to each stage
+  if (threadIdx.x == 0)
+    for (int st2 = 0; st2 < 2; ++st2) {
+      const int t = (int)blockIdx.x + st2 * (int)gridDim.x;
+      if (t < ntile) {
+        double* dst = st2 ? stage1 : stage0;
+        mbar_expect_tx(&full[st2], bytes);
+        for (int b = 0; b < nbox; ++b)
+          tma_load_2d(dst + b * kBoxCols * kTileRows, &tV, vrow(t), kBoxCols * b, &full[st2]);
+        issued[st2] = st2;
+      }
+    }
   double acc[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-  bool failed = false;
   int it = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
     const int s = it & 1;
-    double* cur = s ? stage1 : stage0;
-    double* nxt = s ? stage0 : stage1;
-    // the other stage was last read in the previous iteration, which ended
-    // with a block barrier
-    const int tn = t + gridDim.x;
-    if (threadIdx.x == 0 && tn < ntile) {
-      mbar_expect_tx(&full[s ^ 1], bytes);
-      for (int b = 0; b < nbox; ++b)
-        tma_load_2d(nxt + b * kBoxCols * kTileRows, &tV, vrow(tn), kBoxCols * b, &full[s ^ 1]);
-    }
+    const double* cur = s ? stage1 : stage0;
     const int64_t i = (int64_t)t * kTileRows + rs + lane;
     const double x = i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0);
-    const bool ok = mbar_wait(&full[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit);
-    if (ok) {
-      const double* tile = cur + cg * 32 * kTileRows + rs + lane;   // column q at tile[q * 128]
-      if (g == 4) dots_acc<4>(acc, tile, x);
-      else if (g == 3) dots_acc<3>(acc, tile, x);
-      else if (g == 2) dots_acc<2>(acc, tile, x);
-      else if (g == 1) dots_acc<1>(acc, tile, x);
-    }
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      if (threadIdx.x == 0) {
-        atomicExch(&st->internal, 3);
-        // let a copy still in flight into this block's shared memory land
-        if (tn < ntile) mbar_wait(&full[s ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitLimit);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit));
+    if (!ok) abort_flag = 1;
+    if (abort_flag) break;
+    const double* tile = cur + cg * 32 * kTileRows + rs + lane;   // column q at tile[q * 128]
+    if (g == 4) dots_acc<4>(acc, tile, x);
+    else if (g == 3) dots_acc<3>(acc, tile, x);
+    else if (g == 2) dots_acc<2>(acc, tile, x);
+    else if (g == 1) dots_acc<1>(acc, tile, x);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (threadIdx.x == 0) {
+      const int tn = t + 2 * (int)gridDim.x;
+      if (tn < ntile) {
+        if (!mbar_wait(&empty[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit)) {
+          abort_flag = 1;
+        } else {
+          double* dst = s ? stage1 : stage0;
+          mbar_expect_tx(&full[s], bytes);
+          for (int b = 0; b < nbox; ++b)
+            tma_load_2d(dst + b * kBoxCols * kTileRows, &tV, vrow(tn), kBoxCols * b, &full[s]);
+          issued[s] = it + 2;
+        }
       }
-      __syncthreads();
-      break;
     }
   }
-  if (failed) return;
+  __syncthreads();
+  if (abort_flag) {
+    if (threadIdx.x == 0) {
+      atomicExch(&st->internal, 3);
+      // let the copies still in flight into this block's shared memory land
+      for (int st2 = 0; st2 < 2; ++st2)
+        if (issued[st2] >= 0)
+          mbar_wait(&full[st2], (uint32_t)((issued[st2] >> 1) & 1), kTmaWaitLimit);
+    }
+    __syncthreads();
+    return;
+  }
   // lane l <- the warp's sum for column 32 cg + l
   if (g > 0) {
 #pragma unroll
@@ -304,8 +327,10 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
 }
 
 // z[i] -= sum_c V[i, c] h[c] over the 2 Np rows of column z (ld stride in V)
-__global__ void k_update(const double* V, int64_t ld, int ncol, const double* h, double* z,
-                         int64_t rows) {
+// One row per thread, eight basis loads in flight; launched as two equal
+// blocks per SM (a single balanced wave).
+__global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, int ncol,
+                                                 const double* h, double* z, int64_t rows) {
   pdl_trigger();
   pdl_wait();
   __shared__ double hs[kMaxKrylov + 1];
@@ -314,17 +339,19 @@ __global__ void k_update(const double* V, int64_t ld, int ncol, const double* h,
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const double* vr = V + i;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double a[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) a[t] = 0.0;
   int c = 0;
-  for (; c + 4 <= ncol; c += 4) {
-    double v0 = vr[ld * c], v1 = vr[ld * (c + 1)], v2 = vr[ld * (c + 2)], v3 = vr[ld * (c + 3)];
-    a0 += v0 * hs[c];
-    a1 += v1 * hs[c + 1];
-    a2 += v2 * hs[c + 2];
-    a3 += v3 * hs[c + 3];
+  for (; c + 8 <= ncol; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = vr[ld * (c + t)];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = fma(v[t], hs[c + t], a[t]);
   }
-  for (; c < ncol; ++c) a0 += vr[ld * c] * hs[c];
-  z[i] -= (a0 + a1) + (a2 + a3);
+  for (; c < ncol; ++c) a[0] = fma(vr[ld * c], hs[c], a[0]);
+  z[i] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
 // z *= 1 / ||z||_B over its 3 Np rows (v_u, v_l and the B-image M v_l);
@@ -635,6 +662,7 @@ struct Work {
   double ritz_ms = 0.0;
   CUtensorMap tV{};  // the Krylov basis V for the TMA-fed kernels
   int nsm = 0;       // SMs of the device (one TMA block each)
+  int upd_threads = 256;   // k_update block: two equal blocks per SM
   ~Work() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : rz)
@@ -694,8 +722,9 @@ struct Work {
     ++n_apply;
     for (int pass = 0; pass < 2; ++pass) {
       dots(j, r, r + Np);   // V_u^T r_u + W^T r_l
-      launch_pdl(k_update, dim3((unsigned)((2 * Np + 255) / 256)), dim3(256), 0, s,
-                 (const double*)P.V.p, ld, j + 1, (const double*)P.hvec.p, r, 2 * Np);
+      launch_pdl(k_update, dim3((unsigned)((2 * Np + upd_threads - 1) / upd_threads)),
+                 dim3((unsigned)upd_threads), 0, s, (const double*)P.V.p, ld, j + 1,
+                 (const double*)P.hvec.p, r, 2 * Np);
       ++P.launches;
       n_vv += 4 * (j + 1);
     }
@@ -728,6 +757,9 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
     RQ_CUDA(cudaGetDevice(&dev));
     RQ_CUDA(cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, dev));
     smem_at_least((const void*)k_dots_tma, dots_tma_smem());
+    // rows of the update split into 2 nsm blocks of whole warps (<= 1024)
+    const int64_t per = (2 * W.Np + 2 * W.nsm - 1) / (2 * W.nsm);
+    W.upd_threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (per + 31) / 32 * 32));
   }
   P.Vtmp.alloc(ld * m);
   P.H.alloc((m + 1) * m);
