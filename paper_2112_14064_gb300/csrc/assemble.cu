@@ -238,6 +238,80 @@ void launch_norms(Problem& P) {
   P.info.norm_C = d[2];
 }
 
+// ND-ordered CSR of the pattern, one warp per ND row j (the original row
+// perm[j]): its columns renumbered by iperm and sorted (each entry's rank
+// among the row's distinct keys gives its slot), the original slot of each
+// entry, and the row of each lower-triangle entry (column i >= j) in the
+// front of j's supernode: i - a for the supernode's own pivots, k + (place of
+// i in its structure) otherwise, -1 above the diagonal.  err: 1 a row longer
+// than kNdMaxRow, 2 an entry outside the front (a broken symbolic phase).
+constexpr int kNdMaxRow = 256;
+constexpr int kNdWarps = 8;
+
+__global__ void __launch_bounds__(32 * kNdWarps) k_nd_csr(
+    const int32_t* perm, const int32_t* iperm, const int32_t* rowptr, const int32_t* col,
+    const int32_t* rowptr_n, const int32_t* sptr, int nsuper, const int32_t* upd_ptr,
+    const int32_t* upd_idx, int64_t N, int32_t* col_n, int32_t* slot_map, int32_t* fpos,
+    int32_t* err) {
+  __shared__ int32_t keys[kNdWarps][kNdMaxRow];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * kNdWarps + warp;
+  if (j >= N) return;   // whole warps
+  const int32_t o = perm[j], q0 = rowptr[o], n = rowptr[o + 1] - q0;
+  if (n > kNdMaxRow) {
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
+  for (int e = lane; e < n; e += 32) keys[warp][e] = iperm[col[q0 + e]];
+  __syncwarp();
+  // supernode of row j: the last s with sptr[s] <= j
+  int lo = 0, hi = nsuper - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sptr[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  const int a = sptr[lo], e1 = sptr[lo + 1], k = e1 - a;
+  const int32_t* ps = upd_idx + upd_ptr[lo];
+  const int u = upd_ptr[lo + 1] - upd_ptr[lo];
+  const int32_t base = rowptr_n[j];
+  for (int e = lane; e < n; e += 32) {
+    const int32_t key = keys[warp][e];
+    int rank = 0;
+    for (int f = 0; f < n; ++f) rank += keys[warp][f] < key ? 1 : 0;
+    const int32_t t = base + rank;
+    col_n[t] = key;
+    slot_map[t] = q0 + e;
+    int32_t fp = -1;
+    if (key >= j) {
+      if (key < e1) {
+        fp = key - a;
+      } else {
+        int l2 = 0, h2 = u;   // first structure entry >= key
+        while (l2 < h2) {
+          const int mid = (l2 + h2) >> 1;
+          if (ps[mid] < key) l2 = mid + 1;
+          else h2 = mid;
+        }
+        if (l2 < u && ps[l2] == key) fp = k + l2;
+        else atomicExch(err, 2);
+      }
+    }
+    fpos[t] = fp;
+  }
+}
+
+void launch_nd_csr(Problem& P, int32_t* err) {
+  const Plan& L = P.plan;
+  P.col_n.alloc(L.nnz);
+  P.slot_map.alloc(L.nnz);
+  P.fpos.alloc(L.nnz);
+  k_nd_csr<<<(unsigned)((L.N + kNdWarps - 1) / kNdWarps), 32 * kNdWarps, 0, P.stream>>>(
+      P.perm.p, P.iperm.p, P.rowptr.p, P.col.p, P.rowptr_n.p, P.sptr.p, L.nsuper, P.upd_ptr.p,
+      P.upd_idx.p, L.N, P.col_n.p, P.slot_map.p, P.fpos.p, err);
+  RQ_CUDA(cudaGetLastError());
+}
+
 void launch_permute_values(Problem& P) {
   int64_t n = P.plan.nnz;
   P.Kn.alloc(n);

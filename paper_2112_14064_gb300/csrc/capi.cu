@@ -173,9 +173,10 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
     P.loff.upload(L.loff, s);
     P.uoff.upload(L.uoff, s);
     P.rowptr_n.upload(L.rowptr_n, s);
-    P.col_n.upload(L.col_n, s);
-    P.fpos.upload(L.fpos, s);
-    P.slot_map.upload(L.slot_map, s);
+    rq::DBuf<int32_t> nd_err;
+    nd_err.alloc(1);
+    RQ_CUDA(cudaMemsetAsync(nd_err.p, 0, sizeof(int32_t), s));
+    rq::launch_nd_csr(P, nd_err.p);
     rq::launch_permute_values(P);
     rq::launch_sell(P);
     P.lvl_maxF.assign(L.nlevels, 0);
@@ -197,7 +198,11 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob) {
     rq::factor_configure(smax);
     rq::fb_plan(P);
     rq::factor_plan(P);
+    int32_t h_err = 0;
+    RQ_CUDA(cudaMemcpyAsync(&h_err, nd_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RQ_CUDA(cudaStreamSynchronize(s));
+    need(h_err != 1, RIGAQEP_ERR_ARG, "a matrix row has more than 256 entries");
+    if (h_err == 2) throw rq::Error(RIGAQEP_ERR_INTERNAL, "matrix entry outside the front");
     P.info.nsuper = L.nsuper;
     P.info.nlevels = L.nlevels;
     P.info.nnz_L = L.nnz_L;

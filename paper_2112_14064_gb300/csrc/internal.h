@@ -207,6 +207,9 @@ struct Problem {
 
 // kernels / launch helpers (each .cu file)
 void launch_assemble(Problem& P);
+// ND-ordered CSR columns, original slots and front rows (after the symbolic
+// arrays are on the device); err receives 1 or 2 on a bad pattern
+void launch_nd_csr(Problem& P, int32_t* err);
 void launch_permute_values(Problem& P);
 // SELL-32 copy of the ND pattern with M and C (after launch_permute_values)
 void launch_sell(Problem& P);

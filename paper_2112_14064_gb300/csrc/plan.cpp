@@ -17,7 +17,6 @@
 #include "plan.h"
 
 #include <algorithm>
-#include <atomic>
 #include <iterator>
 #include <stdexcept>
 #include <thread>
@@ -266,59 +265,12 @@ void Plan::build_symbolic() {
     }
   }
 
-  // ND-ordered CSR and the front row of every lower-triangle entry.  Rows are
-  // independent, so they are split over host threads.  Within one row the
-  // original columns run bj-major, bi-minor; inside one box the ND order is
-  // y-major, x-minor, so the entries of each owning box are already ascending
-  // and a stable bucketing by owner (ascending) yields the sorted row.
+  // row pointers of the ND-ordered CSR (row j is the original row perm[j])
   rowptr_n.assign(N + 1, 0);
   for (int64_t j = 0; j < N; ++j) {
     int32_t o = perm[j];
     rowptr_n[j + 1] = rowptr_n[j] + (rowptr[o + 1] - rowptr[o]);
   }
-  col_n.resize(nnz);
-  slot_map.resize(nnz);
-  fpos.resize(nnz);
-  std::atomic<int> bad{0};
-  parallel_ranges(N, 4096, [&](int64_t j0, int64_t j1) {
-    std::vector<int32_t> owners;
-    for (int64_t j = j0; j < j1; ++j) {
-      int32_t o = perm[j];
-      int32_t q0 = rowptr[o], q1 = rowptr[o + 1];
-      owners.clear();
-      for (int32_t q = q0; q < q1; ++q) {
-        int32_t ow = owner[iperm[col[q]]];
-        if (std::find(owners.begin(), owners.end(), ow) == owners.end()) owners.push_back(ow);
-      }
-      std::sort(owners.begin(), owners.end());
-      int s = owner[j];
-      int a = sptr[s], e = sptr[s + 1], k = e - a;
-      const int32_t* ps = upd_idx.data() + upd_ptr[s];
-      const int32_t* pe = upd_idx.data() + upd_ptr[s + 1];
-      int64_t t = rowptr_n[j];
-      for (int32_t ow : owners)
-        for (int32_t q = q0; q < q1; ++q) {
-          int32_t i = iperm[col[q]];
-          if (owner[i] != ow) continue;
-          if (t > rowptr_n[j] && col_n[t - 1] >= i) bad = 1;
-          col_n[t] = i;
-          slot_map[t] = q;
-          fpos[t] = -1;
-          if (i >= j) {
-            if (i < e) {
-              fpos[t] = i - a;
-            } else {
-              const int32_t* w = std::lower_bound(ps, pe, i);
-              if (w == pe || *w != i) bad = 2;
-              else fpos[t] = k + (int32_t)(w - ps);
-            }
-          }
-          ++t;
-        }
-    }
-  });
-  if (bad == 1) throw std::logic_error("ND-ordered row is not ascending");
-  if (bad == 2) throw std::logic_error("matrix entry outside the front");
 
   // level sets
   lvl_ptr.assign(nlevels + 1, 0);

@@ -54,11 +54,9 @@ struct Plan {
   std::vector<int32_t> parent, level, upd_ptr, upd_idx;
   int nlevels = 0;
   std::vector<int32_t> child_ptr, child_idx;  // children of each supernode
-  // ND-ordered CSR (columns ascending) and the map to original slots
+  // row pointers of the ND-ordered CSR (its columns, original slots and front
+  // rows are formed on the device when the problem is analysed)
   std::vector<int32_t> rowptr_n;
-  ivec col_n;
-  ivec slot_map;                   // slot_map[new slot] = original slot (nnz < 2^31)
-  ivec fpos;                       // front row of a new-order slot, -1 if col < row
   // front storage layout
   std::vector<int64_t> loff;       // factor panel of s: (k+u) x k, column-major
   std::vector<int64_t> uoff;       // update block of s: u x u, column-major
