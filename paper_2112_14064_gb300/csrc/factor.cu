@@ -71,21 +71,34 @@ FrontArgs<float> front_args<float>(Problem& P) {
                           P.Uval32.p,    P.Dinv32.p,  P.Dval32.p,  P.status.p};
 }
 
+// Assembly of the fronts of one level: nsplit CTAs per front, CTA `part`
+// owning the front columns [part F / nsplit, (part + 1) F / nsplit).  Every
+// front entry belongs to one column, so the CTAs of a front never write the
+// same entry; each zeroes its columns of the panel L (pivot columns) and of
+// the update block U, scatters the original entries of its pivot columns,
+// and adds the children's update blocks in child order (the child columns
+// that map into its range are contiguous: relmap is increasing).
 template <class T>
-__global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, const int32_t* rowptr_n,
-                                 const int32_t* fpos, const double* Kn, const double* Mn,
-                                 const double* Cn, double s2, double s1) {
-  int s = A.lvl_nodes[lvl_begin + blockIdx.x];
+__global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, int nsplit,
+                                 const int32_t* rowptr_n, const int32_t* fpos, const double* Kn,
+                                 const double* Mn, const double* Cn, double s2, double s1) {
+  const int f = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
+  int s = A.lvl_nodes[lvl_begin + f];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
   int64_t F = k + u;
+  const int c_lo = (int)(F * part / nsplit), c_hi = (int)(F * (part + 1) / nsplit);
   T* L = A.Lval + A.loff[s];
   T* U = A.Uval + A.uoff[s];
-  for (int64_t i = threadIdx.x; i < F * k; i += blockDim.x) L[i] = T(0);
-  for (int64_t i = threadIdx.x; i < (int64_t)u * u; i += blockDim.x) U[i] = T(0);
+  // zero the owned columns
+  const int lk_lo = min(c_lo, k), lk_hi = min(c_hi, k);          // pivot columns
+  const int uk_lo = max(c_lo, k) - k, uk_hi = max(c_hi, k) - k;  // update-block columns
+  for (int64_t i = threadIdx.x; i < F * (lk_hi - lk_lo); i += blockDim.x) L[F * lk_lo + i] = T(0);
+  for (int64_t i = threadIdx.x; i < (int64_t)u * (uk_hi - uk_lo); i += blockDim.x)
+    U[(int64_t)u * uk_lo + i] = T(0);
   __syncthreads();
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int t = warp; t < k; t += nw) {
+  for (int t = lk_lo + warp; t < lk_hi; t += nw) {
     int j = a + t;
     for (int32_t q = rowptr_n[j] + lane; q < rowptr_n[j + 1]; q += 32) {
       int pos = fpos[q];
@@ -98,7 +111,21 @@ __global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, const int32_t* r
     int uc = A.upd_ptr[c + 1] - A.upd_ptr[c];
     const int32_t* rm = A.relmap + A.upd_ptr[c];
     const T* Uc = A.Uval + A.uoff[c];
-    for (int q = warp; q < uc; q += nw) {
+    // child columns q with rm[q] in [c_lo, c_hi)
+    int q_lo = 0, h = uc;
+    while (q_lo < h) {
+      const int mid = (q_lo + h) >> 1;
+      if (rm[mid] < c_lo) q_lo = mid + 1;
+      else h = mid;
+    }
+    int q_hi = q_lo;
+    h = uc;
+    while (q_hi < h) {
+      const int mid = (q_hi + h) >> 1;
+      if (rm[mid] < c_hi) q_hi = mid + 1;
+      else h = mid;
+    }
+    for (int q = q_lo + warp; q < q_hi; q += nw) {
       int pc = rm[q];
       for (int r = q + lane; r < uc; r += 32) {
         int pr = rm[r];
@@ -119,7 +146,7 @@ template <class T>
 __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* lb = reinterpret_cast<T*>(dyn_smem);
-  __shared__ T dsh;
+  __shared__ T dsh, rdsh;   // pivot and its reciprocal (one FP64 division per pivot)
   int s = fronts[blockIdx.x];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
   int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
@@ -134,13 +161,14 @@ __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
         d = T(1);  // keep going with a harmless value; the host reports the failure
       }
       dsh = d;
+      rdsh = T(1) / d;
       L[t + F * t] = T(1);
-      A.Dinv[a + t] = T(1) / d;
+      A.Dinv[a + t] = rdsh;
       A.Dval[a + t] = d;
     }
     __syncthreads();
     T d = dsh;
-    T rd = T(1) / d;
+    T rd = rdsh;
     for (int i = t + 1 + threadIdx.x; i < k; i += blockDim.x) {
       T l = L[i + F * t] * rd;
       lb[i] = l;
@@ -197,6 +225,7 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
   __shared__ T bl[32][33];                 // L_JJ
   __shared__ T bx[32][33];                 // inv(L_JJ)
   __shared__ T dv[32];
+  __shared__ T rdv;                        // 1 / pivot, formed once
   const int s = fronts[blockIdx.x / CS];
   const int a = A.sptr[s], k = A.sptr[s + 1] - a;
   const int u = A.upd_ptr[s + 1] - A.upd_ptr[s];
@@ -221,9 +250,10 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
             d = T(1);  // keep going with a harmless value; the host reports the failure
           }
           dv[t] = d;
+          rdv = T(1) / d;
         }
         __syncthreads();
-        const T d = dv[t], rd = T(1) / d;
+        const T d = dv[t], rd = rdv;
         for (int r = t + 1 + tid; r < R; r += 256) Y[r + R * t] *= rd;
         __syncthreads();
         for (int c = t + 1 + warp; c < jb; c += 8) {
@@ -798,8 +828,10 @@ void launch_factor_t(Problem& P, double sigma) {
   const int4* tiles = (const int4*)P.tile_items.p;
   for (int l = 0; l < L.nlevels; ++l) {
     int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
-    k_front_assemble<T><<<cnt, 256, 0, s>>>(A, b, P.rowptr_n.p, P.fpos.p, P.Kn.p, P.Mn.p, P.Cn.p,
-                                            sigma * sigma, sigma);
+    // several CTAs per front on levels with few fronts (about two CTAs per SM)
+    const int nsplit = std::max(1, std::min(P.lvl_maxF[l] / 32, (2 * 152 + cnt - 1) / cnt));
+    k_front_assemble<T><<<cnt * nsplit, 256, 0, s>>>(A, b, nsplit, P.rowptr_n.p, P.fpos.p, P.Kn.p,
+                                                     P.Mn.p, P.Cn.p, sigma * sigma, sigma);
     RQ_CUDA(cudaGetLastError());
     const int nsm = P.piv_lvl[2 * l + 1] - P.piv_lvl[2 * l];
     const int nbig = P.piv_lvl[2 * l + 2] - P.piv_lvl[2 * l + 1];
