@@ -237,12 +237,15 @@ __device__ void rotate(Smem& S, int m, int j, double c, double s, int lane) {
 // Returns true when the block stays a complex pair.  With a queue (during the
 // QR iteration) only the block itself is rotated here and the rotation is
 // appended to the open batch for the rest of T and for Z.
-__device__ bool standardize2(Smem& S, int m, int j, int lane, Queue* q = nullptr) {
+// Rotation (c, s) that standardises the 2x2 block at j (no synchronisation;
+// any number of threads may compute it).  Returns 0 when the block is
+// already split (T[j+1, j] = 0), 1 when its eigenvalues are real, 2 when they
+// are a complex pair.
+__device__ int std2_params(const Smem& S, int j, double& c, double& s) {
   double a = TT(j, j), b = TT(j, j + 1), e = TT(j + 1, j), d = TT(j + 1, j + 1);
-  if (e == 0.0) return false;
+  if (e == 0.0) return 0;
   double hp = 0.5 * (a - d);
   double disc = hp * hp + b * e;
-  double c, s;
   bool cplx;
   if (disc >= 0.0) {
     // eigenvector of the eigenvalue l1; g1 = (c, s) spans it
@@ -278,6 +281,14 @@ __device__ bool standardize2(Smem& S, int m, int j, int lane, Queue* q = nullptr
     }
     cplx = true;
   }
+  return cplx ? 2 : 1;
+}
+
+__device__ bool standardize2(Smem& S, int m, int j, int lane, Queue* q = nullptr) {
+  double c, s;
+  const int kind = std2_params(S, j, c, s);
+  if (kind == 0) return false;
+  const bool cplx = kind == 2;
   if (q) {
     rotate_block(S, m, j, c, s, lane);
     if (lane == 0) {
@@ -302,8 +313,12 @@ __device__ bool standardize2(Smem& S, int m, int j, int lane, Queue* q = nullptr
   return cplx;
 }
 
-// Swap the adjacent diagonal blocks at j (size n1) and j+n1 (size n2).
-__device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm, int lane) {
+// Reflectors of the swap of the adjacent diagonal blocks at j (size n1) and
+// j+n1 (size n2): the Sylvester equation A X - X B = C, then the Householder
+// QR of [X; -I] (n2 reflectors of length n - q in vh[q], tau[q]).  No
+// synchronisation; any number of threads may compute it.
+__device__ void swap_setup(const Smem& S, int j, int n1, int n2, double tnorm, double (&vh)[2][4],
+                           double (&tau)[2]) {
   int n = n1 + n2;
   double A[2][2], B[2][2], Cm[2][2];
   for (int r = 0; r < n1; ++r)
@@ -358,7 +373,6 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
     for (int c = 0; c < n2; ++c) W[r][c] = xs[r + n1 * c];
   for (int r = 0; r < n2; ++r)
     for (int c = 0; c < n2; ++c) W[n1 + r][c] = (r == c) ? -1.0 : 0.0;
-  double vh[2][4], tau[2];
   for (int q = 0; q < n2; ++q) {
     double x[4];
     for (int i = q; i < n; ++i) x[i - q] = W[i][q];
@@ -373,6 +387,13 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
       for (int i = q; i < n; ++i) W[i][c] -= s * vh[q][i];
     }
   }
+}
+
+// Swap the adjacent diagonal blocks at j (size n1) and j+n1 (size n2).
+__device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm, int lane) {
+  const int n = n1 + n2;
+  double vh[2][4], tau[2];
+  swap_setup(S, j, n1, n2, tnorm, vh, tau);
   __syncthreads();
   for (int q = 0; q < n2; ++q) {
     apply_left(S.T, S.ld, vh[q], tau[q], n, j, j, m, lane);
@@ -386,6 +407,151 @@ __device__ void swap_blocks(Smem& S, int m, int j, int n1, int n2, double tnorm,
   __syncthreads();
   if (n2 == 2) standardize2(S, m, j, lane);
   if (n1 == 2) standardize2(S, m, j + n2, lane);
+}
+
+// ---- block reordering in parallel rounds ----
+// In each round every unselected block directly above a selected block swaps
+// with it; such pairs occupy disjoint diagonal ranges, so up to one pair per
+// warp is swapped at once.  Each warp forms its pair's reflectors and
+// standardising rotations; the updates then run in phases separated by CTA
+// barriers: every warp's left (row) updates, then every warp's right (column)
+// updates of T and Z.  Left updates of different pairs touch disjoint rows,
+// right updates disjoint columns, and a left and a right update commute, so
+// the result is that of the same swaps one after another.
+constexpr int kMaxPairs = kMaxKrylov / 2;
+
+// rows r0..r0+n-1 of A <- P rows, columns c0..c1-1, the lanes of one warp
+__device__ void warp_apply_left(double* A, int ld, const double* v, double tau, int n, int r0,
+                                int c0, int c1, int wl) {
+  if (tau == 0.0) return;
+  for (int c = c0 + wl; c < c1; c += 32) {
+    double sd = 0.0;
+    for (int i = 0; i < n; ++i) sd += v[i] * A[(r0 + i) + ld * c];
+    sd *= tau;
+    for (int i = 0; i < n; ++i) A[(r0 + i) + ld * c] -= sd * v[i];
+  }
+}
+
+// T columns c0..c0+n-1 (rows 0..r1-1) and Z columns c0..c0+n-1 (all rows)
+// <- cols P, the lanes of one warp
+__device__ void warp_apply_right_tz(double* T, double* Z, int m, int ld, const double* v,
+                                    double tau, int n, int c0, int r1, int wl) {
+  if (tau == 0.0) return;
+  for (int q = wl; q < r1 + m; q += 32) {
+    double* A = q < r1 ? T : Z;
+    int r = q < r1 ? q : q - r1;
+    double sd = 0.0;
+    for (int i = 0; i < n; ++i) sd += v[i] * A[r + ld * (c0 + i)];
+    sd *= tau;
+    for (int i = 0; i < n; ++i) A[r + ld * (c0 + i)] -= sd * v[i];
+  }
+}
+
+// Moves the selected blocks (S.sel) to the top of T; returns their size.
+__device__ int reorder_parallel(Smem& S, int m, double tnorm, int lane) {
+  __shared__ int npair, pj[kMaxPairs], pn1[kMaxPairs], pn2[kMaxPairs];
+  const int warp = lane >> 5, wl = lane & 31;
+  constexpr int kW = NT / 32;
+  for (int round = 0; round < 2 * m; ++round) {
+    if (lane == 0) {
+      // (unselected, selected) neighbours, top down, each block in one pair
+      int np = 0, pos = 0, up = -1, un = 0;
+      while (pos < m) {
+        const int bs = (pos + 1 < m && TT(pos + 1, pos) != 0.0) ? 2 : 1;
+        if (S.sel[pos] && up >= 0 && np < kMaxPairs) {
+          pj[np] = up;
+          pn1[np] = un;
+          pn2[np] = bs;
+          ++np;
+          up = -1;
+        } else {
+          up = S.sel[pos] ? -1 : pos;
+          un = bs;
+        }
+        pos += bs;
+      }
+      npair = np;
+    }
+    __syncthreads();
+    const int np = npair;
+    if (np == 0) break;
+    for (int g0 = 0; g0 < np; g0 += kW) {
+      const bool act = warp < np - g0;
+      const int pi = g0 + warp;
+      int j = 0, n1 = 0, n2 = 0, cf_sel[2] = {0, 0}, cf_oth[2] = {0, 0};
+      double vh[2][4], tau[2] = {0.0, 0.0};
+      if (act) {
+        j = pj[pi];
+        n1 = pn1[pi];
+        n2 = pn2[pi];
+        cf_oth[0] = S.cflag[j];
+        cf_oth[1] = n1 == 2 ? S.cflag[j + 1] : 0;
+        cf_sel[0] = S.cflag[j + n1];
+        cf_sel[1] = n2 == 2 ? S.cflag[j + n1 + 1] : 0;
+        swap_setup(S, j, n1, n2, tnorm, vh, tau);
+      }
+      const int n = n1 + n2;
+      __syncthreads();
+      for (int q = 0; q < 2; ++q) {
+        if (act && q < n2) warp_apply_left(S.T, S.ld, vh[q], tau[q], n, j, j, m, wl);
+        __syncthreads();
+        if (act && q < n2) warp_apply_right_tz(S.T, S.Z, m, S.ld, vh[q], tau[q], n, j, j + n, wl);
+        __syncthreads();
+      }
+      if (act && wl == 0)
+        for (int r = j + n2; r < j + n; ++r)
+          for (int c = j; c < j + n2; ++c) TT(r, c) = 0.0;
+      __syncthreads();
+      // standardise the new blocks at j (size n2) and j + n2 (size n1)
+      int rk[2] = {0, 0}, rj[2] = {j, j + n2};
+      double rc[2] = {1.0, 1.0}, rs[2] = {0.0, 0.0};
+      if (act) {
+        if (n2 == 2) rk[0] = std2_params(S, j, rc[0], rs[0]);
+        if (n1 == 2) rk[1] = std2_params(S, j + n2, rc[1], rs[1]);
+      }
+      __syncthreads();
+      for (int b = 0; b < 2; ++b)   // left: rows j', j'+1, columns from j'
+        if (act && rk[b])
+          for (int col = rj[b] + wl; col < m; col += 32) {
+            const double x = TT(rj[b], col), y = TT(rj[b] + 1, col);
+            TT(rj[b], col) = rc[b] * x + rs[b] * y;
+            TT(rj[b] + 1, col) = -rs[b] * x + rc[b] * y;
+          }
+      __syncthreads();
+      for (int b = 0; b < 2; ++b)   // right: columns j', j'+1 of T (rows <= j'+1) and Z
+        if (act && rk[b])
+          for (int r = wl; r < m; r += 32) {
+            if (r <= rj[b] + 1) {
+              const double x = TT(r, rj[b]), y = TT(r, rj[b] + 1);
+              TT(r, rj[b]) = rc[b] * x + rs[b] * y;
+              TT(r, rj[b] + 1) = -rs[b] * x + rc[b] * y;
+            }
+            const double x = ZZ(r, rj[b]), y = ZZ(r, rj[b] + 1);
+            ZZ(r, rj[b]) = rc[b] * x + rs[b] * y;
+            ZZ(r, rj[b] + 1) = -rs[b] * x + rc[b] * y;
+          }
+      __syncthreads();
+      if (act && wl == 0) {
+        for (int b = 0; b < 2; ++b) {
+          const int jj = rj[b];
+          if (rk[b] == 1) {
+            TT(jj + 1, jj) = 0.0;
+          } else if (rk[b] == 2) {
+            const double avg = 0.5 * (TT(jj, jj) + TT(jj + 1, jj + 1));
+            TT(jj, jj) = avg;
+            TT(jj + 1, jj + 1) = avg;
+          }
+        }
+        // the selected block now starts at j; keep the flags in step
+        for (int i = 0; i < n2; ++i) { S.sel[j + i] = 1; S.cflag[j + i] = cf_sel[i]; }
+        for (int i = 0; i < n1; ++i) { S.sel[j + n2 + i] = 0; S.cflag[j + n2 + i] = cf_oth[i]; }
+      }
+      __syncthreads();
+    }
+  }
+  int k = 0;
+  while (k < m && S.sel[k]) ++k;
+  return k;
 }
 
 // Sum over the CTA; every thread gets the result.
@@ -1134,39 +1300,14 @@ __device__ void ritz_main(const RitzArgs& R, Smem& S, Queue& Q, double* wbuf, in
   }
   __syncthreads();
   // reorder: move selected blocks to the top
-  int ks = 0, pos = 0;
-  while (pos < m) {
-    int bs = (pos + 1 < m && TT(pos + 1, pos) != 0.0) ? 2 : 1;
-    if (S.sel[pos]) {
-      int here = pos;
-      while (here > ks) {
-        int nbf = (here >= 2 && TT(here - 1, here - 2) != 0.0) ? 2 : 1;
-        int prev = here - nbf;
-        int cf_sel[2] = {S.cflag[here], bs == 2 ? S.cflag[here + 1] : 0};
-        int cf_oth[2] = {S.cflag[prev], nbf == 2 ? S.cflag[prev + 1] : 0};
-        __syncthreads();
-        swap_blocks(S, m, prev, nbf, bs, tnorm, lane);
-        // the selected block now starts at prev; keep the flags in step
-        __syncthreads();
-        if (lane == 0) {
-          for (int i = 0; i < bs; ++i) { S.sel[prev + i] = 1; S.cflag[prev + i] = cf_sel[i]; }
-          for (int i = 0; i < nbf; ++i) { S.sel[prev + bs + i] = 0; S.cflag[prev + bs + i] = cf_oth[i]; }
-        }
-        __syncthreads();
-        here = prev;
-      }
-      ks += bs;
-    }
-    pos += bs;
-  }
+  const int k = reorder_parallel(S, m, tnorm, lane);
   __syncthreads();
-  int k = ks;
   t_ph[5] = clock64();
   // locking: converged blocks among the kept ones move to the front (after
   // the blocks locked earlier); their spike entries are dropped below, which
   // decouples them from the rest of the projected matrix
   int nl = R.lock;
-  pos = R.lock;
+  int pos = R.lock;
   while (pos < k) {
     int bs = (pos + 1 < m && TT(pos + 1, pos) != 0.0) ? 2 : 1;
     bool conv = S.cflag[pos] && (bs == 1 || S.cflag[pos + 1]);
