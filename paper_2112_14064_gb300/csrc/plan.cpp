@@ -17,6 +17,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <iterator>
 #include <stdexcept>
 #include <thread>
@@ -186,6 +187,9 @@ void Plan::build_symbolic() {
   std::vector<std::vector<int32_t>> kids(nsuper);
   std::vector<std::vector<int32_t>> st(nsuper);
   parallel_ranges(nsuper, 64, [&](int64_t s0, int64_t s1) {
+    // stamp[i] = the last supernode that listed i: each neighbour is kept
+    // once, so only the distinct entries are sorted
+    std::vector<int32_t> stamp(N, -1);
     for (int64_t s = s0; s < s1; ++s) {
       int a = sptr[s], e = sptr[s + 1];
       std::vector<int32_t>& S = st[s];
@@ -193,11 +197,13 @@ void Plan::build_symbolic() {
         int32_t o = perm[j];
         for (int32_t q = rowptr[o]; q < rowptr[o + 1]; ++q) {
           int32_t i = iperm[col[q]];
-          if (i >= e) S.push_back(i);
+          if (i >= e && stamp[i] != (int32_t)s) {
+            stamp[i] = (int32_t)s;
+            S.push_back(i);
+          }
         }
       }
       std::sort(S.begin(), S.end());
-      S.erase(std::unique(S.begin(), S.end()), S.end());
     }
   });
   std::vector<int32_t> merged;
@@ -248,22 +254,30 @@ void Plan::build_symbolic() {
   u_total = uoff[nsuper];
 
   // extend-add maps: struct(s) -> rows of the parent's front
+  // (independent per supernode: host threads)
   relmap.assign(upd_idx.size(), -1);
-  for (int s = 0; s < nsuper; ++s) {
-    int pa = parent[s];
-    if (pa < 0) continue;
-    int a = sptr[pa], e = sptr[pa + 1], k = e - a;
-    const int32_t* ps = upd_idx.data() + upd_ptr[pa];
-    int pu = upd_ptr[pa + 1] - upd_ptr[pa];
-    int w = 0;
-    for (int32_t q = upd_ptr[s]; q < upd_ptr[s + 1]; ++q) {
-      int32_t i = upd_idx[q];
-      if (i < e) { relmap[q] = i - a; continue; }
-      while (w < pu && ps[w] < i) ++w;
-      if (w >= pu || ps[w] != i) throw std::logic_error("child structure not in parent front");
-      relmap[q] = k + w;
+  std::atomic<int> outside{0};
+  parallel_ranges(nsuper, 64, [&](int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s) {
+      int pa = parent[s];
+      if (pa < 0) continue;
+      int a = sptr[pa], e = sptr[pa + 1], k = e - a;
+      const int32_t* ps = upd_idx.data() + upd_ptr[pa];
+      int pu = upd_ptr[pa + 1] - upd_ptr[pa];
+      int w = 0;
+      for (int32_t q = upd_ptr[s]; q < upd_ptr[s + 1]; ++q) {
+        int32_t i = upd_idx[q];
+        if (i < e) { relmap[q] = i - a; continue; }
+        while (w < pu && ps[w] < i) ++w;
+        if (w >= pu || ps[w] != i) {
+          outside = 1;
+          break;
+        }
+        relmap[q] = k + w;
+      }
     }
-  }
+  });
+  if (outside) throw std::logic_error("child structure not in parent front");
 
   // row pointers of the ND-ordered CSR (row j is the original row perm[j])
   rowptr_n.assign(N + 1, 0);
