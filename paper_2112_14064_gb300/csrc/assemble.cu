@@ -102,25 +102,34 @@ __global__ void k_assemble_rows(Tables T, const int32_t* rowptr, const int32_t* 
     int jx = c % n1, jy = c / n1;
     int ex0 = max(T.elo[ix], T.elo[jx]), ex1 = min(T.ehi[ix], T.ehi[jx]);
     int ey0 = max(T.elo[iy], T.elo[jy]), ey1 = min(T.ehi[iy], T.ehi[jy]);
-    double sm = 0.0, sk = 0.0, sc = 0.0;
+    // The shared elements are the product [ex0, ex1) x [ey0, ey1), so the
+    // element sums of M and K factor into 1-D sums:
+    //   M = (sum_x m_x)(sum_y m_y),  K = (sum_x k_x)(sum_y m_y) + (sum_x m_x)(sum_y k_y);
+    // C = sum_y m_y sum_x sigma(x, y) m_x keeps its double sum.
+    double mxs[kMaxP + 1];
+    double Mx = 0.0, Kx = 0.0;
+    for (int ex = ex0; ex < ex1; ++ex) {
+      int g0 = T.first_fn[ex];
+      int ax = ix + 1 - g0, bx = jx + 1 - g0;
+      double mx = m1[((int64_t)ex * np1 + ax) * np1 + bx];
+      mxs[ex - ex0] = mx;
+      Mx += mx;
+      Kx += k1[((int64_t)ex * np1 + ax) * np1 + bx];
+    }
+    double My = 0.0, Ky = 0.0, sc = 0.0;
     for (int ey = ey0; ey < ey1; ++ey) {
       int f0 = T.first_fn[ey];
       int ay = iy + 1 - f0, by = jy + 1 - f0;
       double my = m1[((int64_t)ey * np1 + ay) * np1 + by];
-      double ky = k1[((int64_t)ey * np1 + ay) * np1 + by];
-      for (int ex = ex0; ex < ex1; ++ex) {
-        int g0 = T.first_fn[ex];
-        int ax = ix + 1 - g0, bx = jx + 1 - g0;
-        double mx = m1[((int64_t)ex * np1 + ax) * np1 + bx];
-        double kx = k1[((int64_t)ex * np1 + ax) * np1 + bx];
-        double mxy = mx * my;
-        sm += mxy;
-        sk += kx * my + mx * ky;
-        sc += sig[ex + (int64_t)T.ne * ey] * mxy;
-      }
+      My += my;
+      Ky += k1[((int64_t)ey * np1 + ay) * np1 + by];
+      const double* sg = sig + ex0 + (int64_t)T.ne * ey;
+      double in = 0.0;
+      for (int ex = ex0; ex < ex1; ++ex) in += sg[ex - ex0] * mxs[ex - ex0];
+      sc += my * in;
     }
-    K[q] = sk;
-    M[q] = sm;
+    K[q] = Kx * My + Mx * Ky;
+    M[q] = Mx * My;
     C[q] = sc;
   }
 }
