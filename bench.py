@@ -5,7 +5,7 @@ C^0 lines every 16 elements (82,369 DOFs): Gauss-quadrature assembly of
 K, M, C, the symbolic phase, the multifrontal factorisation and the
 Krylov-Schur eigensolve of the 20 eigenpairs nearest the target 500
 (FP64).  The spectral shift is placed inside the spectrum region (shift 0,
-56 candidates, Krylov dimension 88) and the selection nearest the target is
+56 candidates, Krylov dimension 96) and the selection nearest the target is
 certified; a pair counts only when its backward error is <= 1e-10 and the
 selection is certified.
 

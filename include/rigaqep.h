@@ -52,7 +52,8 @@ typedef enum {
   RIGAQEP_ERR_CUDA = 3,            /* a CUDA runtime call failed */
   RIGAQEP_ERR_OOM = 4,             /* device or host allocation failed */
   RIGAQEP_ERR_PIVOT = 5,           /* non-positive pivot in LDL^T (Q(s) not SPD) */
-  RIGAQEP_ERR_REFINEMENT = 6,      /* reserved: iterative refinement stagnated */
+  RIGAQEP_ERR_REFINEMENT = 6,      /* iterative refinement of the low-precision factor
+                                      does not contract (rigaqep_factor) */
   RIGAQEP_ERR_NO_CONVERGENCE = 7,  /* max_restarts reached; partial results returned */
   RIGAQEP_ERR_TIMEOUT = 8,         /* a bounded device-side wait gave up */
   RIGAQEP_ERR_INTERNAL = 9         /* a device-side consistency check failed */
@@ -86,9 +87,11 @@ typedef enum { RIGAQEP_FP64 = 0, RIGAQEP_FP32_IR = 2 } rigaqep_precision;
  *    shift inside the spectrum region; Q(shift) must be SPD, shift = 0 gives
  *    Q = K), the ncand pairs nearest the shift are converged, and the neig of
  *    them nearest the target sigma are returned.  The selection is certified
- *    (info.certified = 1) when no other eigenvalue can be nearer the target:
- *    every eigenvalue not converged lies at least r from the shift (r = the
- *    largest candidate distance), complex eigenvalues have
+ *    (info.certified = 1) when no other eigenvalue can be nearer the target,
+ *    assuming that every eigenvalue not converged lies at least r from the
+ *    shift (r = the largest candidate distance; Krylov-Schur converges the
+ *    eigenvalues nearest the shift first, but the call does not prove that
+ *    none was skipped), since complex eigenvalues have
  *    Re lambda in [-max sigma_e / 2, -min sigma_e / 2] (Rayleigh quotients of
  *    the QEP with K, M SPD and C = sum sigma_e M_e, sigma_e >= 0) and real
  *    ones are <= 0, which bounds their distance to the target from below. */
@@ -123,7 +126,11 @@ typedef struct {
   double factor_ms;      /* device time of the last rigaqep_factor */
   double eigs_ms;        /* device time of the last rigaqep_eigs */
   double fb_ms;          /* device time of its FB solves (CUDA events around each) */
-  int64_t certified;     /* 1: the returned pairs are provably the neig nearest the target */
+  int64_t certified;     /* 1: no eigenvalue outside the converged candidates can be nearer
+                            the target than the returned pairs, given that the candidates
+                            include every eigenvalue within their largest distance to the
+                            shift (what Krylov-Schur converges first, not proved by the
+                            call; checked against dense eigensolves in the tests) */
   double cert_margin;    /* lower bound on the distance of any other eigenvalue to the
                             target, minus the largest returned distance (>= 0 when certified) */
   int64_t n_launches;    /* kernels launched by the last eigs (including its factorisation) */

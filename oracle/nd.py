@@ -92,7 +92,8 @@ class Symbolic:
         return ch
 
     def nnz_L(self):
-        """Entries of the supernodal factor (dense lower pivot blocks)."""
+        """Entries of the supernodal factor (dense lower pivot blocks): the
+        storage a supernodal factorisation holds and its sweeps read."""
         tot = 0
         for s in range(self.nsuper):
             k = int(self.sptr[s + 1] - self.sptr[s])
@@ -102,7 +103,8 @@ class Symbolic:
 
     def factor_flops(self):
         """Cholesky flop count sum_j (c_j^2 + 2 c_j), c_j = off-diagonal
-        entries of column j in the supernodal structure."""
+        entries of column j in the supernodal structure (dense pivot
+        blocks: the work a supernodal factorisation executes)."""
         tot = 0
         for s in range(self.nsuper):
             k = int(self.sptr[s + 1] - self.sptr[s])
@@ -111,6 +113,42 @@ class Symbolic:
                 c = (k - 1 - t) + u
                 tot += c * c + 2 * c
         return tot
+
+    def scalar_col_counts(self, indptr, indices):
+        """Exact off-diagonal count c_j of every column of L (new order):
+        the textbook column structure with the elimination tree,
+        struct(j) = {i > j : Q_ij != 0} union the structures of j's
+        etree children less {j}, the etree parent of j being the first
+        entry of struct(j).  No supernodal amalgamation: pivot blocks count
+        only their structurally non-zero entries."""
+        N = len(self.perm)
+        kids = [[] for _ in range(N)]
+        st = [None] * N
+        cnt = np.zeros(N, dtype=np.int64)
+        for j in range(N):
+            o = self.perm[j]
+            nb = self.iperm[indices[indptr[o]:indptr[o + 1]]]
+            s = set(int(i) for i in nb if i > j)
+            for c in kids[j]:
+                s |= st[c]
+                st[c] = None
+            s.discard(j)
+            st[j] = s
+            cnt[j] = len(s)
+            if s:
+                kids[min(s)].append(j)
+        return cnt
+
+    def nnz_L_scalar(self, indptr, indices):
+        """Structurally non-zero entries of L including the diagonal,
+        sum_j (1 + c_j): the algorithmic size of the factor."""
+        return int((self.scalar_col_counts(indptr, indices) + 1).sum())
+
+    def factor_flops_scalar(self, indptr, indices):
+        """Algorithmic Cholesky flop count sum_j (c_j^2 + 2 c_j) with the
+        exact column counts c_j."""
+        c = self.scalar_col_counts(indptr, indices)
+        return int((c * c + 2 * c).sum())
 
 
 def symbolic(n, c0, p, indptr, indices, leaf_min=8, use_c0=True):

@@ -32,8 +32,10 @@ Target/shift split (the paper places its single shift inside the spectrum
 region of interest, Section 4.1.4): with a target t different from the shift
 s, the ncand pairs nearest s are converged and the neig of them nearest t are
 returned.  The choice is certified when no unconverged eigenvalue can be
-nearer t: every eigenvalue outside the candidates is at least r from s (r the
-largest candidate distance); for K, M SPD and C = sum sigma_e M_e with
+nearer t, under one assumption the Krylov iteration does not prove: that
+every eigenvalue within r of s (r the largest candidate distance) is among
+the candidates (Krylov--Schur converges the eigenvalues nearest the shift
+first).  Given that, for K, M SPD and C = sum sigma_e M_e with
 sigma_e >= 0, x^H(lambda^2 M + lambda C + K)x = 0 gives complex eigenvalues
 Re lambda = -x^H C x / (2 x^H M x) <= -min(sigma_e)/2 and real ones <= 0, so
 for 0 <= s <= t
@@ -193,6 +195,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
     res = EigsResult(lam_w, np.array(X), np.array(eta), int(conv[chosen].sum()), it,
                      n_apply, n_vv)
     res.certified = certified
+    res.candidates = lam_c        # the ncand converged values around the shift
     return res
 
 
