@@ -68,11 +68,28 @@ typedef struct {
   int32_t ne_x, ne_y, p, block_x, block_y, n_quad, leaf_min;
 } rigaqep_mesh_desc;
 
-/* Factor precision.  RIGAQEP_FP64: FP64 fronts and solves.  RIGAQEP_FP32_IR:
- * FP32 fronts and FP32 forward/backward sweeps, every solve refined in FP64
- * (x += Q32^{-1}(y - Q x) with the FP64 residual of the assembled K, M, C) for
- * a number of steps chosen when the factor is made (info.n_ir). */
-typedef enum { RIGAQEP_FP64 = 0, RIGAQEP_FP32_IR = 2 } rigaqep_precision;
+/* Factor precision (the paper does not state its own; these are the
+ * mixed-precision forms of Algorithm 2's "Factorize Q(s)" and of the solves of
+ * Section 4.2.2).
+ *  RIGAQEP_FP64: FP64 fronts and solves.
+ *  RIGAQEP_FP32_IR: FP32 fronts (SIMT) and FP32 forward/backward sweeps,
+ *    every solve refined in FP64 (x += Q32^{-1}(y - Q x) with the FP64
+ *    residual of the assembled K, M, C) for a number of steps chosen when
+ *    the factor is made (info.n_ir).
+ *  RIGAQEP_TF32_IR: as FP32_IR, with the dense products of every front
+ *    (L21 = F21 inv(L11)^T D^{-1}, the Schur update U -= L21 D L21^T and
+ *    W = L21 inv(L11)) on the tensor cores in TF32 with FP32 accumulation;
+ *    each operand is split into two TF32 terms (hi + lo, 22 significant bits)
+ *    and the product is hi*hi + hi*lo + lo*hi.  Pivot blocks stay FP32.
+ *  RIGAQEP_BF16_IR: the same products in BF16 (two BF16 terms, 16 bits),
+ *    with the pivot-scaled operands of each front multiplied by a power of
+ *    two that brings them near 1. */
+typedef enum {
+  RIGAQEP_FP64 = 0,
+  RIGAQEP_TF32_IR = 1,
+  RIGAQEP_FP32_IR = 2,
+  RIGAQEP_BF16_IR = 3
+} rigaqep_precision;
 
 /* Krylov-Schur options.  krylov_dim = m (neig < m <= 96), max_restarts
  * (0 selects 1000), tol = Ritz-estimate tolerance |h_{m+1,m} y_m|/|theta|
@@ -271,6 +288,19 @@ rigaqep_status rigaqep_grad_damping(rigaqep_problem* prob, int32_t neig,
  * them.  Synchronises the handle's stream before returning. */
 rigaqep_status rigaqep_grad_damping_noalloc(rigaqep_problem* prob, int32_t neig,
                                             const double* lambda, const double* X, double* G);
+
+/* The dense product of the front factorisation's tensor-core path, on its
+ * own: C = A B^T with A (m x k), B (n x k) and C (m x n) row-major FP32
+ * device arrays, computed by the same operand staging (two-term split) and
+ * tcgen05 kernels as the RIGAQEP_TF32_IR / RIGAQEP_BF16_IR fronts, on
+ * cuda_stream (a cudaStream_t; NULL = legacy default).  m, n <= 2^20,
+ * k <= 2^16; m = 0 or n = 0 does nothing.  Allocates its staging buffers
+ * from the library's pool; synchronises the stream.  Returns
+ * RIGAQEP_ERR_TIMEOUT if a bounded wait of the pipeline ran out.
+ * Defined by: Algorithm 2 ("Factorize Q(s)"): the Schur-complement and panel
+ * products of each front are this product. */
+rigaqep_status rigaqep_front_gemm(int32_t precision, int32_t m, int32_t n, int32_t k,
+                                  const float* A, const float* B, float* C, void* cuda_stream);
 
 /* Copy the original-order CSR (rowptr N+1, col nnz int32; K, M, C nnz
  * doubles) to host buffers; any pointer may be NULL to skip it. */

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "librigaqep.so")
-SOURCES = ["plan.cpp", "assemble.cu", "factor.cu", "krylov.cu", "ritz.cu", "capi.cu"]
+SOURCES = ["plan.cpp", "assemble.cu", "factor.cu", "tcfront.cu", "krylov.cu", "ritz.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(HERE, "..", "include")]

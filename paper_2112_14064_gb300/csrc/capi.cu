@@ -43,6 +43,10 @@ void need(bool cond, rigaqep_status code, const char* msg) {
   if (!cond) throw rq::Error(code, msg);
 }
 
+bool valid_precision(int32_t p) {
+  return p == RIGAQEP_FP64 || p == RIGAQEP_TF32_IR || p == RIGAQEP_FP32_IR || p == RIGAQEP_BF16_IR;
+}
+
 void check_mesh(const rigaqep_mesh_desc* m) {
   need(m != nullptr, RIGAQEP_ERR_ARG, "mesh descriptor is NULL");
   need(m->ne_x == m->ne_y && m->ne_x >= 2, RIGAQEP_ERR_ARG, "only square meshes ne_x == ne_y >= 2");
@@ -220,15 +224,15 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     rq::Problem& P = prob->impl;
     rq::StreamScope scope(P.stream);
     need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_factor");
-    need(precision == RIGAQEP_FP64 || precision == RIGAQEP_FP32_IR, RIGAQEP_ERR_ARG,
-         "precision must be RIGAQEP_FP64 or RIGAQEP_FP32_IR");
+    need(valid_precision(precision), RIGAQEP_ERR_ARG,
+         "precision must be RIGAQEP_FP64, RIGAQEP_TF32_IR, RIGAQEP_FP32_IR or RIGAQEP_BF16_IR");
     need(sigma == sigma, RIGAQEP_ERR_ARG, "sigma is NaN");
-    const bool fp32 = precision == RIGAQEP_FP32_IR;
+    const bool fp32 = precision != RIGAQEP_FP64;
     P.factored = false;
     P.cand_valid = false;
     RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
     RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
-    rq::launch_factor(P, sigma, fp32);
+    rq::launch_factor(P, sigma, precision);
     RQ_CUDA(cudaEventRecord(P.ev1, P.stream));
     rq::DevStatus st;
     RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
@@ -236,11 +240,14 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     float ms = 0.f;
     RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
     P.info.factor_ms = ms;
+    if (st.timeout)
+      throw rq::Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait of the tensor-core front products ran out");
     if (st.pivot_fail)
       throw rq::Error(RIGAQEP_ERR_PIVOT, "non-positive pivot in supernode " +
                                              std::to_string(st.pivot_fail - 1) +
                                              ": Q(sigma) is not positive definite");
     P.fact_fp32 = fp32;
+    P.fact_prec = precision;
     P.n_ir = 0;
     P.info.n_ir = 0;
     P.info.ir_residual = 0.0;
@@ -256,8 +263,8 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
           best = (int)k + 1;
         }
       if (best == 0 || !(best_res < 1e-6))
-        throw rq::Error(RIGAQEP_ERR_REFINEMENT, "FP64 refinement with the FP32 factor does not "
-                                                "contract (residual " + std::to_string(best_res) + ")");
+        throw rq::Error(RIGAQEP_ERR_REFINEMENT, "FP64 refinement with the low-precision factor "
+                                                "does not contract (residual " + std::to_string(best_res) + ")");
       P.n_ir = best;
       P.info.n_ir = best;
       P.info.ir_residual = best_res;
@@ -312,18 +319,17 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
     E.seed = opts ? opts->seed : 1;
     const int32_t prec = opts ? opts->precision : RIGAQEP_FP64;
-    need(prec == RIGAQEP_FP64 || prec == RIGAQEP_FP32_IR, RIGAQEP_ERR_ARG,
-         "precision must be RIGAQEP_FP64 or RIGAQEP_FP32_IR");
+    need(valid_precision(prec), RIGAQEP_ERR_ARG,
+         "precision must be RIGAQEP_FP64, RIGAQEP_TF32_IR, RIGAQEP_FP32_IR or RIGAQEP_BF16_IR");
     need(neig >= 1 && neig <= E.ncand, RIGAQEP_ERR_ARG, "need 1 <= neig <= ncand");
     need(E.ncand < E.m && E.m <= rq::kMaxKrylov, RIGAQEP_ERR_ARG, "need ncand < krylov_dim <= 96");
     need(E.m <= 2 * P.plan.N, RIGAQEP_ERR_ARG, "krylov_dim exceeds 2N");
     need(sigma > 0.0, RIGAQEP_ERR_ARG, "the target must be real and positive");
     need(!E.in_region || E.shift == E.shift, RIGAQEP_ERR_ARG, "shift is NaN");
     P.launches = 0;
-    if (!P.factored || P.fact_sigma != E.shift || P.fact_fp32 != (prec == RIGAQEP_FP32_IR)) {
+    if (!P.factored || P.fact_sigma != E.shift || P.fact_prec != prec) {
       rigaqep_status fs = rigaqep_factor(prob, E.shift, prec);
       if (fs != RIGAQEP_OK) throw rq::Error(fs, g_last_error);
-      P.launches = 2 * P.plan.nlevels;
     }
     int nconv = 0;
     rq::eigs_run(P, E, v1, lambda, X, eta, &nconv);
@@ -525,3 +531,19 @@ void rigaqep_destroy(rigaqep_problem* prob) {
 }
 
 }  // extern "C"
+
+rigaqep_status rigaqep_front_gemm(int32_t precision, int32_t m, int32_t n, int32_t k,
+                                  const float* A, const float* B, float* C, void* cuda_stream) {
+  return guard([&] {
+    need(precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR, RIGAQEP_ERR_ARG,
+         "precision must be RIGAQEP_TF32_IR or RIGAQEP_BF16_IR");
+    need(m >= 0 && n >= 0 && k >= 1, RIGAQEP_ERR_ARG, "need m, n >= 0 and k >= 1");
+    need(m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 16), RIGAQEP_ERR_ARG,
+         "need m, n <= 2^20 and k <= 2^16");
+    if (m == 0 || n == 0) return;
+    need(A != nullptr && B != nullptr && C != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rq::StreamScope scope(s);
+    rq::tc_plain_gemm(m, n, k, A, B, C, precision == RIGAQEP_BF16_IR, s);
+  });
+}

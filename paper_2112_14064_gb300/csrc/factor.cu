@@ -819,8 +819,10 @@ void factor_plan(Problem& P) {
   if (piv / 2 > 48 * 1024) smem_at_least((const void*)k_pivot_factor<float>, piv / 2);
 }
 
+// tc: the products after the pivot blocks (L21, the Schur update, W) run on
+// the tensor cores (tcfront.cu) instead of k_panel_rows / k_schur_tile
 template <class T>
-void launch_factor_t(Problem& P, double sigma) {
+void launch_factor_t(Problem& P, double sigma, bool tc = false) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FrontArgs<T> A = front_args<T>(P);
@@ -859,6 +861,10 @@ void launch_factor_t(Problem& P, double sigma) {
       ++P.launches;
     }
     ++P.launches;
+    if (tc) {
+      launch_tc_level(P, l);
+      continue;
+    }
     int rb = P.row_lvl[l], rc = P.row_lvl[l + 1] - rb;
     int tb = P.tile_lvl[l], tc = P.tile_lvl[l + 1] - tb;
     size_t smem = sizeof(T) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);
@@ -880,8 +886,8 @@ void launch_factor_t(Problem& P, double sigma) {
   }
 }
 
-void launch_factor(Problem& P, double sigma, bool fp32) {
-  if (fp32) {
+void launch_factor(Problem& P, double sigma, int precision) {
+  if (precision != RIGAQEP_FP64) {
     Plan& L = P.plan;
     if (P.Lval32.n < (size_t)L.l_total) {   // FP32 factor storage on first use
       P.Lval32.alloc(L.l_total);
@@ -893,7 +899,9 @@ void launch_factor(Problem& P, double sigma, bool fp32) {
       P.ir_y.alloc(L.N);
       P.ir_r32.alloc(L.N);
     }
-    launch_factor_t<float>(P, sigma);
+    const bool tc = precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR;
+    if (tc) tc_plan(P, precision == RIGAQEP_BF16_IR);
+    launch_factor_t<float>(P, sigma, tc);
   } else {
     launch_factor_t<double>(P, sigma);
   }

@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of rigaqep.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -113,7 +114,7 @@ struct DevStatus {
   int32_t pivot_fail;   // first failing supernode + 1 (0 = none)
   int32_t ritz_fail;    // QR iteration limit reached
   int32_t internal;     // consistency check failed
-  int32_t pad;
+  int32_t timeout;      // a bounded wait of a tensor-core pipeline ran out
 };
 
 // Output of the Ritz kernel.
@@ -128,6 +129,29 @@ struct RitzOut {
   long long phase_cycles[6];     // hessenberg, QR, eigenvalues+ranks, eigvecs, reorder, lock
   double lam[2 * kMaxKrylov];    // wanted lambdas (re, im), first neig
   double est[kMaxKrylov];        // Ritz estimates of the wanted pairs
+};
+
+// Staged-operand geometry of one front for the tensor-core products
+// (tcfront.cu): rows of the 128-byte K-block layout, counted from the start
+// of the front's level region.
+struct TcFront {
+  int32_t u, k, kb, a;                  // update rows, pivots, K-blocks, first pivot
+  int32_t offA3, offB3, offB5, offA4;   // F21, inv(L11) rows, inv(L11) columns, L21
+  int32_t offB4, nB0, pad0, pad1;       // Z; B rows of the plain product
+  int64_t loff, uoff;                   // FP32 panel and update-block offsets
+};
+static_assert(sizeof(TcFront) == 64, "TcFront layout");
+
+// Plan and buffers of the tensor-core products of one precision.
+struct TcPlan {
+  bool ready = false, bf16 = false;
+  DBuf<TcFront> fr;
+  DBuf<int32_t> stage, t3, t4, t5;      // stage items and output tiles (int4 each)
+  std::vector<int32_t> stage_lvl, t3_lvl, t4_lvl, t5_lvl;
+  std::vector<int32_t> n35, kbmax;      // per level: N of products (3), (5); K-blocks
+  DBuf<unsigned char> hi, lo;           // the two staged planes (split terms)
+  DBuf<float> scale;                    // per-front power of two (BF16)
+  CUtensorMap maps[4];                  // hi/lo planes, boxes of 128 and 64 rows
 };
 
 struct EigsParams {
@@ -172,7 +196,9 @@ struct Problem {
   // FP32 factor (mixed precision: FP32 fronts, FP64 iterative refinement)
   DBuf<float> Lval32, Uval32, Dinv32, Dval32, yvec32, zbuf32, ir_r32;
   DBuf<double> ir_y;
-  bool fact_fp32 = false;       // the current factor is the FP32 one
+  bool fact_fp32 = false;       // the current factor is stored in FP32 (FP32, TF32 or BF16 fronts)
+  int32_t fact_prec = RIGAQEP_FP64;   // precision of the current factor
+  TcPlan tc;                    // tensor-core products (TF32 / BF16 fronts)
   int n_ir = 0;                 // refinement steps per solve with the FP32 factor
   DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
   DBuf<int32_t> piv_fronts;     // per level: small pivot blocks, then cluster-sized ones
@@ -214,7 +240,13 @@ void launch_permute_values(Problem& P);
 // SELL-32 copy of the ND pattern with M and C (after launch_permute_values)
 void launch_sell(Problem& P);
 void launch_norms(Problem& P);
-void launch_factor(Problem& P, double sigma, bool fp32);
+// precision: RIGAQEP_FP64, RIGAQEP_FP32_IR, RIGAQEP_TF32_IR or RIGAQEP_BF16_IR
+void launch_factor(Problem& P, double sigma, int precision);
+// tensor-core products of the front factorisation (tcfront.cu)
+void tc_plan(Problem& P, bool bf16);
+void launch_tc_level(Problem& P, int level);
+void tc_plain_gemm(int m, int n, int K, const float* A, const float* B, float* C, bool bf16,
+                   cudaStream_t s);
 // relative residuals of FP64 refinement steps 1, 2, ... with the FP32 factor
 std::vector<double> ir_history(Problem& P, double sigma, int max_steps, double target,
                                uint64_t seed);

@@ -25,10 +25,11 @@ EXPORTS = [
     "rigaqep_grad_damping", "rigaqep_grad_damping_noalloc", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
+    "rigaqep_front_gemm",
 ]
 
 
-FP64, FP32_IR = 0, 2   # rigaqep_precision
+FP64, TF32_IR, FP32_IR, BF16_IR = 0, 1, 2, 3   # rigaqep_precision
 
 
 class RigaqepError(RuntimeError):
@@ -105,6 +106,7 @@ def load():
         "rigaqep_symbolic_sizes": [P, ctypes.POINTER(I64)],
         "rigaqep_symbolic_export": [P, P, P, P, P, P, P, P, P],
         "rigaqep_batch_eigs": [ctypes.POINTER(P), I32, ctypes.POINTER(BatchJob), I32, I32],
+        "rigaqep_front_gemm": [I32, I32, I32, I32, P, P, P, V],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -254,13 +256,26 @@ class Problem:
 
     def grad_damping_noalloc(self, lam, X, out=None):
         """Same as grad_damping, writing into the caller's buffer out (neig,
-        ne*ne, 2 float64) with no device allocation inside the library call."""
+        ne*ne, 2 float64) with no device allocation inside the library call.
+        lam (neig complex128) and X (neig x N complex128) must be on the
+        device of out; every shape, dtype and device is checked here, since
+        the library writes neig * ne^2 complex values through out."""
         torch = self._torch
+        if lam.dtype != torch.complex128 or X.dtype != torch.complex128:
+            raise ValueError("lam and X must be complex128")
+        if lam.dim() != 1 or X.dim() != 2 or X.shape[0] != lam.shape[0] or X.shape[1] != self.N:
+            raise ValueError(f"need lam (neig,) and X (neig, {self.N})")
         neig = lam.shape[0]
         lam_r = torch.view_as_real(lam.contiguous()).contiguous()
         X_r = torch.view_as_real(X.contiguous()).contiguous()
         if out is None:
             out = torch.empty((neig, self.ne * self.ne, 2), dtype=torch.float64, device=lam.device)
+        if (out.dtype != torch.float64 or not out.is_contiguous()
+                or tuple(out.shape) != (neig, self.ne * self.ne, 2)):
+            raise ValueError(f"out must be a contiguous float64 tensor of shape "
+                             f"({neig}, {self.ne * self.ne}, 2)")
+        if not (out.device == lam.device == X.device) or out.device.type != "cuda":
+            raise ValueError("lam, X and out must be on the same CUDA device")
         _check(self.lib.rigaqep_grad_damping_noalloc(self._h, neig, _ptr(lam_r), _ptr(X_r),
                                                      _ptr(out)))
         return torch.view_as_complex(out)
@@ -341,3 +356,24 @@ def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):
                         n_converged=J.n_converged, status=J.status, certified=J.certified,
                         reused_candidates=J.reused_candidates, eigs_ms=J.eigs_ms))
     return res
+
+
+def front_gemm(A, B, precision=TF32_IR, stream=None):
+    """C = A B^T on the tensor cores through the front factorisation's
+    staging and tcgen05 kernels (rigaqep_front_gemm); A (m x k), B (n x k):
+    contiguous float32 CUDA tensors.  Returns C (m x n float32)."""
+    import torch
+    if A.dtype != torch.float32 or B.dtype != torch.float32:
+        raise ValueError("A and B must be float32")
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[1]:
+        raise ValueError("need A (m x k) and B (n x k)")
+    if A.device.type != "cuda" or B.device != A.device:
+        raise ValueError("A and B must be on one CUDA device")
+    A, B = A.contiguous(), B.contiguous()
+    m, k = A.shape
+    n = B.shape[0]
+    C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    st = stream if stream is not None else torch.cuda.current_stream(A.device)
+    _check(load().rigaqep_front_gemm(precision, m, n, k, _ptr(A), _ptr(B), _ptr(C),
+                                     ctypes.c_void_p(st.cuda_stream)))
+    return C

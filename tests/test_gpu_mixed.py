@@ -1,5 +1,8 @@
-"""Mixed precision on the GPU: FP32 fronts and FP32 sweeps, every solve
-refined in FP64 against the assembled K, M, C (RIGAQEP_FP32_IR).
+"""Mixed precision on the GPU: FP32 factor storage and FP32 sweeps, every
+solve refined in FP64 against the assembled K, M, C.  Three front
+precisions: FP32 SIMT (RIGAQEP_FP32_IR), and the front products on the
+tensor cores in split TF32 (RIGAQEP_TF32_IR) or split BF16
+(RIGAQEP_BF16_IR).
 
 Tolerances:
 * solves: 1e-12 relative to the FP64 oracle solve (the refinement runs until
@@ -41,15 +44,26 @@ def _oracle(c):
 
 
 
-@pytest.mark.parametrize("name,sigma", [("tiny", 0.0), ("tiny", 20.0), ("p3_64_b16", 0.0)])
-def test_mixed_solve_matches_oracle(rq, name, sigma):
+PRECS = ["FP32_IR", "TF32_IR", "BF16_IR"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,sigma,over", [
+    ("tiny", 0.0, {}), ("tiny", 20.0, {}), ("p3_64_b16", 0.0, {}),
+    # fronts of several 128-row tiles and K-blocks: pivot blocks of 143 and
+    # update blocks of up to 287 rows
+    ("tiny", 5.0, dict(ne=128, p=3, block=16)),
+    # degree 5: wide macroelement separators (k not a multiple of 32)
+    ("tiny", 1.0, dict(ne=24, p=5, block=8))])
+def test_mixed_solve_matches_oracle(rq, name, sigma, over, prec):
     c = dict(workloads.CONFIGS[name])
+    c.update(over)
     A, sym = _oracle(c)
     F = factorize(sym, A.Q(sigma))
     b = np.random.default_rng(5).standard_normal((2, A.N))
     ref = np.stack([F.solve(bb) for bb in b])
     pr = rq.Problem(c["ne"], c["p"], c["block"], workloads.sigma_e(c)).analyze()
-    pr.factor(sigma, rq.FP32_IR)
+    pr.factor(sigma, getattr(rq, prec))
     inf = pr.info()
     assert inf["n_ir"] >= 1 and inf["ir_residual"] <= 1e-13
     x = pr.solve(torch.from_numpy(b).cuda()).cpu().numpy()
@@ -58,7 +72,8 @@ def test_mixed_solve_matches_oracle(rq, name, sigma):
     pr.close()
 
 
-def test_mixed_eigs_literal_shift_matches_oracle(rq):
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_eigs_literal_shift_matches_oracle(rq, prec):
     c = dict(workloads.CONFIGS["tiny"])
     A, sym = _oracle(c)
     v1 = workloads.start_vector(1, 2 * A.N)
@@ -66,7 +81,7 @@ def test_mixed_eigs_literal_shift_matches_oracle(rq):
     ref = qep.eigs(A.K, A.C, A.M, c["shift"], c["neig"], c["m"], F.solve, v1)
     pr = rq.Problem(c["ne"], c["p"], c["block"], workloads.sigma_e(c)).analyze()
     lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], m=c["m"],
-                                     v1=torch.from_numpy(v1).cuda(), precision=rq.FP32_IR)
+                                     v1=torch.from_numpy(v1).cuda(), precision=getattr(rq, prec))
     assert st == 0 and nconv == c["neig"]
     lam = lam.cpu().numpy()
     assert same_multiset(ref.lam, lam, 1e-9)
@@ -74,7 +89,8 @@ def test_mixed_eigs_literal_shift_matches_oracle(rq):
     pr.close()
 
 
-def test_mixed_eigs_in_region_matches_oracle(rq):
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_eigs_in_region_matches_oracle(rq, prec):
     c = dict(workloads.CONFIGS["p3_64_b16"])
     A, sym = _oracle(c)
     sig = workloads.sigma_e(c)
@@ -85,7 +101,7 @@ def test_mixed_eigs_in_region_matches_oracle(rq):
     assert ref.certified
     pr = rq.Problem(c["ne"], c["p"], c["block"], sig).analyze()
     lam, X, eta, nconv, st = pr.eigs(c["neig"], 500.0, m=96, v1=torch.from_numpy(v1).cuda(),
-                                     shift=0.0, ncand=56, precision=rq.FP32_IR)
+                                     shift=0.0, ncand=56, precision=getattr(rq, prec))
     assert st == 0 and pr.info()["certified"] == 1
     lam = lam.cpu().numpy()
     assert same_multiset(ref.lam, lam, 1e-9)
@@ -93,14 +109,15 @@ def test_mixed_eigs_in_region_matches_oracle(rq):
     pr.close()
 
 
-def test_mixed_against_fp64_full_size(rq):
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_against_fp64_full_size(rq, prec):
     """256 x 256, p = 3, blocks of 16, target 500 (the bench workload)."""
     c = dict(workloads.CONFIGS["p3_256_b16"])
     sig = torch.from_numpy(workloads.sigma_e(c)).cuda()
     kw = dict(m=96, shift=0.0, ncand=56, seed=1)
     pr = rq.Problem(c["ne"], c["p"], c["block"], sig).analyze()
     a = pr.eigs(c["neig"], c["shift"], **kw)[0].cpu().numpy()
-    lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], precision=rq.FP32_IR, **kw)
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], precision=getattr(rq, prec), **kw)
     inf = pr.info()
     assert st == 0 and inf["certified"] == 1 and inf["n_ir"] >= 1
     b = lam.cpu().numpy()
