@@ -328,6 +328,16 @@ rigaqep_status rigaqep_symbolic_export(const rigaqep_symbolic* sym, int32_t* per
                                        int32_t* level, int32_t* rowptr, int32_t* col);
 void rigaqep_symbolic_destroy(rigaqep_symbolic* sym);
 
+/* Number of polls after which a wait between the cooperating CTAs of the
+ * Ritz step (the batch queue of the QR iteration) gives up; the step then
+ * ends and rigaqep_eigs returns RIGAQEP_ERR_TIMEOUT, leaving the CUDA
+ * context usable.  Process-wide; 0 restores the default (2^22 polls, far
+ * beyond any wait of a correct run).  Meant for failure-injection tests: a
+ * limit of 1 makes the waits run out on any problem.  The waits of the TMA
+ * copies are not affected (a copy must land before its CTA exits).
+ * Defined by: no counterpart in the paper (failure reporting of the library). */
+void rigaqep_set_wait_limit(uint32_t polls);
+
 /* Thread-local message of the calling thread's last failed call ("" if none). */
 const char* rigaqep_last_error(void);
 

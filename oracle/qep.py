@@ -116,10 +116,12 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
     lock = 0        # leading Schur columns locked (converged, decoupled)
     n_apply = 0
     n_vv = 0
+    steps = []      # basis index j of every operator application, in order
     for it in range(max_restarts + 1):
         for j in range(k, m):
             r = apply_operator(V[:, j], s, M, C, solve)
             n_apply += 1
+            steps.append(j)
             for _ in range(2):                      # CGS2
                 h = V[:, :j + 1].T @ b_apply(r, M)
                 r = r - V[:, :j + 1] @ h
@@ -196,6 +198,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
                      n_apply, n_vv)
     res.certified = certified
     res.candidates = lam_c        # the ncand converged values around the shift
+    res.steps = steps
     return res
 
 

@@ -12,6 +12,16 @@
 
 #include "internal.h"
 
+namespace rq {
+namespace {
+std::atomic<uint32_t> g_wait_limit{kDefaultWaitLimit};
+}
+uint32_t ritz_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+void set_ritz_wait_limit(uint32_t polls) {
+  g_wait_limit.store(polls == 0 ? kDefaultWaitLimit : polls, std::memory_order_relaxed);
+}
+}  // namespace rq
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -126,6 +136,8 @@ rigaqep_status rigaqep_assemble(const rigaqep_mesh_desc* mesh, const double* sig
       rq::Problem& P = h->impl;
       P.stream = (cudaStream_t)cuda_stream;
       rq::StreamScope scope(P.stream);
+      RQ_CUDA(cudaGetDevice(&P.device));
+      RQ_CUDA(cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, P.device));
       P.plan.build_pattern(mesh->ne_x, mesh->p, mesh->block_x, mesh->n_quad, mesh->leaf_min);
       RQ_CUDA(cudaEventCreate(&P.ev0));
       RQ_CUDA(cudaEventCreate(&P.ev1));
@@ -360,6 +372,12 @@ rigaqep_status rigaqep_grad_damping_noalloc(rigaqep_problem* prob, int32_t neig,
   return guard([&] {
     need(prob != nullptr && lambda != nullptr && X != nullptr && G != nullptr, RIGAQEP_ERR_ARG,
          "NULL argument");
+    // the scratch array is looked up for the current device and the kernels
+    // run on the handle's stream: both must be the same GPU
+    int dev = -1;
+    RQ_CUDA(cudaGetDevice(&dev));
+    need(dev == prob->impl.device, RIGAQEP_ERR_STATE,
+         "the current device is not the device the problem was created on");
     rq::grad_run_noalloc(prob->impl, neig, lambda, X, G);
   });
 }
@@ -547,3 +565,5 @@ rigaqep_status rigaqep_front_gemm(int32_t precision, int32_t m, int32_t n, int32
     rq::tc_plain_gemm(m, n, k, A, B, C, precision == RIGAQEP_BF16_IR, s);
   });
 }
+
+void rigaqep_set_wait_limit(uint32_t polls) { rq::set_ritz_wait_limit(polls); }

@@ -831,7 +831,7 @@ void launch_factor_t(Problem& P, double sigma, bool tc = false) {
   for (int l = 0; l < L.nlevels; ++l) {
     int b = L.lvl_ptr[l], cnt = L.lvl_ptr[l + 1] - b;
     // several CTAs per front on levels with few fronts (about two CTAs per SM)
-    const int nsplit = std::max(1, std::min(P.lvl_maxF[l] / 32, (2 * 152 + cnt - 1) / cnt));
+    const int nsplit = std::max(1, std::min(P.lvl_maxF[l] / 32, (2 * P.nsm + cnt - 1) / cnt));
     k_front_assemble<T><<<cnt * nsplit, 256, 0, s>>>(A, b, nsplit, P.rowptr_n.p, P.fpos.p, P.Kn.p,
                                                      P.Mn.p, P.Cn.p, sigma * sigma, sigma);
     RQ_CUDA(cudaGetLastError());
@@ -973,7 +973,7 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
   }
   for (int l = L.nlevels - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
-    if (ic < 2 * 152)
+    if (ic < 2 * P.nsm)
       launch_pdl(k_fb_bwd<T, 8>, dim3(ic), dim3(256), bwd_smem<T>(8), s, A, ib, xn, sigma, vu, ru,
                  rl);
     else

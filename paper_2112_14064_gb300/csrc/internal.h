@@ -75,6 +75,12 @@ __device__ __forceinline__ void pdl_trigger() {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 #endif
 
+// Polls after which a wait between the CTAs of the Ritz step gives up
+// (process-wide; rigaqep_set_wait_limit).
+constexpr uint32_t kDefaultWaitLimit = 1u << 22;
+uint32_t ritz_wait_limit();
+void set_ritz_wait_limit(uint32_t polls);
+
 // Raises a kernel's dynamic shared memory limit to at least `bytes` (never
 // lowers it, so concurrent callers with different sizes cannot race a launch
 // below its own request).
@@ -146,9 +152,9 @@ static_assert(sizeof(TcFront) == 64, "TcFront layout");
 struct TcPlan {
   bool ready = false, bf16 = false;
   DBuf<TcFront> fr;
-  DBuf<int32_t> stage, t3, t4, t5;      // stage items and output tiles (int4 each)
-  std::vector<int32_t> stage_lvl, t3_lvl, t4_lvl, t5_lvl;
-  std::vector<int32_t> n35, kbmax;      // per level: N of products (3), (5); K-blocks
+  DBuf<int32_t> stage, t3, t45;         // stage items, tiles of (3), tiles of (4) and (5)
+  std::vector<int32_t> stage_lvl, t3_lvl, t45_lvl;
+  std::vector<int32_t> n35, kbmax;      // per level: N of product (3); K-blocks
   DBuf<unsigned char> hi, lo;           // the two staged planes (split terms)
   DBuf<float> scale;                    // per-front power of two (BF16)
   CUtensorMap maps[4];                  // hi/lo planes, boxes of 128 and 64 rows
@@ -168,6 +174,8 @@ struct EigsParams {
 struct Problem {
   Plan plan;
   cudaStream_t stream = nullptr;
+  int device = 0;               // CUDA device the handle was created on
+  int nsm = 1;                  // its multiprocessor count (grid sizing)
   bool analyzed = false;
   bool factored = false;
   double fact_sigma = 0.0;

@@ -748,7 +748,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   RQ_CUDA(cudaEventCreate(&W.rz[1]));
   W.Np = basis_np(L.N);
   W.ld = basis_ld(L.N);
-  W.nblk = 2 * 152;
+  W.nblk = 2 * P.nsm;
   int64_t ld = W.ld, Np = W.Np, N = L.N;
   P.V.alloc(ld * (m + 1));
   make_tmap_f64(&W.tV, P.V.p, (uint64_t)ld, (uint64_t)(m + 1), (uint64_t)ld, kTileRows, kBoxCols);
@@ -816,7 +816,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
       W.ritz_ms += ms;
     }
     if (h_out.fail == 2)
-      throw Error(RIGAQEP_ERR_INTERNAL, "a bounded wait between the Ritz-step CTAs ran out");
+      throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the Ritz-step CTAs ran out");
     if (h_out.fail) throw Error(RIGAQEP_ERR_INTERNAL, "QR iteration on the projected matrix did not converge");
     qr_sweeps += h_out.sweeps;
     for (int q = 0; q < 6; ++q) P.info.ritz_phase_cycles[q] += (double)h_out.phase_cycles[q];
@@ -976,7 +976,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   dim3 g((unsigned)((N + 255) / 256), neig);
   k_colnormalise<<<g, 256, 0, s>>>(X, N, stats.p);
   RQ_CUDA(cudaGetLastError());
-  int qb = 2 * 152;
+  int qb = 2 * P.nsm;
   dim3 gq(qb, neig);
   k_qres<<<gq, 256, 0, s>>>(P.rowptr.p, P.col.p, P.K.p, P.M.p, P.C.p, X, lambda, N, P.part.p);
   RQ_CUDA(cudaGetLastError());
@@ -988,7 +988,7 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaMemcpyAsync(&dst, P.status.p, sizeof(dst), cudaMemcpyDeviceToHost, s));
   RQ_CUDA(cudaStreamSynchronize(s));
   if (dst.internal)
-    throw Error(RIGAQEP_ERR_INTERNAL, "a bounded wait for a tensor-memory copy ran out");
+    throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait for a TMA copy of the basis ran out");
   float ms = 0.f;
   RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
   P.info.eigs_ms = ms;
@@ -1000,7 +1000,7 @@ void grad_run(Problem& P, int neig, const double* lambda, const double* X, doubl
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   int64_t N = L.N;
-  int nb = 2 * 152;
+  int nb = 2 * P.nsm;
   DBuf<double> part, den;
   part.alloc(2 * (size_t)nb * neig);
   den.alloc(2 * (size_t)neig);
@@ -1020,7 +1020,9 @@ void grad_run(Problem& P, int neig, const double* lambda, const double* X, doubl
 // ---- allocation-free variant of the damping sensitivity ----
 //
 // Scratch for the reduction of x^T (2 lambda M + C) x: per-block partial sums
-// (re, im) of up to kNoAllocMaxEig eigenpairs, then the denominators.  It
+// (re, im) of up to kNoAllocMaxEig eigenpairs over a fixed grid of
+// kNoAllocBlocks blocks (two per SM of a 152-SM GB300; the reduction is
+// correct for any SM count), then the denominators.  It
 // lives in this file-scope device array, so the call needs no cudaMalloc;
 // every GPU that loads the library keeps these 305 KiB until the process
 // exits.  Every entry the kernels read is written earlier in the same call.

@@ -45,7 +45,6 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr int NT = 128;   // threads of each Ritz CTA
 constexpr int kRitzCTAs = 3;   // cluster: the Ritz CTA, the Z CTA and the off-window T CTA
 constexpr int kMaxRot = 48;    // rotations per batch (2 x 2 deflations between sweeps)
-constexpr uint32_t kQueueWaitLimit = 1u << 22;   // polls of a batch barrier before giving up
 
 struct RitzArgs {
   const double* H;   // (m+1) x m, column-major, ld = m+1
@@ -55,6 +54,7 @@ struct RitzArgs {
   RitzOut* out;
   int m, neig, kwant, final_pass, lock;   // final_pass: 0 restart, 1 finish, 2 finish if converged
   double sigma, tol;
+  uint32_t wait_limit;   // polls of a batch barrier before giving up
 };
 
 struct Smem {
@@ -150,6 +150,7 @@ struct Queue {
   size_t bbytes;
   uint64_t* bars;    // [0..1] full, [2..3] empty, [4] done (same offsets in every CTA)
   int* err;          // shared flag: a bounded wait ran out
+  uint32_t limit;    // polls of a barrier before a wait gives up
   int bq;            // batch being filled
   int nrot;          // its rotations so far
   bool open;         // its buffer has been released by the helpers
@@ -163,7 +164,7 @@ struct Queue {
 __device__ void q_acquire(Queue& Q, int lane) {
   if (Q.open) return;
   if (Q.bq >= 2 && lane == 0 &&
-      !mbar_wait_cluster(&Q.bars[2 + (Q.bq & 1)], (uint32_t)(((Q.bq >> 1) - 1) & 1), kQueueWaitLimit))
+      !mbar_wait_cluster(&Q.bars[2 + (Q.bq & 1)], (uint32_t)(((Q.bq >> 1) - 1) & 1), Q.limit))
     *Q.err = 1;
   __syncthreads();
   Q.open = true;
@@ -756,7 +757,7 @@ __device__ int francis(Smem& S, int m, int lane, int& sweeps, int lock, Queue& Q
   // have applied everything and written Z back
   q_acquire(Q, lane);
   q_publish(Q, lane, 0, 0, 0, 0, 0, 1);
-  if (lane == 0 && !mbar_wait_cluster(&Q.bars[4], 0, kQueueWaitLimit)) *Q.err = 1;
+  if (lane == 0 && !mbar_wait_cluster(&Q.bars[4], 0, Q.limit)) *Q.err = 1;
   __syncthreads();
   if (*Q.err) status = 2;
   sweeps = total;
@@ -847,7 +848,7 @@ __device__ void ritz_helper(const RitzArgs& R, unsigned rank, Smem& S, Queue& Q)
   int err = 0;
   for (int b = 0;; ++b) {
     if (lane == 0)
-      *Q.err = mbar_wait_cluster(&Q.bars[b & 1], (uint32_t)((b >> 1) & 1), kQueueWaitLimit) ? 0 : 1;
+      *Q.err = mbar_wait_cluster(&Q.bars[b & 1], (uint32_t)((b >> 1) & 1), Q.limit) ? 0 : 1;
     __syncthreads();
     if (*Q.err) { err = 1; break; }
     fence_acq_rel_cluster();
@@ -1371,7 +1372,7 @@ __global__ void __launch_bounds__(NT) k_ritz(RitzArgs R) {
   double* wbuf;
   int* wlist;
   ritz_layout(sm, R.m, S, wbuf, wlist);
-  Queue Q{S.batch, batch_bytes(R.m), qbar, &qerr, 0, 0, false};
+  Queue Q{S.batch, batch_bytes(R.m), qbar, &qerr, R.wait_limit, 0, 0, false};
   if (rank == 0)
     ritz_main(R, S, Q, wbuf, wlist);
   else
@@ -1388,7 +1389,7 @@ size_t ritz_smem(int m) {
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
                  int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s) {
-  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol};
+  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol, ritz_wait_limit()};
   size_t smem = ritz_smem(m);
   smem_at_least((const void*)k_ritz, smem);
   cudaLaunchConfig_t cfg = {};

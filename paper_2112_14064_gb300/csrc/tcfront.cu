@@ -173,6 +173,21 @@ __device__ __forceinline__ void split2(float x, __nv_bfloat16& hi, __nv_bfloat16
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// 16 bytes of consecutive elements x[t..] as one vector
+__device__ __forceinline__ uint4 pack16(const float* x, int t) {
+  return make_uint4(__float_as_uint(x[t]), __float_as_uint(x[t + 1]), __float_as_uint(x[t + 2]),
+                    __float_as_uint(x[t + 3]));
+}
+__device__ __forceinline__ uint32_t bf16_bits(__nv_bfloat16 h) {
+  return (uint32_t)__bfloat16_as_ushort(h);
+}
+__device__ __forceinline__ uint4 pack16(const __nv_bfloat16* x, int t) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) w[q] = bf16_bits(x[t + 2 * q]) | (bf16_bits(x[t + 2 * q + 1]) << 16);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // --- kernels -----------------------------------------------------------------
 
 // Per-front power of two for the BF16 operands: 2^-e with e the exponent of
@@ -272,6 +287,7 @@ __device__ __forceinline__ void tc_fail(DevStatus* st) { atomicCAS(&st->timeout,
 //   mode 3: Z = scale acc, L21 = Z D^{-1}: both staged as operands of (4), (5)
 //   mode 4: U[i + u j] -= scale acc            (tiles on or below the diagonal)
 //   mode 5: W[i, j] = acc into the panel       (rows k.., column-major)
+// (MODE 45: modes 4 and 5 in one launch, the mode of each tile in its item.)
 // Every wait is bounded; on a timeout the CTA records it in the status word,
 // waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
 // returns without writing.
@@ -294,13 +310,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   const int4 it = tiles[tile_begin + blockIdx.x];
   const int s = it.x, I0 = it.y, J0 = it.z;
+  // mode 45: products (4) and (5) of a level in one launch, the tile's mode in it.w
+  const int mode = MODE == 45 ? it.w : MODE;
   const TcFront f = A.fr[s];
   const int u = f.u, k = f.k, kb = f.kb;
   // operands of this mode: A rows nA from offA, B rows nB from offB
   int nA, nB, offA, offB;
-  if (MODE == 0) { nA = u; nB = f.nB0; offA = f.offA3; offB = f.offB3; }
-  else if (MODE == 3) { nA = u; nB = k; offA = f.offA3; offB = f.offB3; }
-  else if (MODE == 4) { nA = u; nB = u; offA = f.offA4; offB = f.offB4; }
+  if (mode == 0) { nA = u; nB = f.nB0; offA = f.offA3; offB = f.offB3; }
+  else if (mode == 3) { nA = u; nB = k; offA = f.offA3; offB = f.offB3; }
+  else if (mode == 4) { nA = u; nB = u; offA = f.offA4; offB = f.offB4; }
   else { nA = u; nB = k; offA = f.offA4; offB = f.offB5; }
 
   if (tid == 0) {
@@ -394,54 +412,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int i = I0 + tid;                        // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     float sc = 1.f;
-    if ((MODE == 3 || MODE == 4) && A.scale) sc = 1.f / A.scale[s];
+    if ((mode == 3 || mode == 4) && A.scale) sc = 1.f / A.scale[s];
     E* hi = (E*)A.hi;
     E* lo = (E*)A.lo;
 #pragma unroll 1
     for (int c0 = 0; c0 < N; c0 += 32) {
       const int j0 = J0 + c0;
-      if (MODE == 3 || MODE == 5 || MODE == 0) {
-        if (j0 >= (MODE == 0 ? nB : ((k + RW - 1) / RW) * RW)) break;
+      if (mode == 3 || mode == 5 || mode == 0) {
+        if (j0 >= (mode == 0 ? nB : ((k + RW - 1) / RW) * RW)) break;
       } else if (j0 >= u) {
         break;
       }
       float v[32];
       tc_ld32(lane_base + (uint32_t)c0, v);
-      if (MODE == 0) {
+      if (mode == 0) {
         if (i < u)
           for (int t = 0; t < 32; ++t)
             if (j0 + t < nB) A.C[(int64_t)i * A.ldc + j0 + t] = v[t];
-      } else if (MODE == 3) {
+      } else if (mode == 3) {
         if (i < u) {
-          // this chunk is RW-block b = j0 / RW, elements (j0 % RW)..+31
+          // this chunk is RW-block b = j0 / RW, elements (j0 % RW)..+31; the
+          // pivot reciprocals are loaded before any store so that the loads
+          // overlap (the stores could alias them as far as the compiler knows)
           const int b = j0 / RW, e0 = j0 % RW;
+          float dv[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) dv[t] = j0 + t < k ? __ldg(A.Dinv + f.a + j0 + t) : 0.f;
+          const float zs = A.scale ? A.scale[s] : 1.f;
+          E lh[32], ll[32], zh[32], zl[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            const float z = j0 + t < k ? v[t] * sc : 0.f;   // unscaled Z (zero past k)
+            split2(z * dv[t], lh[t], ll[t]);                // L21 = Z D^{-1}
+            split2(z * zs, zh[t], zl[t]);                   // Z staged with the front's scale
+          }
           const int64_t ra = ((int64_t)f.offA4 + (int64_t)b * u + i) * RW + e0;
           const int64_t rz = ((int64_t)f.offB4 + (int64_t)b * u + i) * RW + e0;
-          for (int t = 0; t < 32; ++t) {
-            const int j = j0 + t;
-            float z = 0.f, l = 0.f;
-            if (j < k) {
-              z = v[t] * sc;                      // unscaled Z
-              l = z * A.Dinv[f.a + j];            // L21
-            }
-            E h, q;
-            split2(l, h, q);
-            hi[ra + t] = h;
-            lo[ra + t] = q;
-            split2(A.scale ? z * A.scale[s] : z, h, q);   // Z staged with the front's scale
-            hi[rz + t] = h;
-            lo[rz + t] = q;
+          // 32 elements per plane and operand, in 16-byte stores
+          constexpr int PER = 16 / sizeof(E);
+#pragma unroll
+          for (int t = 0; t < 32; t += PER) {
+            *reinterpret_cast<uint4*>(hi + ra + t) = pack16(lh, t);
+            *reinterpret_cast<uint4*>(lo + ra + t) = pack16(ll, t);
+            *reinterpret_cast<uint4*>(hi + rz + t) = pack16(zh, t);
+            *reinterpret_cast<uint4*>(lo + rz + t) = pack16(zl, t);
           }
         }
-      } else if (MODE == 4) {
+      } else if (mode == 4) {
         if (i < u) {
+          // all 32 entries are loaded before the first store (see above)
           float* U = A.Uval + f.uoff;
-          for (int t = 0; t < 32; ++t) {
-            const int j = j0 + t;
-            if (j < u) U[i + (int64_t)u * j] -= v[t] * sc;
-          }
+          float old[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) old[t] = j0 + t < u ? U[i + (int64_t)u * (j0 + t)] : 0.f;
+#pragma unroll
+          for (int t = 0; t < 32; ++t)
+            if (j0 + t < u) U[i + (int64_t)u * (j0 + t)] = old[t] - v[t] * sc;
         }
-      } else {   // MODE 5
+      } else {   // mode 5
         if (i < u) {
           float* P = A.Lval + f.loff;
           const int64_t F = k + u;
@@ -521,11 +549,10 @@ void tc_plan(Problem& P, bool bf16) {
   Plan& L = P.plan;
   if (P.tc.ready && P.tc.bf16 == bf16) return;
   std::vector<TcFront> fr(L.nsuper);
-  std::vector<int32_t> stage, t3, t4, t5;
+  std::vector<int32_t> stage, t3, t45;
   P.tc.stage_lvl.assign(L.nlevels + 1, 0);
   P.tc.t3_lvl.assign(L.nlevels + 1, 0);
-  P.tc.t4_lvl.assign(L.nlevels + 1, 0);
-  P.tc.t5_lvl.assign(L.nlevels + 1, 0);
+  P.tc.t45_lvl.assign(L.nlevels + 1, 0);
   P.tc.n35.assign(L.nlevels, 64);
   P.tc.kbmax.assign(L.nlevels, 1);
   int64_t rows_max = 0;
@@ -559,11 +586,9 @@ void tc_plan(Problem& P, bool bf16) {
           for (int r = 0; r < k; r += 32) stage.insert(stage.end(), {s, 2, b, r});
         }
         for (int I = 0; I < u; I += 128) {
-          for (int J = 0; J < k; J += n35) {
-            t3.insert(t3.end(), {s, I, J, 0});
-            t5.insert(t5.end(), {s, I, J, 0});
-          }
-          for (int J = 0; J <= I; J += 128) t4.insert(t4.end(), {s, I, J, 0});
+          for (int J = 0; J < k; J += n35) t3.insert(t3.end(), {s, I, J, 0});
+          for (int J = 0; J <= I; J += 128) t45.insert(t45.end(), {s, I, J, 4});
+          for (int J = 0; J < k; J += 128) t45.insert(t45.end(), {s, I, J, 5});
         }
       }
       fr[s] = f;
@@ -572,16 +597,14 @@ void tc_plan(Problem& P, bool bf16) {
     rows_max = std::max(rows_max, row);
     P.tc.stage_lvl[l + 1] = (int32_t)(stage.size() / 4);
     P.tc.t3_lvl[l + 1] = (int32_t)(t3.size() / 4);
-    P.tc.t4_lvl[l + 1] = (int32_t)(t4.size() / 4);
-    P.tc.t5_lvl[l + 1] = (int32_t)(t5.size() / 4);
+    P.tc.t45_lvl[l + 1] = (int32_t)(t45.size() / 4);
   }
   cudaStream_t s = P.stream;
   P.tc.fr.alloc(fr.size());
   RQ_CUDA(cudaMemcpyAsync(P.tc.fr.p, fr.data(), fr.size() * sizeof(TcFront), cudaMemcpyHostToDevice, s));
   P.tc.stage.upload(stage, s);
   P.tc.t3.upload(t3, s);
-  P.tc.t4.upload(t4, s);
-  P.tc.t5.upload(t5, s);
+  P.tc.t45.upload(t45, s);
   const uint64_t rows = (uint64_t)std::max<int64_t>(rows_max, 128);
   P.tc.hi.alloc(rows * 128);
   P.tc.lo.alloc(rows * 128);
@@ -621,23 +644,18 @@ void launch_tc_level(Problem& P, int l) {
   ++P.launches;
   const int kbm = P.tc.kbmax[l];
   const int b3 = P.tc.t3_lvl[l], c3 = P.tc.t3_lvl[l + 1] - b3;
-  const int b4 = P.tc.t4_lvl[l], c4 = P.tc.t4_lvl[l + 1] - b4;
-  const int b5 = P.tc.t5_lvl[l], c5 = P.tc.t5_lvl[l + 1] - b5;
+  const int b45 = P.tc.t45_lvl[l], c45 = P.tc.t45_lvl[l + 1] - b45;
   const CUtensorMap* mp = P.tc.maps;
   if (bf16) {
     if (P.tc.n35[l] == 64) launch_gemm<__nv_bfloat16, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
     else launch_gemm<__nv_bfloat16, 128, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    launch_gemm<__nv_bfloat16, 128, 4>(A, mp, P.tc.t4.p, b4, c4, kbm, s);
-    if (P.tc.n35[l] == 64) launch_gemm<__nv_bfloat16, 64, 5>(A, mp, P.tc.t5.p, b5, c5, kbm, s);
-    else launch_gemm<__nv_bfloat16, 128, 5>(A, mp, P.tc.t5.p, b5, c5, kbm, s);
+    launch_gemm<__nv_bfloat16, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
   } else {
     if (P.tc.n35[l] == 64) launch_gemm<float, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
     else launch_gemm<float, 128, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    launch_gemm<float, 128, 4>(A, mp, P.tc.t4.p, b4, c4, kbm, s);
-    if (P.tc.n35[l] == 64) launch_gemm<float, 64, 5>(A, mp, P.tc.t5.p, b5, c5, kbm, s);
-    else launch_gemm<float, 128, 5>(A, mp, P.tc.t5.p, b5, c5, kbm, s);
+    launch_gemm<float, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
   }
-  P.launches += 3;
+  P.launches += 2;
 }
 
 // Plain product C = A B^T (A m x K, B n x K, C m x n, all row-major FP32 on

@@ -25,7 +25,7 @@ EXPORTS = [
     "rigaqep_grad_damping", "rigaqep_grad_damping_noalloc", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
-    "rigaqep_front_gemm",
+    "rigaqep_front_gemm", "rigaqep_set_wait_limit",
 ]
 
 
@@ -116,6 +116,8 @@ def load():
     lib.rigaqep_symbolic_destroy.restype = None
     lib.rigaqep_destroy.argtypes = [P]
     lib.rigaqep_destroy.restype = None
+    lib.rigaqep_set_wait_limit.argtypes = [ctypes.c_uint32]
+    lib.rigaqep_set_wait_limit.restype = None
     lib.rigaqep_last_error.argtypes = []
     lib.rigaqep_last_error.restype = ctypes.c_char_p
     _lib = lib

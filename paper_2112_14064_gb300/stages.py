@@ -30,6 +30,7 @@ from . import rigaqep, workloads
 EIGS_OPTS = {
     "p3_256_b16": dict(m=96, shift=0.0, ncand=56),
     "p3_64_b16": dict(m=96, shift=0.0, ncand=80),
+    "p3_256_iga": dict(m=96, shift=0.0, ncand=56),
 }
 
 
@@ -40,6 +41,8 @@ def main(argv=None):
                     choices=["assemble", "analyze", "factor", "solve", "eigs"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--factor-shift", type=float, default=0.0)
+    ap.add_argument("--precision", default="FP64", choices=["FP64", "TF32_IR", "FP32_IR", "BF16_IR"],
+                    help="front precision of the factor, solve and eigs stages")
     a = ap.parse_args(argv)
     if a.reps < 1:
         ap.error("--reps must be >= 1")
@@ -51,6 +54,7 @@ def main(argv=None):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.reps)]
     make = lambda: rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig)  # noqa: E731
+    prec = getattr(rigaqep, a.precision)
     opts = EIGS_OPTS.get(a.workload, {})
     extra = {}
     pr = None
@@ -71,10 +75,10 @@ def main(argv=None):
         if a.stage == "factor":
             for r in range(a.reps):
                 ev[r][0].record(stream)
-                pr.factor(a.factor_shift)
+                pr.factor(a.factor_shift, prec)
                 ev[r][1].record(stream)
         elif a.stage == "solve":
-            pr.factor(a.factor_shift)
+            pr.factor(a.factor_shift, prec)
             g = torch.Generator(device="cpu").manual_seed(1)
             b = torch.rand(pr.N, dtype=torch.float64, generator=g).to(dev) - 0.5
             x = torch.empty_like(b)
@@ -85,14 +89,16 @@ def main(argv=None):
         else:
             for r in range(a.reps):
                 ev[r][0].record(stream)
-                pr.eigs(cfg["neig"], cfg["shift"], raise_on_noconv=False, **opts)
+                pr.eigs(cfg["neig"], cfg["shift"], raise_on_noconv=False, precision=prec, **opts)
                 ev[r][1].record(stream)
             inf = pr.info()
             extra = {k: inf[k] for k in ("n_apply", "n_restarts", "certified", "fb_ms",
                                          "ritz_ms", "eigs_ms", "factor_ms")}
         torch.cuda.synchronize()
         inf = pr.info()
-        extra.update(nnz_L=inf["nnz_L"], nlevels=inf["nlevels"], factor_flops=inf["factor_flops"])
+        extra.update(nnz_L=inf["nnz_L"], nlevels=inf["nlevels"], factor_flops=inf["factor_flops"],
+                     precision=a.precision, n_ir=inf["n_ir"], ir_residual=inf["ir_residual"],
+                     last_factor_ms=inf["factor_ms"])
         pr.close()
     torch.cuda.synchronize()
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]

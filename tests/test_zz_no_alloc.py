@@ -54,8 +54,11 @@ def test_noalloc_gradient_rejects_too_many_pairs(rq):
     c = dict(workloads.CONFIGS["tiny"])
     pr = rq.Problem(c["ne"], c["p"], c["block"], workloads.sigma_e(c)).analyze()
     lib = rq.load()
-    dummy = ctypes.c_void_p(1)   # never dereferenced: the size check comes first
-    code = lib.rigaqep_grad_damping_noalloc(pr._h, 65, dummy, dummy, dummy)
+    # real (small) device buffers: the size check comes first, but a wrong
+    # order would then give a wrong status, never a stray device address
+    buf = torch.zeros(64, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    code = lib.rigaqep_grad_damping_noalloc(pr._h, 65, p, p, p)
     assert code == 1
     assert b"64" in lib.rigaqep_last_error()
     pr.close()
