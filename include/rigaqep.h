@@ -131,8 +131,9 @@ typedef struct {
   int64_t nnz;           /* entries of the shared K/M/C pattern */
   int64_t nsuper;        /* supernodes (= fronts) */
   int64_t nlevels;       /* assembly-tree levels */
-  int64_t nnz_L;         /* supernodal factor entries, dense pivot blocks */
-  int64_t factor_flops;  /* sum_j (c_j^2 + 2 c_j), c_j = off-diagonals of column j */
+  int64_t nnz_L;         /* supernodal factor entries, dense pivot blocks (stored and read) */
+  int64_t factor_flops;  /* sum_j (c_j^2 + 2 c_j), c_j = off-diagonals of column j in the
+                            supernodal structure (the arithmetic the fronts execute) */
   int64_t max_front;     /* largest front order k+u */
   int64_t n_apply;       /* operator applications (FB solves) of the last eigs */
   int64_t n_restarts;    /* Krylov-Schur restarts of the last eigs */
@@ -161,6 +162,11 @@ typedef struct {
                                  previous in-region call (same factor, shift, ncand,
                                  krylov_dim, tol, max_restarts, seed; seeded start) and
                                  only selected and extracted for its target */
+  int64_t nnz_L_exact;        /* structurally non-zero entries of L (diagonal included)
+                                 with the exact column counts: the algorithmic factor
+                                 size (-1 before rigaqep_analyze) */
+  int64_t factor_flops_exact; /* sum_j (c_j^2 + 2 c_j) with the exact column counts: the
+                                 algorithmic factorisation flops (-1 before analyze) */
 } rigaqep_info;
 
 /* Create a handle and assemble K, M, C (original DOF order, one CSR
@@ -326,6 +332,9 @@ rigaqep_status rigaqep_symbolic_sizes(const rigaqep_symbolic* sym, int64_t* size
 rigaqep_status rigaqep_symbolic_export(const rigaqep_symbolic* sym, int32_t* perm, int32_t* sptr,
                                        int32_t* parent, int32_t* upd_ptr, int32_t* upd_idx,
                                        int32_t* level, int32_t* rowptr, int32_t* col);
+/* counts[0..3] = {nnz_L, factor_flops, nnz_L_exact, factor_flops_exact} of the
+ * plan, with the meaning of the rigaqep_info fields of those names; host only. */
+rigaqep_status rigaqep_symbolic_counts(const rigaqep_symbolic* sym, int64_t* counts);
 void rigaqep_symbolic_destroy(rigaqep_symbolic* sym);
 
 /* Number of polls after which a wait between the cooperating CTAs of the

@@ -419,7 +419,11 @@ rigaqep_status rigaqep_export_symbolic(const rigaqep_problem* prob, int32_t* per
 rigaqep_status rigaqep_get_info(const rigaqep_problem* prob, rigaqep_info* info) {
   return guard([&] {
     need(prob != nullptr && info != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
-    *info = prob->impl.info;
+    rq::Problem& P = const_cast<rigaqep_problem*>(prob)->impl;
+    if (P.analyzed) P.plan.exact_counts();   // once per handle, on the host
+    *info = P.info;
+    info->nnz_L_exact = P.analyzed ? P.plan.nnz_L_exact : -1;
+    info->factor_flops_exact = P.analyzed ? P.plan.flops_exact : -1;
   });
 }
 
@@ -505,6 +509,18 @@ rigaqep_status rigaqep_symbolic_create(const rigaqep_mesh_desc* mesh, rigaqep_sy
       throw;
     }
     *out = h;
+  });
+}
+
+rigaqep_status rigaqep_symbolic_counts(const rigaqep_symbolic* sym, int64_t* counts) {
+  return guard([&] {
+    need(sym != nullptr && counts != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    rq::Plan& L = const_cast<rigaqep_symbolic*>(sym)->plan;
+    L.exact_counts();
+    counts[0] = L.nnz_L;
+    counts[1] = L.flops;
+    counts[2] = L.nnz_L_exact;
+    counts[3] = L.flops_exact;
   });
 }
 

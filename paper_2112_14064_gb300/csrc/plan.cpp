@@ -295,4 +295,44 @@ void Plan::build_symbolic() {
   for (int s = 0; s < nsuper; ++s) lvl_nodes[fill[level[s]]++] = s;
 }
 
+// Exact column structures of L in the ND order (no supernodal amalgamation):
+// struct(j) = {i > j : Q_ij != 0} united with the structures of j's
+// elimination-tree children, less j; the parent of j is the first entry of
+// struct(j).  Each structure is merged once into its parent and released.
+void Plan::exact_counts() {
+  if (nnz_L_exact >= 0) return;
+  std::vector<std::vector<int32_t>> st(N);
+  std::vector<int32_t> head(N, -1), next(N, -1);
+  std::vector<int32_t> buf, tmp;
+  int64_t nnz = 0, fl = 0;
+  for (int64_t j = 0; j < N; ++j) {
+    const int32_t o = perm[j];
+    buf.clear();
+    for (int32_t q = rowptr[o]; q < rowptr[o + 1]; ++q) {
+      const int32_t i = iperm[col[q]];
+      if (i > j) buf.push_back(i);
+    }
+    std::sort(buf.begin(), buf.end());
+    for (int32_t c = head[j]; c >= 0; c = next[c]) {
+      tmp.clear();
+      std::set_union(buf.begin(), buf.end(), st[c].begin(), st[c].end(), std::back_inserter(tmp));
+      buf.swap(tmp);
+      std::vector<int32_t>().swap(st[c]);
+    }
+    auto it = std::lower_bound(buf.begin(), buf.end(), (int32_t)j);
+    if (it != buf.end() && *it == (int32_t)j) buf.erase(it);
+    const int64_t c = (int64_t)buf.size();
+    nnz += 1 + c;
+    fl += c * c + 2 * c;
+    if (!buf.empty()) {
+      const int32_t p = buf[0];
+      next[j] = head[p];
+      head[p] = (int32_t)j;
+      st[j] = buf;
+    }
+  }
+  nnz_L_exact = nnz;
+  flops_exact = fl;
+}
+
 }  // namespace rq

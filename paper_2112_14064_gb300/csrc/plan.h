@@ -64,10 +64,15 @@ struct Plan {
   int64_t l_total = 0, u_total = 0;
   std::vector<int32_t> lvl_ptr, lvl_nodes;  // supernodes of each level, ascending
   int64_t nnz_L = 0, flops = 0, max_front = 0;
+  // exact (scalar) counts: structurally non-zero entries of L and
+  // sum_j (c_j^2 + 2 c_j) with the exact column counts c_j (exact_counts())
+  int64_t nnz_L_exact = -1, flops_exact = -1;
 
   // build the pattern only (assemble) and the symbolic phase (analyze)
   void build_pattern(int ne_, int p_, int block_, int nq_, int leaf_min_);
   void build_symbolic();
+  // exact column counts of L by the elimination tree (after build_symbolic)
+  void exact_counts();
 };
 
 }  // namespace rq

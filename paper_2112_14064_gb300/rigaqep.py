@@ -24,6 +24,7 @@ EXPORTS = [
     "rigaqep_assemble", "rigaqep_analyze", "rigaqep_factor", "rigaqep_solve", "rigaqep_eigs",
     "rigaqep_grad_damping", "rigaqep_grad_damping_noalloc", "rigaqep_export_csr", "rigaqep_export_symbolic", "rigaqep_get_info",
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
+    "rigaqep_symbolic_counts",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
     "rigaqep_front_gemm", "rigaqep_set_wait_limit",
 ]
@@ -68,7 +69,8 @@ class Info(ctypes.Structure):
                    ("n_launches", ctypes.c_int64), ("ritz_ms", ctypes.c_double),
                    ("ritz_phase_cycles", ctypes.c_double * 6),
                    ("n_ir", ctypes.c_int64), ("ir_residual", ctypes.c_double),
-                   ("reused_candidates", ctypes.c_int64)])
+                   ("reused_candidates", ctypes.c_int64), ("nnz_L_exact", ctypes.c_int64),
+                   ("factor_flops_exact", ctypes.c_int64)])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}
@@ -104,6 +106,7 @@ def load():
         "rigaqep_get_info": [P, ctypes.POINTER(Info)],
         "rigaqep_symbolic_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(P)],
         "rigaqep_symbolic_sizes": [P, ctypes.POINTER(I64)],
+        "rigaqep_symbolic_counts": [P, ctypes.POINTER(I64)],
         "rigaqep_symbolic_export": [P, P, P, P, P, P, P, P, P],
         "rigaqep_batch_eigs": [ctypes.POINTER(P), I32, ctypes.POINTER(BatchJob), I32, I32],
         "rigaqep_front_gemm": [I32, I32, I32, I32, P, P, P, V],
@@ -160,6 +163,9 @@ def symbolic_host(ne, p, block, n_quad=0, leaf_min=0):
                                                  "level", "rowptr", "col")]))
         out["nlevels"] = nl
         out["n1"] = n1
+        cnt = (ctypes.c_int64 * 4)()
+        _check(lib.rigaqep_symbolic_counts(h, cnt))
+        out["nnz_L"], out["factor_flops"], out["nnz_L_exact"], out["factor_flops_exact"] = list(cnt)
         return out
     finally:
         lib.rigaqep_symbolic_destroy(h)

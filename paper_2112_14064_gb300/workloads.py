@@ -36,6 +36,9 @@ CONFIGS = {
     # 64 x 64 version of the sensitivity workload (checker-sized)
     "p3_64_b16": dict(ne=64, p=3, block=16, shift=800.0, neig=20, m=60,
                       sigma_law="uniform", lo=0.1, hi=1.0, seed=20211232),
+    # 64 x 64 version of the mixed-precision workload (checker-sized)
+    "p4_64_b32": dict(ne=64, p=4, block=32, shift=2000.0, neig=20, m=60,
+                      sigma_law="lognormal", median=0.5, logstd=1.0, seed=20211230),
 }
 
 

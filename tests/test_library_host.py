@@ -71,3 +71,26 @@ def test_host_symbolic_bit_exact_full_size(lib, ne, p, b):
     s = _oracle_sym(ne, p, b, g["rowptr"].astype(np.int64), g["col"].astype(np.int64))
     for k in ("perm", "sptr", "parent", "upd_ptr", "upd_idx", "level"):
         assert np.array_equal(getattr(s, k), g[k]), k
+
+
+@pytest.mark.parametrize("ne,p,b", [(16, 2, 4), (64, 3, 16), (10, 2, 0), (32, 5, 8), (24, 4, 0)])
+def test_host_factor_counts_match_oracle(lib, ne, p, b):
+    """Supernodal and exact nnz(L) / flop counts of the library's plan equal
+    the oracle's (which tests/test_oracle_pins.py pins to brute-force
+    elimination)."""
+    g = rigaqep.symbolic_host(ne, p, b)
+    A = assemble(ne, p, b, np.ones(ne * ne))
+    s = _oracle_sym(ne, p, b, A.indptr, A.indices)
+    assert g["nnz_L"] == s.nnz_L()
+    assert g["factor_flops"] == s.factor_flops()
+    assert g["nnz_L_exact"] == s.nnz_L_scalar(A.indptr, A.indices)
+    assert g["factor_flops_exact"] == s.factor_flops_scalar(A.indptr, A.indices)
+
+
+def test_host_exact_counts_full_size(lib):
+    """256 x 256, p = 3, blocks of 16: the exact counts (7,291,970 entries,
+    841,058,277 flops) are those of the oracle's elimination-tree count on the
+    same plan; the supernodal ones are 8,669,570 and 1,067,962,341."""
+    g = rigaqep.symbolic_host(256, 3, 16)
+    assert (g["nnz_L_exact"], g["factor_flops_exact"]) == (7291970, 841058277)
+    assert (g["nnz_L"], g["factor_flops"]) == (8669570, 1067962341)
