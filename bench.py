@@ -9,6 +9,14 @@ Krylov-Schur eigensolve of the 20 eigenpairs nearest the target 500
 certified; a pair counts only when its backward error is <= 1e-10 and the
 selection is certified.
 
+Further legs of the same JSON line (each its own workload, timed the same
+way): the same step with FP32, split-TF32 and split-BF16 fronts and FP64
+refinement (`mixed`); the p = 4, 512 x 512 lognormal-damping workload in
+FP64 and with tensor-core fronts (`workload_mixed`); the p = 3, 512 x 512
+differentiation workload with all 262,144 damping gradients (`workload_grad`);
+the same 256 x 256 mesh with maximum-continuity IGA against rIGA (`iga`);
+and the 64-problem batch (`batch`).
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy
@@ -39,7 +47,7 @@ ETA_MAX = 1e-10
 METRIC = "eigenpairs/s at rel. residual <= 1e-10 (FP64)"
 UNIT = "eigenpairs/s"
 BATCH_KW = dict(shift=0.0, ncand=24, m=48, seed=1)   # in-region solve shared by a problem's 4 targets
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
 def parse():
@@ -51,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 512^2 workload legs and the IGA comparison")
     return ap.parse_args()
 
 
@@ -124,11 +134,12 @@ def fb_traffic(nnz_L):
         return None
 
 
-def oracle_sample(cfg, sig, v1, n_apply_full):
-    """Time the FP64 CPU oracle on a bounded sample of the workload: its own
-    assembly, symbolic phase, factorisation at the shift and one Krylov-Schur
-    cycle (m operator applications with CGS2); extrapolate one full solve as
-    setup + n_apply_full / m cycles.  Returns (pairs/s, seconds, description)."""
+def oracle_sample(cfg, sig, v1):
+    """Time the FP64 CPU oracle as it stands on one full solve of the
+    workload: its own assembly, symbolic phase, factorisation at the shift
+    and the whole Krylov-Schur eigensolve (same target, shift, candidates and
+    Krylov dimension as the GPU step).  Returns (pairs/s, seconds,
+    description)."""
     from oracle.assemble import assemble
     from oracle.nd import symbolic
     from oracle.multifrontal import factorize
@@ -138,15 +149,14 @@ def oracle_sample(cfg, sig, v1, n_apply_full):
     sym = symbolic(A.n1, A.space.c0_dofs, cfg["p"], A.indptr, A.indices)
     F = factorize(sym, A.Q(TARGET_KW["shift"]))
     t1 = time.perf_counter()
-    qep.eigs(A.K, A.C, A.M, TARGET_KW["shift"], cfg["neig"], TARGET_KW["m"], F.solve, v1,
-             max_restarts=0, target=cfg["shift"], ncand=TARGET_KW["ncand"], sigma_min=sig.min())
+    r = qep.eigs(A.K, A.C, A.M, TARGET_KW["shift"], cfg["neig"], TARGET_KW["m"], F.solve, v1,
+                 target=cfg["shift"], ncand=TARGET_KW["ncand"], sigma_min=sig.min())
     t2 = time.perf_counter()
-    cycle = (t2 - t1) / TARGET_KW["m"]
-    full = (t1 - t0) + n_apply_full * cycle
-    desc = (f"oracle assemble+symbolic+factor ({t1 - t0:.1f} s) and one Krylov-Schur cycle of "
-            f"{TARGET_KW['m']} applies ({t2 - t1:.1f} s) on the full workload; one solve "
-            f"extrapolated to the GPU's {n_apply_full} applies = {full:.1f} s")
-    return cfg["neig"] / full, t2 - t0, desc
+    pairs = int((r.eta <= ETA_MAX).sum()) if r.certified else 0
+    desc = (f"one full oracle solve of the workload: assemble+symbolic+factor {t1 - t0:.1f} s, "
+            f"Krylov-Schur {t2 - t1:.1f} s ({r.n_apply} applies, {r.n_restarts} restarts), "
+            f"{pairs} certified pairs; single thread (host has {os.cpu_count()} cores)")
+    return pairs / (t2 - t0), t2 - t0, desc
 
 
 def run_reference(args):
@@ -164,10 +174,9 @@ def run_reference(args):
     from oracle.assemble import assemble
     for _ in range(args.warmup):
         assemble(tiny["ne"], tiny["p"], tiny["block"], workloads.sigma_e(tiny))
-    n_apply_full = int(os.environ.get("RIGAQEP_REF_APPLIES", "167"))   # the GPU arm's applies
     vals, secs, desc = [], [], ""
     for _ in range(args.steps):
-        v, t, desc = oracle_sample(cfg, sig, v1, n_apply_full)
+        v, t, desc = oracle_sample(cfg, sig, v1)
         vals.append(v)
         secs.append(t)
     value = float(np.mean(vals))
@@ -179,7 +188,7 @@ def run_reference(args):
                        "block": cfg["block"], "target": cfg["shift"], "neig": cfg["neig"],
                        **TARGET_KW},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -223,6 +232,204 @@ def batch_leg(rank, world, barrier):
     secs = time.perf_counter() - t0
     return dict(problems=len(mine), jobs=njobs, pairs_converged=conv, pairs_certified=cert,
                 seconds=secs)
+
+
+def measured_fp64_peak(dev, n=4096, reps=3):
+    """FP64 dense-product rate of this GPU (TFLOP/s): best of `reps`
+    torch.matmul (cuBLAS DGEMM) of n x n matrices, CUDA events."""
+    import torch
+    a = torch.rand((n, n), dtype=torch.float64, device=dev)
+    b = torch.rand((n, n), dtype=torch.float64, device=dev)
+    c = a @ b
+    torch.cuda.synchronize()
+    best = float("inf")
+    st = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        c = a @ b
+        e1.record(st)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del a, b, c
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def _timed(step, n, flush, stream):
+    """n steps, each after an L2 flush, CUDA events on the stream around each."""
+    import torch
+    times, outs = [], []
+    for i in range(n):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, outs
+
+
+def _rel_diffs(ref, got):
+    """Per computed eigenvalue: relative distance to the nearest reference value."""
+    return [float(np.min(np.abs(ref - v)) / abs(v)) for v in got]
+
+
+def _solve_step(cfg, sig_d, kw, prec, v1_d=None):
+    """One assemble + analyze + factor + eigs step; returns (lam, eta, info)."""
+    from paper_2112_14064_gb300 import rigaqep
+    pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
+    lam, X, eta, nconv, st = pr.eigs(cfg["neig"], cfg["shift"], v1=v1_d, raise_on_noconv=False,
+                                     precision=getattr(rigaqep, prec), **kw)
+    inf = pr.info()
+    pr.close()
+    return lam, eta, inf
+
+
+def _leg_entry(times, outs, lam64, certified_only=True):
+    lam, eta, inf = outs[-1]
+    good = 0
+    for l_, e_, i_ in outs:
+        ok = int((e_ <= ETA_MAX).sum().item())
+        good += ok if (i_["certified"] == 1 or not certified_only) else 0
+    ent = {"value": 1e3 * good / sum(times), "unit": UNIT,
+           "ms_per_step": sum(times) / len(times), "steps": len(times),
+           "certified": int(inf["certified"]), "cert_margin": inf["cert_margin"],
+           "factor_ms": inf["factor_ms"],
+           "factor_tflops": inf["factor_flops_exact"] / (inf["factor_ms"] * 1e-3) / 1e12,
+           "factor_tflops_executed": inf["factor_flops"] / (inf["factor_ms"] * 1e-3) / 1e12,
+           "refinement_steps": inf["n_ir"], "probe_residual": inf["ir_residual"],
+           "n_apply": inf["n_apply"], "fb_ms": inf["fb_ms"], "eigs_ms": inf["eigs_ms"],
+           "max_eta": float(eta.max().item())}
+    if lam64 is not None:
+        d = _rel_diffs(lam64, lam.cpu().numpy())
+        ent["rel_eigenvalue_diff_vs_fp64"] = d
+        ent["max_rel_eigenvalue_diff_vs_fp64"] = max(d)
+    return ent
+
+
+def precision_leg(cfg, kw, sig_d, v1_d, lam64, flush, stream, barrier, steps=2):
+    """The bench step with FP32 (SIMT), split-TF32 and split-BF16 (tcgen05)
+    fronts, every solve refined in FP64; eigenvalues against the FP64 step's
+    result by result."""
+    out = {"workload": WORKLOAD, "note": "same step as the headline with low-precision fronts "
+           "and FP64-refined solves; value counts certified pairs with eta <= 1e-10"}
+    for prec in ("FP32_IR", "TF32_IR", "BF16_IR"):
+        _solve_step(cfg, sig_d, kw, prec, v1_d)
+        barrier()
+        times, outs = _timed(lambda: _solve_step(cfg, sig_d, kw, prec, v1_d), steps, flush, stream)
+        out[prec] = _leg_entry(times, outs, lam64)
+    return out
+
+
+WORKLOAD_MIXED_KW = dict(m=96, shift=0.0, ncand=88, seed=1)
+WORKLOAD_GRAD_KW = dict(m=96, shift=0.0, ncand=80, seed=1)
+
+
+def workload_mixed_leg(flush, stream, barrier):
+    """p = 4, 512 x 512, blocks of 32, lognormal damping (median 0.5,
+    log-std 1), 20 pairs nearest the target 2000: FP64 fronts and split
+    TF32 / BF16 tensor-core fronts with FP64 refinement, eigenvalues against
+    the FP64 result.  With 88 candidates (m = 96) the selection at this
+    target is not certified (the damping spread needs ~400 candidates), so
+    the value counts converged pairs with eta <= 1e-10 and `certified` is
+    reported."""
+    import torch
+    from paper_2112_14064_gb300 import workloads
+    cfg = workloads.CONFIGS["p4_512_b32"]
+    sig_d = torch.from_numpy(workloads.sigma_e(cfg)).cuda()
+    out = {"workload": "p4_512_b32", "N": None, "solve": WORKLOAD_MIXED_KW,
+           "target": cfg["shift"], "neig": cfg["neig"],
+           "value_counts": "converged pairs with eta <= 1e-10 (selection not certified)"}
+    lam64 = None
+    for prec in ("FP64", "TF32_IR", "BF16_IR"):
+        _solve_step(cfg, sig_d, WORKLOAD_MIXED_KW, prec)
+        barrier()
+        times, outs = _timed(lambda: _solve_step(cfg, sig_d, WORKLOAD_MIXED_KW, prec), 1, flush,
+                             stream)
+        out[prec] = _leg_entry(times, outs, lam64, certified_only=False)
+        out["N"] = outs[-1][2]["N"]
+        if prec == "FP64":
+            lam64 = outs[-1][0].cpu().numpy()
+    return out
+
+
+def workload_grad_leg(flush, stream, barrier):
+    """p = 3, 512 x 512, blocks of 16, sigma_e ~ U[0.1, 1], 20 pairs nearest
+    800 (certified): one step = assemble + analyze + factor + eigs + the
+    gradients of the 20 eigenvalues with respect to all 262,144 sigma_e, in
+    FP64 and with the split-TF32 forward pass."""
+    import torch
+    from paper_2112_14064_gb300 import rigaqep, workloads
+    cfg = workloads.CONFIGS["p3_512_b16"]
+    sig_d = torch.from_numpy(workloads.sigma_e(cfg)).cuda()
+    ne2 = cfg["ne"] ** 2
+    out = {"workload": "p3_512_b16", "solve": WORKLOAD_GRAD_KW, "target": cfg["shift"],
+           "neig": cfg["neig"], "gradients_per_step": cfg["neig"] * ne2}
+
+    def step(prec):
+        pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
+        lam, X, eta, nconv, st = pr.eigs(cfg["neig"], cfg["shift"], raise_on_noconv=False,
+                                         precision=getattr(rigaqep, prec), **WORKLOAD_GRAD_KW)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G = pr.grad_damping(lam, X)
+        e1.record(stream)
+        inf = pr.info()
+        pr.close()
+        return lam, eta, inf, (e0, e1), G
+
+    lam64 = None
+    for prec in ("FP64", "TF32_IR"):
+        step(prec)
+        barrier()
+        times, outs = _timed(lambda: step(prec), 2, flush, stream)
+        lam, eta, inf, (e0, e1), G = outs[-1]
+        ent = _leg_entry(times, [(o[0], o[1], o[2]) for o in outs], lam64)
+        ent["adjoint_ms"] = e0.elapsed_time(e1)
+        ent["gradients_per_s"] = 1e3 * cfg["neig"] * ne2 / (sum(times) / len(times))
+        ent["adjoint_gradients_per_s"] = 1e3 * cfg["neig"] * ne2 / ent["adjoint_ms"]
+        ent["adjoint_gb_per_s"] = (16.0 * cfg["neig"] * (outs[-1][2]["N"] + 2 * ne2)
+                                   / (ent["adjoint_ms"] * 1e-3) / 1e9)
+        out[prec] = ent
+        if prec == "FP64":
+            lam64 = lam.cpu().numpy()
+    return out
+
+
+def iga_leg(inf_riga, riga_ms, flush, stream, barrier):
+    """The headline step on the same mesh with maximum-continuity IGA (C^2,
+    no C^0 separators) against rIGA (blocks of 16): factor flops (exact),
+    factor time, factor entries (the FB bytes), eigensolve time and
+    eigenpairs/s; the analogue of the paper's rIGA-vs-IGA comparison
+    (Table 2) for this scalar problem."""
+    import torch
+    from paper_2112_14064_gb300 import workloads
+    cfg = workloads.CONFIGS["p3_256_iga"]
+    sig_d = torch.from_numpy(workloads.sigma_e(cfg)).cuda()
+    _solve_step(cfg, sig_d, TARGET_KW, "FP64")
+    barrier()
+    times, outs = _timed(lambda: _solve_step(cfg, sig_d, TARGET_KW, "FP64"), 2, flush, stream)
+    ent = _leg_entry(times, outs, None)
+    inf = outs[-1][2]
+    ent.update(N=inf["N"], nnz_L_exact=inf["nnz_L_exact"], factor_flops_exact=inf["factor_flops_exact"],
+               fb_ms_per_solve=inf["fb_ms"] / max(1, inf["n_apply"]))
+    r = {"N": inf_riga["N"], "nnz_L_exact": inf_riga["nnz_L_exact"],
+         "factor_flops_exact": inf_riga["factor_flops_exact"], "factor_ms": inf_riga["factor_ms"],
+         "fb_ms_per_solve": inf_riga["fb_ms"] / max(1, inf_riga["n_apply"]),
+         "eigs_ms": inf_riga["eigs_ms"], "ms_per_step": riga_ms}
+    return {"workload": "p3_256_iga (C^2) against p3_256_b16 (rIGA, blocks of 16)",
+            "iga": ent, "riga": r,
+            "improvement_riga_over_iga": {
+                "factor_flops": inf["factor_flops_exact"] / r["factor_flops_exact"],
+                "factor_time": ent["factor_ms"] / r["factor_ms"],
+                "factor_entries": inf["nnz_L_exact"] / r["nnz_L_exact"],
+                "fb_time": ent["fb_ms_per_solve"] / r["fb_ms_per_solve"],
+                "eigs_time": ent["eigs_ms"] / r["eigs_ms"],
+                "step_time": ent["ms_per_step"] / r["ms_per_step"]}}
 
 
 def run_ours(args):
@@ -335,43 +542,15 @@ def run_ours(args):
 
     batch = None if args.no_batch else batch_leg(rank, world, barrier)
 
-    # mixed precision: the same step with FP32 fronts and FP64-refined solves,
-    # its eigenvalues against the FP64 step's
-    mixed = None
+    # precision, workload and discretisation legs (each its own workload)
+    legs = {}
     if not args.no_mixed:
-        lam64 = lam.cpu().numpy()
-
-        def step_mixed():
-            pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
-            lm, Xm, em, nc, st = pr.eigs(neig, target, v1=v1_d, raise_on_noconv=False,
-                                         precision=rigaqep.FP32_IR, **TARGET_KW)
-            im = pr.info()
-            gm = (em <= ETA_MAX).sum() if im["certified"] == 1 else torch.zeros((), device=dev)
-            pr.close()
-            return lm, gm, im
-
-        step_mixed()
-        barrier()
-        mt, mp, minf, lmx = [], 0, None, None
-        for i in range(2):
-            flush.fill_(float(i))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lmx, gm, minf = step_mixed()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            mt.append(e0.elapsed_time(e1))
-            mp += int(gm.item())
-        lm_h = lmx.cpu().numpy()
-        diff = max(float(np.min(np.abs(lam64 - v)) / abs(v)) for v in lm_h)
-        mixed = {"precision": "FP32 fronts and sweeps, FP64-refined solves",
-                 "value": 1e3 * mp / sum(mt), "unit": UNIT, "ms_per_step": sum(mt) / len(mt),
-                 "factor_ms": minf["factor_ms"],
-                 "factor_tflops": minf["factor_flops"] / (minf["factor_ms"] * 1e-3) / 1e12,
-                 "refinement_steps": minf["n_ir"], "probe_residual": minf["ir_residual"],
-                 "fb_ms": minf["fb_ms"], "n_apply": minf["n_apply"],
-                 "max_rel_eigenvalue_diff_vs_fp64": diff, "steps": len(mt)}
+        legs["mixed"] = precision_leg(cfg, TARGET_KW, sig_d, v1_d, lam.cpu().numpy(), flush,
+                                      stream, barrier, steps=2)
+    if not args.no_workloads:
+        legs["workload_mixed"] = workload_mixed_leg(flush, stream, barrier)
+        legs["workload_grad"] = workload_grad_leg(flush, stream, barrier)
+        legs["iga"] = iga_leg(infos[-1], total_ms / args.steps, flush, stream, barrier)
 
     # max over ranks
     t = torch.tensor([total_ms, float(sum(e2e_ms))], dtype=torch.float64, device=dev)
@@ -385,9 +564,14 @@ def run_ours(args):
     inf = infos[-1]
     fb_avg_s = inf["fb_ms"] / max(1, inf["n_apply"]) / 1e3
     nnz_L = inf["nnz_L"]
-    fb_flops = 4.0 * nnz_L                       # every factor entry: one FMA forward, one backward
-    fb_bytes = 16.0 * nnz_L + 32.0 * inf["N"]    # factor read twice + rhs/solution vectors
+    nnz_exact = inf["nnz_L_exact"]
+    # algorithmic work of one solve: every structurally non-zero entry of L
+    # once forward and once backward (one FMA and 8 bytes each), plus the
+    # right-hand side and solution vectors
+    fb_flops = 4.0 * nnz_exact
+    fb_bytes = 16.0 * nnz_exact + 32.0 * inf["N"]
     achieved_tf = fb_flops / fb_avg_s / 1e12
+    fp64_peak = measured_fp64_peak(dev)
     traffic = fb_traffic(nnz_L)
     line = {
         "metric": METRIC, "value": 1e3 * all_pairs / total_ms, "unit": UNIT,
@@ -400,13 +584,20 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}",
                    "l2": "256 MB buffer written between timed steps"},
         "roofline": {"kernel": "FB solve (forward + backward substitution kernels)",
-                     "bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak,
+                     "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
+                     "peak_source": "FP64 DGEMM (torch.matmul, 4096^3) measured in this run",
+                     "peak_nominal": FP64_NOMINAL_TFLOPS,
                      "traffic": traffic, "algorithmic_bytes": fb_bytes,
-                     "avg_launch_us": fb_avg_s * 1e6,
+                     "algorithmic_flops": fb_flops, "nnz_L_exact": nnz_exact,
+                     "nnz_L_stored": nnz_L, "avg_launch_us": fb_avg_s * 1e6,
                      "hbm_frac": fb_bytes / fb_avg_s / 1e9 / _hbm_peak()},
-        "factor": {"tflops": inf["factor_flops"] / (inf["factor_ms"] * 1e-3) / 1e12,
-                   "ms": inf["factor_ms"], "flops": inf["factor_flops"]},
+        "factor": {"tflops": inf["factor_flops_exact"] / (inf["factor_ms"] * 1e-3) / 1e12,
+                   "tflops_executed": inf["factor_flops"] / (inf["factor_ms"] * 1e-3) / 1e12,
+                   "ms": inf["factor_ms"], "flops_exact": inf["factor_flops_exact"],
+                   "flops_executed": inf["factor_flops"],
+                   "frac_of_fp64_peak": inf["factor_flops_exact"] / (inf["factor_ms"] * 1e-3)
+                   / 1e12 / fp64_peak},
         "solve": {"n_apply": inf["n_apply"], "n_restarts": inf["n_restarts"],
                   "certified": inf["certified"], "eigs_ms": inf["eigs_ms"],
                   "fb_ms": inf["fb_ms"], "ritz_ms": inf["ritz_ms"]},
@@ -417,8 +608,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 16 * neig + 16 * N * neig + 8 * neig},
         "gpu_launches": int(sum(i["n_launches"] + 4 for i in infos)),
     }
-    if mixed is not None:
-        line["mixed"] = mixed
+    line.update(legs)
     if batch is not None:
         bt = torch.tensor([batch["seconds"], batch["jobs"], batch["pairs_converged"],
                            batch["pairs_certified"], batch["problems"]], dtype=torch.float64,
@@ -438,9 +628,9 @@ def run_ours(args):
             "certified_pairs_per_s": float(bt[3]) / secs,
             "timing": "host clock around a device synchronisation, 1 warm-up + 1 timed step"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, secs, desc = oracle_sample(cfg, sig_h, v1_h, inf["n_apply"])
+        v, secs, desc = oracle_sample(cfg, sig_h, v1_h)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc}
+                                "sample": desc, "host_cores": os.cpu_count()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

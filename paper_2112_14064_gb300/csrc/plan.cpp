@@ -17,8 +17,11 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <iterator>
+#include <map>
+#include <mutex>
 #include <stdexcept>
 #include <thread>
 
@@ -299,8 +302,23 @@ void Plan::build_symbolic() {
 // struct(j) = {i > j : Q_ij != 0} united with the structures of j's
 // elimination-tree children, less j; the parent of j is the first entry of
 // struct(j).  Each structure is merged once into its parent and released.
+// The counts depend only on the mesh, so they are computed once per mesh in
+// the process and cached: later handles of the same mesh (repeated solves)
+// pay nothing.
 void Plan::exact_counts() {
   if (nnz_L_exact >= 0) return;
+  static std::mutex mu;
+  static std::map<std::array<int, 5>, std::pair<int64_t, int64_t>> cache;
+  const std::array<int, 5> key{ne, p, block, nq, leaf_min};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      nnz_L_exact = it->second.first;
+      flops_exact = it->second.second;
+      return;
+    }
+  }
   std::vector<std::vector<int32_t>> st(N);
   std::vector<int32_t> head(N, -1), next(N, -1);
   std::vector<int32_t> buf, tmp;
@@ -333,6 +351,8 @@ void Plan::exact_counts() {
   }
   nnz_L_exact = nnz;
   flops_exact = fl;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = {nnz, fl};
 }
 
 }  // namespace rq
