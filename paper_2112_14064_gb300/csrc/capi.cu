@@ -243,6 +243,7 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     P.factored = false;
     P.cand_valid = false;
     RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
+    rq::prepare_factor(P, precision);
     RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
     rq::launch_factor(P, sigma, precision);
     RQ_CUDA(cudaEventRecord(P.ev1, P.stream));

@@ -886,21 +886,27 @@ void launch_factor_t(Problem& P, double sigma, bool tc = false) {
   }
 }
 
+void prepare_factor(Problem& P, int precision) {
+  if (precision == RIGAQEP_FP64) return;
+  Plan& L = P.plan;
+  if (P.Lval32.n < (size_t)L.l_total) {   // FP32 factor storage on first use
+    P.Lval32.alloc(L.l_total);
+    P.Uval32.alloc(L.u_total);
+    P.Dinv32.alloc(L.N);
+    P.Dval32.alloc(L.N);
+    P.yvec32.alloc(L.upd_idx.size());
+    P.zbuf32.alloc(L.N);
+    P.ir_y.alloc(L.N);
+    P.ir_r32.alloc(L.N);
+  }
+  if (precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR)
+    tc_plan(P, precision == RIGAQEP_BF16_IR);
+}
+
 void launch_factor(Problem& P, double sigma, int precision) {
+  prepare_factor(P, precision);
   if (precision != RIGAQEP_FP64) {
-    Plan& L = P.plan;
-    if (P.Lval32.n < (size_t)L.l_total) {   // FP32 factor storage on first use
-      P.Lval32.alloc(L.l_total);
-      P.Uval32.alloc(L.u_total);
-      P.Dinv32.alloc(L.N);
-      P.Dval32.alloc(L.N);
-      P.yvec32.alloc(L.upd_idx.size());
-      P.zbuf32.alloc(L.N);
-      P.ir_y.alloc(L.N);
-      P.ir_r32.alloc(L.N);
-    }
     const bool tc = precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR;
-    if (tc) tc_plan(P, precision == RIGAQEP_BF16_IR);
     launch_factor_t<float>(P, sigma, tc);
   } else {
     launch_factor_t<double>(P, sigma);

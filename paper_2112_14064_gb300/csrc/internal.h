@@ -250,6 +250,9 @@ void launch_sell(Problem& P);
 void launch_norms(Problem& P);
 // precision: RIGAQEP_FP64, RIGAQEP_FP32_IR, RIGAQEP_TF32_IR or RIGAQEP_BF16_IR
 void launch_factor(Problem& P, double sigma, int precision);
+// buffers and tensor-core plan of a precision, on first use (host work and
+// allocations that rigaqep_factor keeps outside its timed region)
+void prepare_factor(Problem& P, int precision);
 // tensor-core products of the front factorisation (tcfront.cu)
 void tc_plan(Problem& P, bool bf16);
 void launch_tc_level(Problem& P, int level);
