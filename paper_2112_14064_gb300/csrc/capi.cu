@@ -268,6 +268,11 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
       // refinement steps: the fewest that reach 1e-14 on a seeded right-hand
       // side, or the step after which the residual stops halving (at most 40)
       std::vector<double> h = rq::ir_history(P, sigma, 40, 1e-14, 0x5eedull);
+      rq::DevStatus st2;
+      RQ_CUDA(cudaMemcpyAsync(&st2, P.status.p, sizeof(st2), cudaMemcpyDeviceToHost, P.stream));
+      RQ_CUDA(cudaStreamSynchronize(P.stream));
+      if (st2.timeout)
+        throw rq::Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the FB work items ran out");
       int best = 0;
       double best_res = 1.0;
       for (size_t k = 0; k < h.size(); ++k)
@@ -304,7 +309,11 @@ rigaqep_status rigaqep_solve(rigaqep_problem* prob, const double* b, double* x, 
       rq::launch_fb(P, P.xwork.p, P.fact_sigma, nullptr, nullptr, nullptr);
       rq::launch_scatter(P.perm.p, P.xwork.p, x + N * c, N, P.stream);
     }
+    rq::DevStatus st;
+    RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
     RQ_CUDA(cudaStreamSynchronize(P.stream));
+    if (st.timeout)
+      throw rq::Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the FB work items ran out");
   });
 }
 

@@ -681,6 +681,342 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs<T> A
   fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
 }
 
+// ---- dependency-driven sweeps of the upper tree levels ----
+//
+// Above the leaves each level has few items and the level-by-level launches
+// leave most of the GPU idle while a level's few items run their latency
+// chains.  These two kernels run all levels from `first level` upwards
+// (forward) or downwards (backward) in one launch: a block takes the next
+// item by ticket (atomic counter; items are ordered so that every item
+// depends only on items with smaller tickets), waits until the fronts it
+// depends on are complete, runs the item and marks it complete.  A block
+// only ever waits for smaller tickets, which running blocks hold, so the
+// launch cannot deadlock whatever the number of resident blocks.
+//
+// Completion counters are cumulative over solves (epoch e = number of this
+// handle's sweeps so far): forward, kdone[s] counts the finished items of
+// the children of s inside the launch, complete when it reaches
+// e * kid_items[s]; backward, bdone[s] counts the finished items of s,
+// complete at e * bwd_items[s].  Producers publish with a release fence and
+// an atomic add; one thread of the consumer polls with an acquire load
+// (bounded: a wait that runs out records a timeout in the status word and
+// the item runs on stale data; the host reports the error) and the block
+// synchronises before reading.  The last block of a launch resets the
+// ticket counters for the next launch.
+struct FBDep {
+  const int32_t* parent;     // supernode parent (-1: root)
+  const int32_t* kid_items;  // forward: items of the children inside the launch
+  const int32_t* bwd_items;  // backward items of each supernode
+  unsigned* kdone;           // cumulative counters (see above)
+  unsigned* bdone;
+  unsigned* ticket;          // [0] ticket, [1] blocks finished
+  unsigned epoch;
+  DevStatus* status;
+};
+
+constexpr uint32_t kDepWaitLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0: wait until *cnt reaches target (modular comparison)
+__device__ __forceinline__ void dep_wait(const unsigned* cnt, unsigned target, DevStatus* st) {
+  uint32_t it = 0;
+  while ((int)(ld_acquire_u32(cnt) - target) < 0) {
+    if (++it >= kDepWaitLimit) {
+      atomicCAS(&st->timeout, 0, 2);
+      return;
+    }
+  }
+}
+
+// one release add (the item's writes, ordered before it by the preceding
+// block barrier, are visible to whoever acquires the counter)
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int dep_ticket(unsigned* ticket) {
+  __shared__ int tk;
+  __syncthreads();
+  if (threadIdx.x == 0) tk = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  return tk;
+}
+
+__device__ __forceinline__ void dep_finish_launch(unsigned* ticket) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket + 1, 1u) == gridDim.x - 1) {   // last block: reset for the next launch
+      atomicExch(ticket, 0u);
+      atomicExch(ticket + 1, 0u);
+      __threadfence();
+    }
+  }
+}
+
+// Forward item of the dependency-driven sweep.  Same arithmetic as
+// fb_fwd_item; everything that does not depend on the children (up to
+// kPreChunks chunks of eight panel columns per warp, the right-hand side and
+// the gather indices) is loaded before the block waits for the children, so
+// that only the children's update values are read after the wait.
+constexpr int kPreChunks = 5;
+
+template <class T, int RC>
+__device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item,
+                                                const T* xin, T* xg) {
+  constexpr int NP = 8 / RC;
+  __shared__ T part[8][32];
+  __shared__ T yadd[32 * RC];
+  const int4* ip = A.fwd_items + 3 * (int64_t)item;
+  int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
+  const int s = i0.x, r0 = i0.y, nr = i0.z, a = i0.w;
+  const int k = i1.x, u = i1.y, gbase = i1.z;
+  const int64_t F = k + u;
+  const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rc = warp % RC, cp = warp / RC;
+  const int cr0 = r0 + 32 * rc;
+  const int cn = max(0, min(32, nr - 32 * rc));
+  const int row = cr0 + min(lane, max(cn, 1) - 1);
+  int cend = cr0 + cn <= k ? cr0 + cn : k;
+  if (cn == 0) cend = 0;
+  const int q = (cend + NP - 1) / NP;
+  const int cb = cp * q, ce = min(cend, cb + q);
+  const T* pr = P + min(row, (int)F - 1);
+  const int cl = max(cend - 1, 0);
+  T v[kPreChunks][8];
+#pragma unroll
+  for (int c = 0; c < kPreChunks; ++c)
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[c][t] = pr[F * min(cb + 8 * c + t, cl)];
+  const bool kids = i2.z != 0;
+  // this thread's gather positions (at most two before the wait)
+  T xr[2];
+  int g0[2], g1[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = threadIdx.x + 256 * h;
+    xr[h] = T(0);
+    g0[h] = g1[h] = 0;
+    if (t < k) {
+      xr[h] = __ldcg(xin + a + t);
+      if (kids) {
+        g0[h] = A.gptr[gbase + t];
+        g1[h] = A.gptr[gbase + t + 1];
+      }
+    }
+  }
+  int y0 = 0, y1 = 0;
+  const bool yrow = threadIdx.x < nr && r0 + (int)threadIdx.x >= k;
+  if (yrow && kids) {
+    y0 = A.gptr[gbase + r0 + threadIdx.x];
+    y1 = A.gptr[gbase + r0 + threadIdx.x + 1];
+  }
+  // the children's update vectors are complete
+  if (threadIdx.x == 0) dep_wait(D.kdone + s, D.epoch * (unsigned)D.kid_items[s], D.status);
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = threadIdx.x + 256 * h;
+    if (t < k) {
+      T acc = xr[h];
+      for (int g = g0[h]; g < g1[h]; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
+      xg[t] = acc;
+    }
+  }
+  for (int t = threadIdx.x + 512; t < k; t += blockDim.x) {
+    T acc = __ldcg(xin + a + t);
+    if (kids)
+      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
+    xg[t] = acc;
+  }
+  if (yrow) {
+    T acc = T(0);
+    for (int g = y0; g < y1; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
+    yadd[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int c = cb;
+#pragma unroll
+  for (int ch = 0; ch < kPreChunks; ++ch) {
+    if (c < ce) {
+      T w[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
+      s0 += v[ch][0] * w[0];
+      s1 += v[ch][1] * w[1];
+      s2 += v[ch][2] * w[2];
+      s3 += v[ch][3] * w[3];
+      s0 += v[ch][4] * w[4];
+      s1 += v[ch][5] * w[5];
+      s2 += v[ch][6] * w[6];
+      s3 += v[ch][7] * w[7];
+    }
+    c += 8;
+  }
+  for (; c < ce; c += 8) {   // columns beyond the preloaded chunks (largest fronts only)
+    T vv[8], w[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) vv[t] = pr[F * min(c + t, cl)];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
+    s0 += vv[0] * w[0];
+    s1 += vv[1] * w[1];
+    s2 += vv[2] * w[2];
+    s3 += vv[3] * w[3];
+    s0 += vv[4] * w[4];
+    s1 += vv[5] * w[5];
+    s2 += vv[6] * w[6];
+    s3 += vv[7] * w[7];
+  }
+  part[warp][lane] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    const int l = threadIdx.x;
+    const int i = r0 + l;
+    const int lrc = l / 32, ll = l % 32;
+    T dot = T(0);
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) dot += part[pp * RC + lrc][ll];
+    if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
+    else A.yvec[i1.w + (i - k)] = yadd[l] - dot;
+  }
+  __syncthreads();
+}
+
+// Backward item of the dependency-driven sweep.  Same arithmetic as
+// fb_bwd_item with eight warps; the panel blocks (up to two per warp), the
+// pivot-row values of the forward sweep and the indices of the update rows
+// are loaded before the block waits for its parent; only the solution
+// entries of the ancestors are read after the wait.
+template <class T>
+__device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item, T* x,
+                                                double sigma, const T* vu, T* ru, T* rl, T* smem) {
+  constexpr int NW = 8;
+  T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
+  __shared__ T gs[NW][32];
+  __shared__ T red[NW][32];
+  const int4* ip = A.bwd_items + 3 * (int64_t)item;
+  int4 i0 = ip[0], i1 = ip[1], i2 = ip[2];
+  const int s = i0.x, c0 = i0.y, nc = i0.z, a = i0.w;
+  const int k = i1.x, u = i1.y;
+  const int64_t F = k + u;
+  const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32)) + F * c0;
+  const int32_t* st = A.upd_idx + i1.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // blocks 0 and 1 of this warp: rows c0 + 32 warp + lane + 256 b
+  T v[2][32];
+  T zv[2];
+  int xi[2];   // update rows: index into x (-1: pivot row or past the front)
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int64_t i = c0 + 32 * warp + lane + 32 * NW * b;
+    const T* pr = P + (i < F ? i : F - 1);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[b][q] = pr[F * min(q, nc - 1)];
+    zv[b] = T(0);
+    xi[b] = -1;
+    if (i < F) {
+      if (i < k) zv[b] = __ldcg(A.zbuf + a + i);
+      else xi[b] = st[i - k];
+    }
+  }
+  const int pa = D.parent[s];
+  if (threadIdx.x == 0 && pa >= 0)
+    dep_wait(D.bdone + pa, D.epoch * (unsigned)D.bwd_items[pa], D.status);
+  __syncthreads();
+  T acc = T(0);
+  // blocks 0 and 1 from the preloaded registers (compile-time indices), the
+  // rest streamed
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    if (c0 + 32 * warp + 32 * NW * b < F) {
+      gs[warp][lane] = xi[b] >= 0 ? -__ldcg(x + xi[b]) : zv[b];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[b][q];
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+      __syncwarp();
+    }
+  }
+  for (int64_t r0 = c0 + 32 * warp + 2 * 32 * NW; r0 < F; r0 += 32 * NW) {
+    const int64_t i = r0 + lane;
+    T g = T(0);
+    if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
+    const T* pr = P + (i < F ? i : F - 1);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) tile[warp][q][lane] = pr[F * min(q, nc - 1)];
+    gs[warp][lane] = g;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+    __syncwarp();
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (threadIdx.x < nc) {
+    const int l = threadIdx.x;
+    T sum = T(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sum += red[w][l];
+    const int cc = a + c0 + l;
+    x[cc] = sum;
+    if (ru) {
+      ru[cc] = -sum;
+      rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
+    }
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fb_fwd_dep(FBArgs<T> A, FBDep D, int item_begin,
+                                                    int n_items, const T* xin) {
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* xg = reinterpret_cast<T*>(dyn_smem);
+  pdl_wait();
+  for (;;) {
+    const int t = dep_ticket(D.ticket);
+    if (t >= n_items) break;
+    const int item = item_begin + t;
+    const int s = A.fwd_items[3 * (int64_t)item].x;
+    if (A.fwd_items[3 * (int64_t)item + 2].w == 4) fb_fwd_item_pre<T, 4>(A, D, item, xin, xg);
+    else fb_fwd_item_pre<T, 1>(A, D, item, xin, xg);
+    if (threadIdx.x == 0) {   // the item's outputs are written (the item ends in a barrier)
+      const int pa = D.parent[s];
+      if (pa >= 0) red_release_add(D.kdone + pa, 1u);
+    }
+  }
+  dep_finish_launch(D.ticket);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const int32_t* order,
+                                                    int n_items, T* x, double sigma, const T* vu,
+                                                    T* ru, T* rl) {
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  T* smem = reinterpret_cast<T*>(dyn_smem);
+  pdl_wait();
+  for (;;) {
+    const int t = dep_ticket(D.ticket);
+    if (t >= n_items) break;
+    const int item = order[t];
+    const int s = A.bwd_items[3 * (int64_t)item].x;
+    fb_bwd_item_pre<T>(A, D, item, x, sigma, vu, ru, rl, smem);
+    if (threadIdx.x == 0) red_release_add(D.bdone + s, 1u);
+  }
+  dep_finish_launch(D.ticket);
+}
+
 // refinement helpers (FP64 vectors, FP32 correction)
 __global__ void k_to_f32(const double* a, float* b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -756,6 +1092,11 @@ __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, in
 
 }  // namespace
 
+// tree levels below this one run as one launch per level and sweep (the
+// leaves stream the bulk of the factor); the levels from it up run in the
+// dependency-driven launches
+constexpr int kDepLevel = 3;
+
 template <class T>
 constexpr size_t bwd_smem(int nw) {
   return sizeof(T) * (size_t)nw * 32 * 33;
@@ -764,6 +1105,8 @@ constexpr size_t bwd_smem(int nw) {
 void factor_configure(size_t smem_max) {
   smem_at_least((const void*)k_fb_bwd<double, 8>, bwd_smem<double>(8));
   smem_at_least((const void*)k_fb_bwd<float, 8>, bwd_smem<float>(8));
+  smem_at_least((const void*)k_fb_bwd_dep<double>, bwd_smem<double>(8));
+  smem_at_least((const void*)k_fb_bwd_dep<float>, bwd_smem<float>(8));
   if (smem_max > 48 * 1024) {
     smem_at_least((const void*)k_fb_fwd<double, 1>, smem_max);
     smem_at_least((const void*)k_fb_fwd<float, 1>, smem_max / 2);
@@ -948,15 +1291,46 @@ void fb_plan(Problem& P) {
       int nkid = gptr[gbase[s + 1]] - gptr[gbase[s]];   // children's update entries
       for (int r = 0; r < k + u; r += rows)
         fwd.insert(fwd.end(), {s, r, std::min(rows, k + u - r), a, k, u, gbase[s], L.upd_ptr[s],
-                               lo, hi, nkid, 0});
+                               lo, hi, nkid, P.fwd_rc[l]});
       for (int c = 0; c < k; c += 32)
         bwd.insert(bwd.end(), {s, c, std::min(32, k - c), a, k, u, L.upd_ptr[s], 0, lo, hi, 0, 0});
     }
     P.fwd_lvl[l + 1] = (int32_t)(fwd.size() / 12);
     P.bwd_lvl[l + 1] = (int32_t)(bwd.size() / 12);
   }
+  // blocks of the dependency-driven launches: as many as fit on the GPU at
+  // once (more would only queue behind the resident ones)
+  {
+    int fa = 0, ba = 0;
+    P.dep_maxK = 1;
+    for (int l = kDepLevel; l < L.nlevels; ++l) P.dep_maxK = std::max(P.dep_maxK, P.lvl_maxK[l]);
+    RQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &fa, k_fb_fwd_dep<double>, 256, sizeof(double) * (size_t)P.dep_maxK));
+    RQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_fb_bwd_dep<double>, 256,
+                                                          bwd_smem<double>(8)));
+    P.dep_grid_fwd = std::max(1, fa) * P.nsm;
+    P.dep_grid_bwd = std::max(1, ba) * P.nsm;
+  }
   P.fwd_items.upload(fwd, P.stream);
   P.bwd_items.upload(bwd, P.stream);
+  // dependency-driven sweeps of the levels from kDepLevel up: forward items
+  // of the children inside that range, backward items per supernode, and
+  // the backward items root level first (the order of their tickets)
+  std::vector<int32_t> nf(L.nsuper, 0), nb(L.nsuper, 0), kid(L.nsuper, 0), border;
+  for (size_t q = 0; q < fwd.size(); q += 12) ++nf[fwd[q]];
+  for (size_t q = 0; q < bwd.size(); q += 12) ++nb[bwd[q]];
+  for (int sn = 0; sn < L.nsuper; ++sn)
+    if (L.level[sn] >= kDepLevel && L.parent[sn] >= 0) kid[L.parent[sn]] += nf[sn];
+  for (int l = L.nlevels - 1; l >= kDepLevel; --l)
+    for (int q = P.bwd_lvl[l]; q < P.bwd_lvl[l + 1]; ++q) border.push_back(q);
+  P.fb_parent.upload(L.parent, P.stream);
+  P.fb_kid_items.upload(kid, P.stream);
+  P.fb_bwd_items.upload(nb, P.stream);
+  P.fb_border.upload(border, P.stream);
+  P.fb_counters.alloc(2 * (size_t)L.nsuper + 4);
+  RQ_CUDA(cudaMemsetAsync(P.fb_counters.p, 0, sizeof(unsigned) * (2 * (size_t)L.nsuper + 4),
+                          P.stream));
+  P.fb_epoch = 0;
   P.fb_gptr.upload(gptr, P.stream);
   P.fb_gsrc.upload(gsrc, P.stream);
   P.zbuf.alloc(L.N);
@@ -968,7 +1342,10 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FBArgs<T> A = fb_args<T>(P);
-  for (int l = 0; l < L.nlevels; ++l) {
+  const int ldep = std::min(kDepLevel, L.nlevels);   // levels below run one launch each
+  FBDep D{P.fb_parent.p, P.fb_kid_items.p, P.fb_bwd_items.p, P.fb_counters.p,
+          P.fb_counters.p + L.nsuper, P.fb_counters.p + 2 * L.nsuper, ++P.fb_epoch, P.status.p};
+  for (int l = 0; l < ldep; ++l) {
     int ib = P.fwd_lvl[l], ic = P.fwd_lvl[l + 1] - ib;
     const size_t sm = sizeof(T) * (size_t)P.lvl_maxK[l];
     if (P.fwd_rc[l] == 4)
@@ -977,7 +1354,18 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
       launch_pdl(k_fb_fwd<T, 1>, dim3(ic), dim3(256), sm, s, A, ib, (const T*)xn);
     ++P.launches;
   }
-  for (int l = L.nlevels - 1; l >= 0; --l) {
+  if (ldep < L.nlevels) {
+    const int ib = P.fwd_lvl[ldep], ic = P.fwd_lvl[L.nlevels] - ib;
+    const size_t sm = sizeof(T) * (size_t)P.dep_maxK;
+    launch_pdl(k_fb_fwd_dep<T>, dim3((unsigned)std::min(ic, P.dep_grid_fwd)), dim3(256), sm, s, A,
+               D, ib, ic, (const T*)xn);
+    const int nb = (int)P.fb_border.n;
+    D.ticket += 2;
+    launch_pdl(k_fb_bwd_dep<T>, dim3((unsigned)std::min(nb, P.dep_grid_bwd)), dim3(256),
+               bwd_smem<T>(8), s, A, D, (const int32_t*)P.fb_border.p, nb, xn, sigma, vu, ru, rl);
+    P.launches += 2;
+  }
+  for (int l = ldep - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
     if (ic < 2 * P.nsm)
       launch_pdl(k_fb_bwd<T, 8>, dim3(ic), dim3(256), bwd_smem<T>(8), s, A, ib, xn, sigma, vu, ru,

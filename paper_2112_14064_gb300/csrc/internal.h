@@ -219,6 +219,11 @@ struct Problem {
   DBuf<int32_t> fb_gptr, fb_gsrc;       // per front position: children's update entries
   std::vector<int32_t> fwd_lvl, bwd_lvl;  // work items of each level
   std::vector<int32_t> fwd_rc;            // 32-row chunks per forward item, per level
+  // dependency-driven sweeps of the upper levels (factor.cu)
+  DBuf<int32_t> fb_parent, fb_kid_items, fb_bwd_items, fb_border;
+  DBuf<unsigned> fb_counters;   // kdone[nsuper], bdone[nsuper], tickets[4]
+  unsigned fb_epoch = 0;        // sweeps so far (the counters are cumulative)
+  int dep_maxK = 1, dep_grid_fwd = 1, dep_grid_bwd = 1;
   // Krylov workspace
   DBuf<double> V, Vtmp, H, part, hvec, yop, wop, scal, Y;
   DBuf<RitzOut> ritz;

@@ -989,6 +989,8 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaStreamSynchronize(s));
   if (dst.internal)
     throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait for a TMA copy of the basis ran out");
+  if (dst.timeout)
+    throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the FB work items ran out");
   float ms = 0.f;
   RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
   P.info.eigs_ms = ms;
