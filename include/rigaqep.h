@@ -122,7 +122,15 @@ typedef struct {
   int32_t shift_mode;
   double shift;
   int32_t ncand;         /* pairs converged around the shift (0 selects neig) */
+  int32_t scaling;       /* 1: solve the scaled pencil of Remark 4 (below); 0: unscaled */
 } rigaqep_eigs_opts;
+/* Scaling (paper, Remark 4): with varsigma = sqrt(max|K_ij| / max|M_ij|)
+ * (the "infinity norm" of the paper is the largest absolute entry), the
+ * Krylov iteration runs on K + gamma C_s + gamma^2 M_s with C_s = varsigma C,
+ * M_s = varsigma^2 M and gamma = lambda / varsigma: the same shifted factor
+ * Q(s), the operator and B-inner product of the scaled linearisation, and
+ * lambda = varsigma gamma on output (info.scale_factor = varsigma).  In exact
+ * arithmetic the eigenpairs are those of the unscaled call. */
 
 /* Sizes and counters of a handle (host struct filled by rigaqep_get_info). */
 typedef struct {
@@ -167,6 +175,7 @@ typedef struct {
                                  size (-1 before rigaqep_analyze) */
   int64_t factor_flops_exact; /* sum_j (c_j^2 + 2 c_j) with the exact column counts: the
                                  algorithmic factorisation flops (-1 before analyze) */
+  double scale_factor;        /* varsigma of the last eigs (1 when it was not scaled) */
 } rigaqep_info;
 
 /* Create a handle and assemble K, M, C (original DOF order, one CSR

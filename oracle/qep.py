@@ -252,3 +252,28 @@ def _trsen(select, T, Z):
     if info != 0:
         raise ArithmeticError(f"dtrsen failed: {info}")
     return T2, Z2, info
+
+
+def scaling_factor(K, M):
+    """Remark 4: varsigma = sqrt(||K|| / ||M||) with the paper's "infinity
+    norm", the largest absolute entry of the matrix."""
+    return float(np.sqrt(abs(K).max() / abs(M).max()))
+
+
+def eigs_scaled(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=None,
+                ncand=None, sigma_min=None):
+    """The scaled eigenproblem of Remark 4: (K + gamma C_s + gamma^2 M_s) u = 0
+    with C_s = varsigma C, M_s = varsigma^2 M and gamma = lambda / varsigma.
+    Its shifted matrix at gamma_s = s / varsigma is Q(s) itself, so the same
+    solve serves; the target and the damping bound scale like gamma.  The
+    result is mapped back to lambda = varsigma gamma (eigenvectors u are
+    shared; backward errors are those of the original QEP)."""
+    vs = scaling_factor(K, M)
+    r = eigs(K, vs * C, vs * vs * M, s / vs, neig, m, solve, v1, tol=tol,
+             max_restarts=max_restarts, target=None if target is None else target / vs,
+             ncand=ncand, sigma_min=None if sigma_min is None else sigma_min / vs)
+    r.lam = vs * r.lam
+    r.candidates = vs * r.candidates
+    r.eta = np.array([backward_error(l, x, K, C, M) for l, x in zip(r.lam, r.X)])
+    r.scale = vs
+    return r

@@ -145,18 +145,22 @@ __global__ void k_permute(const int32_t* map, const double* a, const double* b, 
 }
 
 // max-row-sum norms; non-negative doubles order like their bit patterns
+// max-row-sum norms of K, M, C (out[0..2]) and the largest entries of K and
+// M (out[3..4]); non-negative doubles compare like their bit patterns
 __global__ void k_row_norms(const int32_t* rowptr, const double* K, const double* M,
                             const double* C, int64_t N, unsigned long long* out) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double s[3] = {0.0, 0.0, 0.0};
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (r < N) {
     for (int32_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
       s[0] += fabs(K[q]);
       s[1] += fabs(M[q]);
       s[2] += fabs(C[q]);
+      s[3] = fmax(s[3], fabs(K[q]));
+      s[4] = fmax(s[4], fabs(M[q]));
     }
   }
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 5; ++t) {
     double v = s[t];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out + t, (unsigned long long)__double_as_longlong(v));
@@ -231,20 +235,22 @@ void launch_assemble(Problem& P) {
 
 void launch_norms(Problem& P) {
   DBuf<unsigned long long> out;
-  out.alloc(3);
-  RQ_CUDA(cudaMemsetAsync(out.p, 0, 3 * sizeof(unsigned long long), P.stream));
+  out.alloc(5);
+  RQ_CUDA(cudaMemsetAsync(out.p, 0, 5 * sizeof(unsigned long long), P.stream));
   int64_t N = P.plan.N;
   k_row_norms<<<(unsigned)((N + 255) / 256), 256, 0, P.stream>>>(P.rowptr.p, P.K.p, P.M.p, P.C.p, N,
                                                                   out.p);
   RQ_CUDA(cudaGetLastError());
-  unsigned long long h[3];
+  unsigned long long h[5];
   RQ_CUDA(cudaMemcpyAsync(h, out.p, sizeof(h), cudaMemcpyDeviceToHost, P.stream));
   RQ_CUDA(cudaStreamSynchronize(P.stream));
-  double d[3];
-  for (int t = 0; t < 3; ++t) std::memcpy(&d[t], &h[t], sizeof(double));
+  double d[5];
+  for (int t = 0; t < 5; ++t) std::memcpy(&d[t], &h[t], sizeof(double));
   P.info.norm_K = d[0];
   P.info.norm_M = d[1];
   P.info.norm_C = d[2];
+  P.maxabs_K = d[3];
+  P.maxabs_M = d[4];
 }
 
 // ND-ordered CSR of the pattern, one warp per ND row j (the original row

@@ -1,6 +1,7 @@
 // C-ABI of rigaqep: argument checks, state machine and error mapping.
 // Every entry point catches all C++ exceptions and returns a status code.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -340,6 +341,10 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     E.max_restarts = opts && opts->max_restarts > 0 ? opts->max_restarts : 1000;
     E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
     E.seed = opts ? opts->seed : 1;
+    need(!opts || opts->scaling == 0 || opts->scaling == 1, RIGAQEP_ERR_ARG, "scaling must be 0 or 1");
+    E.vscale = (opts && opts->scaling == 1 && P.maxabs_M > 0.0) ? std::sqrt(P.maxabs_K / P.maxabs_M)
+                                                                : 1.0;
+    P.info.scale_factor = E.vscale;
     const int32_t prec = opts ? opts->precision : RIGAQEP_FP64;
     need(valid_precision(prec), RIGAQEP_ERR_ARG,
          "precision must be RIGAQEP_FP64, RIGAQEP_TF32_IR, RIGAQEP_FP32_IR or RIGAQEP_BF16_IR");

@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, con
 template <class T, int NW>
 __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, double sigma,
                                             const T* vu, T* ru, T* rl,
-                                            T* smem) {
+                                            T* smem, double uscale) {
   T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
   __shared__ T gs[NW][32];
   __shared__ T red[NW][32];
@@ -664,7 +664,7 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
     int cc = a + c0 + l;
     x[cc] = sum;
     if (ru) {
-      ru[cc] = -sum;
+      ru[cc] = (T)(uscale * (double)(-sum));
       rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
     }
   }
@@ -674,11 +674,11 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
 template <class T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs<T> A, int item_begin, T* x,
                                                    double sigma, const T* vu, T* ru,
-                                                   T* rl) {
+                                                   T* rl, double uscale) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* bwd_smem = reinterpret_cast<T*>(dyn_smem);
-  fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem);
+  fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem, uscale);
 }
 
 // ---- dependency-driven sweeps of the upper tree levels ----
@@ -897,7 +897,8 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
 // entries of the ancestors are read after the wait.
 template <class T>
 __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item, T* x,
-                                                double sigma, const T* vu, T* ru, T* rl, T* smem) {
+                                                double sigma, const T* vu, T* ru, T* rl, T* smem,
+                                                double uscale) {
   constexpr int NW = 8;
   T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
   __shared__ T gs[NW][32];
@@ -969,7 +970,7 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     const int cc = a + c0 + l;
     x[cc] = sum;
     if (ru) {
-      ru[cc] = -sum;
+      ru[cc] = (T)(uscale * (double)(-sum));
       rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
     }
   }
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(256) k_fb_fwd_dep(FBArgs<T> A, FBDep D, int it
 template <class T>
 __global__ void __launch_bounds__(256) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const int32_t* order,
                                                     int n_items, T* x, double sigma, const T* vu,
-                                                    T* ru, T* rl) {
+                                                    T* ru, T* rl, double uscale) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* smem = reinterpret_cast<T*>(dyn_smem);
@@ -1011,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const 
     if (t >= n_items) break;
     const int item = order[t];
     const int s = A.bwd_items[3 * (int64_t)item].x;
-    fb_bwd_item_pre<T>(A, D, item, x, sigma, vu, ru, rl, smem);
+    fb_bwd_item_pre<T>(A, D, item, x, sigma, vu, ru, rl, smem, uscale);
     if (threadIdx.x == 0) red_release_add(D.bdone + s, 1u);
   }
   dep_finish_launch(D.ticket);
@@ -1060,11 +1061,11 @@ __global__ void k_ir_residual64(const int32_t* rowptr, const int32_t* col, const
 
 // operator outputs from the solution x of Q x = y: r_u = -x, r_l = s r_u + v_u
 __global__ void k_op_out(const double* x, double s, const double* vu, double* ru, double* rl,
-                         int64_t n) {
+                         int64_t n, double uscale) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
     double v = -x[i];
-    ru[i] = v;
+    ru[i] = uscale * v;
     rl[i] = s * v + vu[i];
   }
 }
@@ -1338,7 +1339,7 @@ void fb_plan(Problem& P) {
 }
 
 template <class T>
-void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
+void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl, double uscale = 1.0) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FBArgs<T> A = fb_args<T>(P);
@@ -1362,17 +1363,18 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
     const int nb = (int)P.fb_border.n;
     D.ticket += 2;
     launch_pdl(k_fb_bwd_dep<T>, dim3((unsigned)std::min(nb, P.dep_grid_bwd)), dim3(256),
-               bwd_smem<T>(8), s, A, D, (const int32_t*)P.fb_border.p, nb, xn, sigma, vu, ru, rl);
+               bwd_smem<T>(8), s, A, D, (const int32_t*)P.fb_border.p, nb, xn, sigma, vu, ru, rl,
+               uscale);
     P.launches += 2;
   }
   for (int l = ldep - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
     if (ic < 2 * P.nsm)
       launch_pdl(k_fb_bwd<T, 8>, dim3(ic), dim3(256), bwd_smem<T>(8), s, A, ib, xn, sigma, vu, ru,
-                 rl);
+                 rl, uscale);
     else
       launch_pdl(k_fb_bwd<T, 4>, dim3(ic), dim3(128), bwd_smem<T>(4), s, A, ib, xn, sigma, vu, ru,
-                 rl);
+                 rl, uscale);
     ++P.launches;
   }
 }
@@ -1381,7 +1383,8 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl) {
 //   d = Q32^{-1} r_i (FP32 sweeps),  x_{i+1} = x_i + d (FP64),
 //   r_{i+1} = y - Q(s) x_{i+1} (FP64 residual from the assembled K, M, C),
 // for a fixed number of steps chosen when the factor was made.
-void launch_fb_ir(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
+void launch_fb_ir(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl,
+                  double uscale) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   const int64_t N = L.N;
@@ -1404,17 +1407,18 @@ void launch_fb_ir(Problem& P, double* xn, double sigma, const double* vu, double
     }
   }
   if (ru) {
-    k_op_out<<<g, 256, 0, s>>>(xn, sigma, vu, ru, rl, N);
+    k_op_out<<<g, 256, 0, s>>>(xn, sigma, vu, ru, rl, N, uscale);
     RQ_CUDA(cudaGetLastError());
     P.launches += 1;
   }
 }
 
-void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl) {
+void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl,
+               double uscale) {
   if (P.fact_fp32)
-    launch_fb_ir(P, xn, sigma, vu, ru, rl);
+    launch_fb_ir(P, xn, sigma, vu, ru, rl, uscale);
   else
-    launch_fb_t<double>(P, xn, sigma, vu, ru, rl);
+    launch_fb_t<double>(P, xn, sigma, vu, ru, rl, uscale);
 }
 
 // Relative residuals ||y - Q x_k|| / ||y|| of the refinement steps k = 1, 2,

@@ -169,6 +169,7 @@ struct EigsParams {
   int m, max_restarts;
   double tol;
   uint64_t seed;
+  double vscale = 1.0;   // scaled pencil (Remark 4): lambda = vscale * gamma; 1 = unscaled
 };
 
 struct Problem {
@@ -232,6 +233,7 @@ struct Problem {
   int64_t Np = 0;               // N rounded up to 32
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double sigma_min = 0.0, sigma_max = 0.0;  // extremes of the damping coefficients
+  double maxabs_K = 0.0, maxabs_M = 0.0;    // largest entries of K and M (scaling)
   int64_t launches = 0;         // kernel launches of the current call
   std::vector<int32_t> h_lvl_ptr;
   std::vector<int32_t> lvl_maxF;  // largest front order per level
@@ -272,7 +274,9 @@ void factor_plan(Problem& P);
 // FB solve of Q x = b in the ND order, in place on xn (device, length N).
 // If vu != nullptr the backward sweep writes r_u = -x to ru and
 // r_l = sigma * r_u + vu to rl instead of writing x back (the operator step).
-void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl);
+// With uscale != 1 (the scaled pencil) r_u = -uscale * x, r_l = -sigma x + vu.
+void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl,
+               double uscale = 1.0);
 void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n, int32_t ld_in,
                    int32_t ncol, cudaStream_t s);
 void launch_scatter(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);

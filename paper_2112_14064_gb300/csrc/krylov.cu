@@ -27,7 +27,8 @@ namespace rq {
 
 size_t ritz_smem(int m);
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
-                 int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s);
+                 int kwant, int final_pass, int lock, double sigma, double tol, double tscale,
+                 cudaStream_t s);
 
 namespace {
 
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
 __global__ void __launch_bounds__(kSellBlock) k_bnorm(
     const int32_t* off, int64_t ns, const int32_t* col, const double* Ms, const double* zu,
     const double* zl, double* wz, int64_t N, double* part, unsigned* counter, double* H, int ldh,
-    int j, double* scal) {
+    int j, double* scal, double bscale) {
   pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = warp % kSplit;
   const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
@@ -288,8 +289,8 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
   if (sub == 0) {
     double v = 0.0;
     if (r < N) {
-      const double a = sell_combine(red, warp, lane);
-      wz[r] = a;   // (M z_l)_r, the B-image kept with the basis vector
+      const double a = bscale * sell_combine(red, warp, lane);
+      wz[r] = a;   // (bscale M z_l)_r, the B-image kept with the basis vector
       v = zl[r] * a + zu[r] * zu[r];
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -355,8 +356,9 @@ __global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, in
 }
 
 // z *= 1 / ||z||_B over its 3 Np rows (v_u, v_l and the B-image M v_l);
-// also w = s z_u + z_l (rows < Np) for the next operator product
-__global__ void k_scale(double* z, const double* scal, int64_t Np, double s, double* w) {
+// also w = s z_u + c z_l (rows < Np) for the next operator product (c = 1,
+// or the scaling factor of the scaled pencil)
+__global__ void k_scale(double* z, const double* scal, int64_t Np, double s, double c, double* w) {
   pdl_trigger();
   pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -366,7 +368,7 @@ __global__ void k_scale(double* z, const double* scal, int64_t Np, double s, dou
     z[i] = u;
     z[Np + i] = l;
     z[2 * Np + i] *= f;
-    w[i] = s * u + l;
+    w[i] = s * u + c * l;
   }
 }
 
@@ -653,6 +655,7 @@ struct Work {
   int nblk;
   cudaStream_t s;
   double sigma;
+  double vscale = 1.0;   // scaling factor of the scaled pencil (1: unscaled)
   int64_t n_apply = 0, n_spmv = 0, n_vv = 0;
   // FB timing: event pairs around every FB solve of one restart cycle
   std::vector<cudaEvent_t> ev;
@@ -700,11 +703,11 @@ struct Work {
                dim3(kSellBlock), 0, s, P.sell_off.p, ns,
                P.sell_col.p, P.sell_M.p, z,
                (const double*)(z + Np), z + 2 * Np, N, P.part.p, P.counter.p + 1,
-               setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p);
+               setH ? P.H.p : nullptr, m + 1, c - 1, P.scal.p, vscale * vscale);
     ++n_spmv;
     P.launches += 2;
     launch_pdl(k_scale, dim3((unsigned)((Np + 255) / 256)), dim3(256), 0, s, z,
-               (const double*)P.scal.p, Np, sigma, P.wop.p);
+               (const double*)P.scal.p, Np, sigma, vscale, P.wop.p);
     n_vv += 2;
   }
   void step(int j) {
@@ -717,7 +720,7 @@ struct Work {
                P.yop.p, N);
     n_spmv += 3;
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
-    launch_fb(P, P.yop.p, sigma, v, r, r + Np);
+    launch_fb(P, P.yop.p, sigma, v, r, r + Np, vscale);
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     ++n_apply;
     for (int pass = 0; pass < 2; ++pass) {
@@ -743,6 +746,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   const double sigma = E.shift, tol = E.tol;
   const uint64_t seed = E.seed;
   Work W{P, m, L.N, 0, 0, 0, s, sigma};
+  W.vscale = E.vscale;
   W.fb_events(m + 1);
   RQ_CUDA(cudaEventCreate(&W.rz[0]));
   RQ_CUDA(cudaEventCreate(&W.rz[1]));
@@ -804,7 +808,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
     RQ_CUDA(cudaEventRecord(W.rz[0], s));
     // the last allowed cycle always finishes; the others finish when converged
     launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, it >= max_restarts ? 1 : 2,
-                lock, sigma, tol, s);
+                lock, sigma, tol, E.vscale, s);
     RQ_CUDA(cudaEventRecord(W.rz[1], s));
     ++P.launches;
     RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
@@ -857,7 +861,8 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
 
 bool same_candidates(const EigsParams& a, const EigsParams& b) {
   return a.in_region && b.in_region && a.shift == b.shift && a.ncand == b.ncand && a.m == b.m &&
-         a.max_restarts == b.max_restarts && a.tol == b.tol && a.seed == b.seed;
+         a.max_restarts == b.max_restarts && a.tol == b.tol && a.seed == b.seed &&
+         a.vscale == b.vscale;
 }
 
 }  // namespace

@@ -55,6 +55,7 @@ struct RitzArgs {
   int m, neig, kwant, final_pass, lock;   // final_pass: 0 restart, 1 finish, 2 finish if converged
   double sigma, tol;
   uint32_t wait_limit;   // polls of a batch barrier before giving up
+  double tscale;         // lambda = sigma + tscale / theta (scaled pencil: the scaling factor)
 };
 
 struct Smem {
@@ -1217,8 +1218,8 @@ __device__ void ritz_main(const RitzArgs& R, Smem& S, Queue& Q, double* wbuf, in
         if (wl == 0) {
           double ir, ii;
           cdiv(1.0, 0.0, S.wr[pos], S.wi[pos], ir, ii);
-          R.out->lam[2 * rk] = R.sigma + ir;
-          R.out->lam[2 * rk + 1] = ii;
+          R.out->lam[2 * rk] = R.sigma + R.tscale * ir;
+          R.out->lam[2 * rk + 1] = R.tscale * ii;
           R.out->est[rk] = 0.0;
           S.cflag[pos] = 1;
         }
@@ -1245,8 +1246,8 @@ __device__ void ritz_main(const RitzArgs& R, Smem& S, Queue& Q, double* wbuf, in
         // lambda = s + 1/theta
         double ir, ii;
         cdiv(1.0, 0.0, lr, li, ir, ii);
-        R.out->lam[2 * rk] = R.sigma + ir;
-        R.out->lam[2 * rk + 1] = ii;
+        R.out->lam[2 * rk] = R.sigma + R.tscale * ir;
+        R.out->lam[2 * rk + 1] = R.tscale * ii;
         R.out->est[rk] = est;
       }
       if (fin) {
@@ -1388,8 +1389,10 @@ size_t ritz_smem(int m) {
 }
 
 void launch_ritz(const double* H, double* Hnew, double* Q, double* Y, RitzOut* out, int m, int neig,
-                 int kwant, int final_pass, int lock, double sigma, double tol, cudaStream_t s) {
-  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol, ritz_wait_limit()};
+                 int kwant, int final_pass, int lock, double sigma, double tol, double tscale,
+                 cudaStream_t s) {
+  RitzArgs R{H, Hnew, Q, Y, out, m, neig, kwant, final_pass, lock, sigma, tol, ritz_wait_limit(),
+             tscale};
   size_t smem = ritz_smem(m);
   smem_at_least((const void*)k_ritz, smem);
   cudaLaunchConfig_t cfg = {};

@@ -48,7 +48,8 @@ class EigsOpts(ctypes.Structure):
     _fields_ = [("krylov_dim", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("shift_mode", ctypes.c_int32),
-                ("shift", ctypes.c_double), ("ncand", ctypes.c_int32)]
+                ("shift", ctypes.c_double), ("ncand", ctypes.c_int32),
+                ("scaling", ctypes.c_int32)]
 
 
 class BatchJob(ctypes.Structure):
@@ -70,7 +71,7 @@ class Info(ctypes.Structure):
                    ("ritz_phase_cycles", ctypes.c_double * 6),
                    ("n_ir", ctypes.c_int64), ("ir_residual", ctypes.c_double),
                    ("reused_candidates", ctypes.c_int64), ("nnz_L_exact", ctypes.c_int64),
-                   ("factor_flops_exact", ctypes.c_int64)])
+                   ("factor_flops_exact", ctypes.c_int64), ("scale_factor", ctypes.c_double)])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}
@@ -229,7 +230,7 @@ class Problem:
         return x
 
     def eigs(self, neig, sigma, m=None, tol=1e-10, max_restarts=1000, seed=1, v1=None,
-             raise_on_noconv=True, shift=None, ncand=None, precision=FP64):
+             raise_on_noconv=True, shift=None, ncand=None, precision=FP64, scaling=False):
         """Eigenpairs nearest the target sigma: (lambda (neig,) complex,
         X (neig, N) complex, eta (neig,), n_converged, status).
 
@@ -243,7 +244,7 @@ class Problem:
         X = torch.empty((neig, self.N, 2), dtype=torch.float64, device=dev)
         eta = torch.empty(neig, dtype=torch.float64, device=dev)
         nconv = ctypes.c_int32(0)
-        opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand, precision)
+        opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand, precision, scaling)
         if v1 is not None:
             v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
         st = self.lib.rigaqep_eigs(self._h, neig, float(sigma), ctypes.byref(opts), _ptr(v1),
@@ -318,12 +319,12 @@ class Problem:
 
 
 def eigs_opts(neig, m=None, tol=1e-10, max_restarts=1000, seed=1, shift=None, ncand=None,
-              precision=FP64):
+              precision=FP64, scaling=False):
     """rigaqep_eigs_opts with the defaults of Problem.eigs."""
     nc = neig if ncand is None else ncand
     m = m or min(96, 2 * nc + 20)
     return EigsOpts(m, max_restarts, tol, seed, precision, 0 if shift is None else 1,
-                    0.0 if shift is None else float(shift), nc)
+                    0.0 if shift is None else float(shift), nc, 1 if scaling else 0)
 
 
 def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):
@@ -348,7 +349,7 @@ def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):
         X = torch.empty((neig, pr.N, 2), dtype=torch.float64, device=dev)
         eta = torch.empty(neig, dtype=torch.float64, device=dev)
         opts = eigs_opts(neig, **{k: d[k] for k in ("m", "tol", "max_restarts", "seed", "shift",
-                                                   "ncand", "precision") if k in d})
+                                                   "ncand", "precision", "scaling") if k in d})
         arr[j] = BatchJob(d["problem"], neig, float(d["target"]), opts, lam.data_ptr(),
                           X.data_ptr(), eta.data_ptr(), 0, 0, 0, 0, 0.0)
         outs.append((lam, X, eta))

@@ -337,3 +337,43 @@ def test_in_region_agrees_with_literal_shift(rq):
     assert pr.info()["certified"] == 1
     assert same_multiset(a, b, 1e-10)
     pr.close()
+
+
+@pytest.mark.parametrize("name,over,target,kw", [
+    ("tiny", {}, 20.0, dict(m=40)),
+    ("p3_64_b16", {}, 500.0, dict(m=72, shift=0.0, ncand=56))])
+def test_scaled_pencil_matches_oracle(rq, name, over, target, kw):
+    """Remark 4's scaled pencil (scaling=True) against the oracle's scaled
+    solve: the same scaling factor, eigenvalues 1e-10 (multiset), eta <= 1e-10."""
+    c = _cfg(name, **over)
+    A, sym = _oracle(c)
+    sig = workloads.sigma_e(c)
+    v1 = workloads.start_vector(1, 2 * A.N)
+    shift = kw.get("shift", target)
+    F = factorize(sym, A.Q(shift))
+    extra = dict(target=target, ncand=kw["ncand"], sigma_min=sig.min()) if "ncand" in kw else {}
+    ref = qep.eigs_scaled(A.K, A.C, A.M, shift, c["neig"], kw["m"], F.solve, v1, **extra)
+    pr = _problem(rq, c)
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], target, v1=torch.from_numpy(v1).cuda(),
+                                     scaling=True, **kw)
+    inf = pr.info()
+    assert st == 0 and nconv == c["neig"]
+    assert inf["scale_factor"] == pytest.approx(ref.scale, rel=1e-14)
+    assert inf["certified"] == int(ref.certified)
+    assert same_multiset(ref.lam, lam.cpu().numpy(), 1e-10)
+    assert eta.max().item() <= 1e-10
+    pr.close()
+
+
+def test_scaled_pencil_full_size(rq):
+    """256 x 256 bench workload: scaled and unscaled solves agree to 1e-10."""
+    c = _cfg("p3_256_b16")
+    kw = dict(m=96, shift=0.0, ncand=56, seed=1)
+    pr = _problem(rq, c)
+    a = pr.eigs(c["neig"], c["shift"], **kw)[0].cpu().numpy()
+    lam, X, eta, nconv, st = pr.eigs(c["neig"], c["shift"], scaling=True, **kw)
+    inf = pr.info()
+    assert st == 0 and inf["certified"] == 1 and inf["scale_factor"] > 1.0
+    assert same_multiset(a, lam.cpu().numpy(), 1e-10)
+    assert eta.max().item() <= 1e-10
+    pr.close()

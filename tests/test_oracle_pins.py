@@ -465,6 +465,29 @@ def test_in_region_selection_against_dense(mesh, neig, target, ncand, m, certifi
         assert err > 1e-6
 
 
+def test_scaled_pencil_same_eigenvalues():
+    """Remark 4's scaling is an exact change of variable: the scaled oracle
+    returns the dense pencil's eigenvalues (literal shift 20 and the
+    in-region shift with target 300), and varsigma is the square root of the
+    ratio of the largest entries of K and M."""
+    A, _ = _solve_tiny()
+    vs = qep.scaling_factor(A.K, A.M)
+    assert vs == pytest.approx(np.sqrt(np.abs(A.K.toarray()).max() / np.abs(A.M.toarray()).max()))
+    assert vs > 10.0      # K and M differ by orders of magnitude here
+    sym = symbolic(A.n1, A.space.c0_dofs, 2, A.indptr, A.indices)
+    v1 = workloads.start_vector(1, 2 * A.N)
+    F = factorize(sym, A.Q(20.0))
+    r = qep.eigs_scaled(A.K, A.C, A.M, 20.0, 10, 40, F.solve, v1)
+    assert multiset_max_rel(_dense_nearest(A, 20.0, 10), r.lam) < 1e-10
+    assert np.all(r.eta <= 1e-10)
+    sig = workloads.sigma_e(workloads.CONFIGS["tiny"])
+    F0 = factorize(sym, A.Q(0.0))
+    r = qep.eigs_scaled(A.K, A.C, A.M, 0.0, 10, 80, F0.solve, v1, target=300.0, ncand=40,
+                        sigma_min=sig.min())
+    assert r.certified
+    assert multiset_max_rel(_dense_nearest(A, 300.0, 10), r.lam) < 1e-10
+
+
 # ---------------------------------------------------------------- gradient
 def test_gradient_sum_rule_proportional():
     """P-2: with C = cM, sum_e dlambda/dsigma_e = -lambda / (2 lambda + c),
