@@ -317,6 +317,39 @@ rigaqep_status rigaqep_grad_damping_noalloc(rigaqep_problem* prob, int32_t neig,
 rigaqep_status rigaqep_front_gemm(int32_t precision, int32_t m, int32_t n, int32_t k,
                                   const float* A, const float* B, float* C, void* cuda_stream);
 
+/* Undamped pencil K x = mu M x (the QEP without its damping term, lambda =
+ * +-i sqrt(mu)): the number of its eigenvalues mu' < mu, by Sylvester's law
+ * of inertia from the negative pivots of the LDL^T of K - mu M (spectrum
+ * slicing, Section 4.1.4).  The factorisation (FP64, pivots of either sign,
+ * no pivoting) replaces the handle's factor.  *n_below: host.  Returns
+ * RIGAQEP_ERR_PIVOT if a pivot is zero (mu is, in floating point, an
+ * eigenvalue of a leading block of the nested-dissection order).
+ * Defined by: Section 4.1.4 (spectrum slicing). */
+rigaqep_status rigaqep_inertia(rigaqep_problem* prob, double mu, int64_t* n_below);
+
+/* Every eigenpair of the undamped pencil K x = mu M x with mu in [mu_lo,
+ * mu_hi): *count (host) = inertia(mu_hi) - inertia(mu_lo) eigenvalues lie
+ * there; shift-and-invert Lanczos at the midpoint (operator (K - s M)^{-1} M
+ * in the M-inner product, full reorthogonalisation, thick restarts of the
+ * Krylov-Schur kind; Remark 3) converges count + 4 pairs nearest it and
+ * returns those inside the interval, ascending.  Outputs (device): mu
+ * (count values), X (N x count real, column-major, original order, unit
+ * 2-norm, largest entry positive), resid (count backward errors
+ * ||K x - mu M x|| / ((||K|| + |mu| ||M||) ||x||)); *n_found (host)
+ * converged pairs inside; *certified (host) = 1 when exactly *count
+ * converged pairs were found inside.  nmax bounds the outputs
+ * (RIGAQEP_ERR_ARG with *count set if count > nmax); count + 4 must be below
+ * the Krylov dimension (<= 96): split wider intervals.  opts: krylov_dim,
+ * max_restarts, tol, seed as for rigaqep_eigs (precision FP64 only; the
+ * other fields are ignored); v1: optional device start vector of N entries
+ * (NULL: entries N..2N-1 of the seeded 2N stream).  Three factorisations
+ * (lo, hi, midpoint) replace the handle's factor.
+ * Defined by: Remark 3 (Lanczos), Section 4.1.4 (spectrum slicing). */
+rigaqep_status rigaqep_eigs_undamped(rigaqep_problem* prob, double mu_lo, double mu_hi,
+                                     int32_t nmax, const rigaqep_eigs_opts* opts, const double* v1,
+                                     double* mu, double* X, double* resid, int32_t* n_found,
+                                     int32_t* count, int32_t* certified);
+
 /* Copy the original-order CSR (rowptr N+1, col nnz int32; K, M, C nnz
  * doubles) to host buffers; any pointer may be NULL to skip it. */
 rigaqep_status rigaqep_export_csr(const rigaqep_problem* prob, int32_t* rowptr, int32_t* col,

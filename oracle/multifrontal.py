@@ -60,8 +60,13 @@ class Factor:
         return out
 
 
-def factorize(sym, Q):
-    """Multifrontal LDL^T of the symmetric CSR matrix Q (original order)."""
+def factorize(sym, Q, indefinite=False):
+    """Multifrontal LDL^T of the symmetric CSR matrix Q (original order).
+
+    indefinite=False: Q must be positive definite (a non-positive pivot
+    raises PivotError).  indefinite=True: pivots of either sign are kept (a
+    zero or non-finite pivot raises), as for Q = K - mu M with mu inside the
+    spectrum (spectrum slicing, Section 4.1.4); D then carries the inertia."""
     Q = Q.tocsr()
     N = Q.shape[0]
     ns = sym.nsuper
@@ -98,7 +103,10 @@ def factorize(sym, Q):
         # partial LDL^T of the k pivot columns
         for t in range(k):
             d = F[t, t]
-            if not d > 0.0:
+            if indefinite:
+                if not (d != 0.0 and np.isfinite(d)):
+                    raise PivotError(f"zero pivot at supernode {s}")
+            elif not d > 0.0:
                 raise PivotError(f"non-positive pivot {d} at supernode {s}")
             l = F[t + 1:, t] / d
             F[t + 1:, t + 1:] -= d * np.outer(l, l)

@@ -262,6 +262,7 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
                                              ": Q(sigma) is not positive definite");
     P.fact_fp32 = fp32;
     P.fact_prec = precision;
+    P.fact_gep = false;
     P.n_ir = 0;
     P.info.n_ir = 0;
     P.info.ir_residual = 0.0;
@@ -354,7 +355,7 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     need(sigma > 0.0, RIGAQEP_ERR_ARG, "the target must be real and positive");
     need(!E.in_region || E.shift == E.shift, RIGAQEP_ERR_ARG, "shift is NaN");
     P.launches = 0;
-    if (!P.factored || P.fact_sigma != E.shift || P.fact_prec != prec) {
+    if (!P.factored || P.fact_gep || P.fact_sigma != E.shift || P.fact_prec != prec) {
       rigaqep_status fs = rigaqep_factor(prob, E.shift, prec);
       if (fs != RIGAQEP_OK) throw rq::Error(fs, g_last_error);
     }
@@ -598,3 +599,125 @@ rigaqep_status rigaqep_front_gemm(int32_t precision, int32_t m, int32_t n, int32
 }
 
 void rigaqep_set_wait_limit(uint32_t polls) { rq::set_ritz_wait_limit(polls); }
+
+namespace {
+
+// LDL^T of K - mu M (FP64, pivots of either sign) into the handle's factor;
+// returns the number of negative pivots
+int64_t factor_gep(rq::Problem& P, double mu) {
+  P.factored = false;
+  P.cand_valid = false;
+  RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
+  RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
+  rq::launch_factor_gep(P, mu);
+  RQ_CUDA(cudaEventRecord(P.ev1, P.stream));
+  rq::DevStatus st;
+  RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
+  RQ_CUDA(cudaStreamSynchronize(P.stream));
+  float ms = 0.f;
+  RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+  P.info.factor_ms = ms;
+  if (st.pivot_fail)
+    throw rq::Error(RIGAQEP_ERR_PIVOT, "zero pivot in supernode " + std::to_string(st.pivot_fail - 1) +
+                                           ": mu is (numerically) an eigenvalue of a leading block");
+  P.fact_fp32 = false;
+  P.fact_prec = RIGAQEP_FP64;
+  P.fact_gep = true;
+  P.fact_sigma = mu;
+  P.n_ir = 0;
+  P.factored = true;
+  return st.neg_pivots;
+}
+
+}  // namespace
+
+rigaqep_status rigaqep_inertia(rigaqep_problem* prob, double mu, int64_t* n_below) {
+  return guard([&] {
+    need(prob != nullptr && n_below != nullptr, RIGAQEP_ERR_ARG, "NULL argument");
+    need(std::isfinite(mu), RIGAQEP_ERR_ARG, "mu must be finite");
+    rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_inertia");
+    *n_below = factor_gep(P, mu);
+  });
+}
+
+rigaqep_status rigaqep_eigs_undamped(rigaqep_problem* prob, double mu_lo, double mu_hi,
+                                     int32_t nmax, const rigaqep_eigs_opts* opts, const double* v1,
+                                     double* mu, double* X, double* resid, int32_t* n_found,
+                                     int32_t* count, int32_t* certified) {
+  return guard([&] {
+    need(prob != nullptr && n_found != nullptr && count != nullptr && certified != nullptr,
+         RIGAQEP_ERR_ARG, "NULL argument");
+    need(std::isfinite(mu_lo) && std::isfinite(mu_hi) && mu_lo < mu_hi, RIGAQEP_ERR_ARG,
+         "need finite mu_lo < mu_hi");
+    need(nmax >= 0, RIGAQEP_ERR_ARG, "nmax must be >= 0");
+    need(!opts || opts->precision == RIGAQEP_FP64, RIGAQEP_ERR_ARG,
+         "the undamped solve runs in FP64");
+    rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_eigs_undamped");
+    *n_found = 0;
+    *certified = 0;
+    P.launches = 0;
+    // spectrum slicing: eigenvalues in [lo, hi) by Sylvester's law of inertia
+    const int64_t below_lo = factor_gep(P, mu_lo);
+    const int64_t below_hi = factor_gep(P, mu_hi);
+    const int64_t cnt = below_hi - below_lo;
+    need(cnt >= 0, RIGAQEP_ERR_INTERNAL, "inertia decreases with mu");
+    *count = (int32_t)cnt;
+    if (cnt == 0) {
+      *certified = 1;
+      return;
+    }
+    need(cnt <= nmax, RIGAQEP_ERR_ARG, "nmax is smaller than the number of eigenvalues in the interval");
+    need(mu != nullptr && X != nullptr && resid != nullptr, RIGAQEP_ERR_ARG, "NULL output");
+    rq::EigsParams E;
+    E.gep = true;
+    E.lo = mu_lo;
+    E.hi = mu_hi;
+    E.shift = 0.5 * (mu_lo + mu_hi);
+    E.target = E.shift;
+    E.in_region = false;
+    const int extra = 4;
+    E.m = opts && opts->krylov_dim > 0 ? opts->krylov_dim
+                                       : std::min(rq::kMaxKrylov, 2 * (int)cnt + 2 * extra + 20);
+    E.ncand = (int)cnt + extra;
+    E.neig = (int)cnt;
+    need(E.ncand < E.m && E.m <= rq::kMaxKrylov, RIGAQEP_ERR_ARG,
+         "interval too wide for one slice: needs count + 4 < krylov_dim <= 96 (split it)");
+    need(E.m <= P.plan.N, RIGAQEP_ERR_ARG, "krylov_dim exceeds N");
+    E.max_restarts = opts && opts->max_restarts > 0 ? opts->max_restarts : 1000;
+    E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
+    E.seed = opts ? opts->seed : 1;
+    E.vscale = 1.0;
+    factor_gep(P, E.shift);
+    // start vector [0; v1] (v1: N entries, original order), or the upper
+    // half dropped from the 2N seeded stream
+    rq::DBuf<double> v2;
+    if (v1) {
+      v2.alloc(2 * P.plan.N);
+      RQ_CUDA(cudaMemsetAsync(v2.p, 0, sizeof(double) * P.plan.N, P.stream));
+      RQ_CUDA(cudaMemcpyAsync(v2.p + P.plan.N, v1, sizeof(double) * P.plan.N,
+                              cudaMemcpyDeviceToDevice, P.stream));
+    }
+    rq::DBuf<double> lam, Xc;
+    lam.alloc(2 * cnt);
+    Xc.alloc(2 * (size_t)P.plan.N * cnt);
+    int nconv = 0;
+    rq::eigs_run(P, E, v1 ? v2.p : nullptr, lam.p, Xc.p, resid, &nconv);
+    // n_found = converged candidates inside the interval
+    const int nf = nconv;
+    *n_found = nf;
+    *certified = (nf == (int)cnt && P.gep_inside == (int)cnt && P.info.certified == 1) ? 1 : 0;
+    P.info.certified = *certified;
+    if (nf > 0) {
+      // real parts: mu (lam holds (mu, 0)) and X (normalised real vectors)
+      RQ_CUDA(cudaMemcpy2DAsync(mu, sizeof(double), lam.p, 2 * sizeof(double), sizeof(double), nf,
+                                cudaMemcpyDeviceToDevice, P.stream));
+      RQ_CUDA(cudaMemcpy2DAsync(X, sizeof(double), Xc.p, 2 * sizeof(double), sizeof(double),
+                                (size_t)P.plan.N * nf, cudaMemcpyDeviceToDevice, P.stream));
+    }
+    RQ_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}

@@ -54,6 +54,7 @@ struct FrontArgs {
   T* Dinv;
   T* Dval;
   DevStatus* status;
+  int indef;   // 1: pivots of either sign (count the negative ones), 0: SPD
 };
 
 template <class T>
@@ -62,13 +63,13 @@ template <>
 FrontArgs<double> front_args<double>(Problem& P) {
   return FrontArgs<double>{P.sptr.p,      P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
                            P.child_idx.p, P.lvl_nodes.p, P.loff.p,  P.uoff.p,   P.Lval.p,
-                           P.Uval.p,      P.Dinv.p,    P.Dval.p,    P.status.p};
+                           P.Uval.p,      P.Dinv.p,    P.Dval.p,    P.status.p, 0};
 }
 template <>
 FrontArgs<float> front_args<float>(Problem& P) {
   return FrontArgs<float>{P.sptr.p,      P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
                           P.child_idx.p, P.lvl_nodes.p, P.loff.p,  P.uoff.p,   P.Lval32.p,
-                          P.Uval32.p,    P.Dinv32.p,  P.Dval32.p,  P.status.p};
+                          P.Uval32.p,    P.Dinv32.p,  P.Dval32.p,  P.status.p, 0};
 }
 
 // Assembly of the fronts of one level: nsplit CTAs per front, CTA `part`
@@ -156,9 +157,11 @@ __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
   for (int t = 0; t < k; ++t) {
     if (threadIdx.x == 0) {
       T d = L[t + F * t];
-      if (!(d > T(0))) {
+      if (A.indef ? !(d != T(0) && isfinite((double)d)) : !(d > T(0))) {
         atomicCAS(&A.status->pivot_fail, 0, s + 1);
         d = T(1);  // keep going with a harmless value; the host reports the failure
+      } else if (d < T(0)) {
+        atomicAdd(&A.status->neg_pivots, 1);
       }
       dsh = d;
       rdsh = T(1) / d;
@@ -245,9 +248,11 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
       for (int t = 0; t < jb; ++t) {
         if (tid == 0) {
           T d = Y[t + R * t];
-          if (!(d > T(0))) {
+          if (A.indef ? !(d != T(0) && isfinite((double)d)) : !(d > T(0))) {
             atomicCAS(&A.status->pivot_fail, 0, s + 1);
             d = T(1);  // keep going with a harmless value; the host reports the failure
+          } else if (d < T(0)) {
+            atomicAdd(&A.status->neg_pivots, 1);
           }
           dv[t] = d;
           rdv = T(1) / d;
@@ -1166,10 +1171,11 @@ void factor_plan(Problem& P) {
 // tc: the products after the pivot blocks (L21, the Schur update, W) run on
 // the tensor cores (tcfront.cu) instead of k_panel_rows / k_schur_tile
 template <class T>
-void launch_factor_t(Problem& P, double sigma, bool tc = false) {
+void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool indef = false) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FrontArgs<T> A = front_args<T>(P);
+  A.indef = indef ? 1 : 0;
   const int4* rows = (const int4*)P.row_items.p;
   const int4* tiles = (const int4*)P.tile_items.p;
   for (int l = 0; l < L.nlevels; ++l) {
@@ -1177,7 +1183,7 @@ void launch_factor_t(Problem& P, double sigma, bool tc = false) {
     // several CTAs per front on levels with few fronts (about two CTAs per SM)
     const int nsplit = std::max(1, std::min(P.lvl_maxF[l] / 32, (2 * P.nsm + cnt - 1) / cnt));
     k_front_assemble<T><<<cnt * nsplit, 256, 0, s>>>(A, b, nsplit, P.rowptr_n.p, P.fpos.p, P.Kn.p,
-                                                     P.Mn.p, P.Cn.p, sigma * sigma, sigma);
+                                                     P.Mn.p, P.Cn.p, cM, cC);
     RQ_CUDA(cudaGetLastError());
     const int nsm = P.piv_lvl[2 * l + 1] - P.piv_lvl[2 * l];
     const int nbig = P.piv_lvl[2 * l + 2] - P.piv_lvl[2 * l + 1];
@@ -1251,10 +1257,14 @@ void launch_factor(Problem& P, double sigma, int precision) {
   prepare_factor(P, precision);
   if (precision != RIGAQEP_FP64) {
     const bool tc = precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR;
-    launch_factor_t<float>(P, sigma, tc);
+    launch_factor_t<float>(P, sigma * sigma, sigma, tc);
   } else {
-    launch_factor_t<double>(P, sigma);
+    launch_factor_t<double>(P, sigma * sigma, sigma);
   }
+}
+
+void launch_factor_gep(Problem& P, double mu) {
+  launch_factor_t<double>(P, -mu, 0.0, false, true);
 }
 
 void fb_plan(Problem& P) {

@@ -120,7 +120,9 @@ struct DevStatus {
   int32_t pivot_fail;   // first failing supernode + 1 (0 = none)
   int32_t ritz_fail;    // QR iteration limit reached
   int32_t internal;     // consistency check failed
-  int32_t timeout;      // a bounded wait of a tensor-core pipeline ran out
+  int32_t timeout;      // a bounded wait ran out (1: tensor-core pipeline, 2: FB items)
+  int32_t neg_pivots;   // negative pivots of an indefinite factorisation (inertia)
+  int32_t pad[3];
 };
 
 // Output of the Ritz kernel.
@@ -170,6 +172,10 @@ struct EigsParams {
   double tol;
   uint64_t seed;
   double vscale = 1.0;   // scaled pencil (Remark 4): lambda = vscale * gamma; 1 = unscaled
+  // undamped pencil K x = mu M x (Lanczos): the basis keeps v_u = 0 and v_l = x,
+  // the operator is (K - shift M)^{-1} M, the candidates in [lo, hi) are returned
+  bool gep = false;
+  double lo = 0.0, hi = 0.0;
 };
 
 struct Problem {
@@ -205,6 +211,8 @@ struct Problem {
   // FP32 factor (mixed precision: FP32 fronts, FP64 iterative refinement)
   DBuf<float> Lval32, Uval32, Dinv32, Dval32, yvec32, zbuf32, ir_r32;
   DBuf<double> ir_y;
+  bool fact_gep = false;        // the current factor is of K - fact_sigma M (undamped pencil)
+  int gep_inside = 0;           // candidates inside the interval of the last undamped solve
   bool fact_fp32 = false;       // the current factor is stored in FP32 (FP32, TF32 or BF16 fronts)
   int32_t fact_prec = RIGAQEP_FP64;   // precision of the current factor
   TcPlan tc;                    // tensor-core products (TF32 / BF16 fronts)
@@ -257,6 +265,9 @@ void launch_sell(Problem& P);
 void launch_norms(Problem& P);
 // precision: RIGAQEP_FP64, RIGAQEP_FP32_IR, RIGAQEP_TF32_IR or RIGAQEP_BF16_IR
 void launch_factor(Problem& P, double sigma, int precision);
+// LDL^T of K - mu M in FP64 with pivots of either sign (the undamped
+// pencil's spectrum slicing): status->neg_pivots counts the negative ones
+void launch_factor_gep(Problem& P, double mu);
 // buffers and tensor-core plan of a precision, on first use (host work and
 // allocations that rigaqep_factor keeps outside its timed region)
 void prepare_factor(Problem& P, int precision);

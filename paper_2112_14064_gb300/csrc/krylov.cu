@@ -355,6 +355,22 @@ __global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, in
   z[i] -= ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
+// H[lock:m, lock:m] <- its symmetric part (the undamped pencil's projected
+// matrix is symmetric; its entries outside the tridiagonal band are rounding
+// from the full reorthogonalisation), so that the Ritz step sees a
+// symmetric active block.  The locked leading columns stay as they are: the
+// Ritz step relies on their decoupling (zero entries below them).
+__global__ void k_symmetrize(double* H, int ldh, int m, int lock) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m * m; q += gridDim.x * blockDim.x) {
+    const int i = q % m, j = q / m;
+    if (i < j && i >= lock) {
+      const double v = 0.5 * (H[i + (int64_t)ldh * j] + H[j + (int64_t)ldh * i]);
+      H[i + (int64_t)ldh * j] = v;
+      H[j + (int64_t)ldh * i] = v;
+    }
+  }
+}
+
 // z *= 1 / ||z||_B over its 3 Np rows (v_u, v_l and the B-image M v_l);
 // also w = s z_u + c z_l (rows < Np) for the next operator product (c = 1,
 // or the scaling factor of the scaled pencil)
@@ -496,7 +512,7 @@ __global__ void k_colnormalise(double* X, int64_t N, const double* stats) {
 // partial sums of ||K x + l C x + l^2 M x||^2 and ||x||^2 for column t
 __global__ void k_qres(const int32_t* rowptr, const int32_t* col, const double* K, const double* M,
                        const double* C, const double* X, const double* lam, int64_t N,
-                       double* part) {
+                       double* part, double cfac) {
   int t = blockIdx.y;
   const double* x = X + 2 * N * t;
   double lr = lam[2 * t], li = lam[2 * t + 1];
@@ -511,8 +527,8 @@ __global__ void k_qres(const int32_t* rowptr, const int32_t* col, const double* 
       cr += C[q] * xr; ci += C[q] * xi;
       mr += M[q] * xr; mi += M[q] * xi;
     }
-    double rr = kr + (lr * cr - li * ci) + (l2r * mr - l2i * mi);
-    double ri = ki + (lr * ci + li * cr) + (l2r * mi + l2i * mr);
+    double rr = kr + cfac * (lr * cr - li * ci) + (l2r * mr - l2i * mi);
+    double ri = ki + cfac * (lr * ci + li * cr) + (l2r * mi + l2i * mr);
     s += rr * rr + ri * ri;
     sx += x[2 * r] * x[2 * r] + x[2 * r + 1] * x[2 * r + 1];
   }
@@ -656,6 +672,9 @@ struct Work {
   cudaStream_t s;
   double sigma;
   double vscale = 1.0;   // scaling factor of the scaled pencil (1: unscaled)
+  // FB outputs r_u = -fb_uscale x, r_l = -fb_sigma x + v_u: the QEP operator
+  // (sigma, vscale), or r_l = x, r_u = 0 for the undamped pencil (-1, 0)
+  double fb_sigma = 0.0, fb_uscale = 1.0;
   int64_t n_apply = 0, n_spmv = 0, n_vv = 0;
   // FB timing: event pairs around every FB solve of one restart cycle
   std::vector<cudaEvent_t> ev;
@@ -720,7 +739,7 @@ struct Work {
                P.yop.p, N);
     n_spmv += 3;
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
-    launch_fb(P, P.yop.p, sigma, v, r, r + Np, vscale);
+    launch_fb(P, P.yop.p, fb_sigma, v, r, r + Np, fb_uscale);
     RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
     ++n_apply;
     for (int pass = 0; pass < 2; ++pass) {
@@ -747,6 +766,9 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   const uint64_t seed = E.seed;
   Work W{P, m, L.N, 0, 0, 0, s, sigma};
   W.vscale = E.vscale;
+  W.fb_sigma = E.gep ? -1.0 : sigma;
+  W.fb_uscale = E.gep ? 0.0 : E.vscale;
+  if (E.gep) W.sigma = 0.0;   // w = 0 * v_u + v_l: the operator input is v_l alone
   W.fb_events(m + 1);
   RQ_CUDA(cudaEventCreate(&W.rz[0]));
   RQ_CUDA(cudaEventCreate(&W.rz[1]));
@@ -792,6 +814,8 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   }
   k_load_start<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(start, P.perm.p, P.V.p, N, Np);
   RQ_CUDA(cudaGetLastError());
+  if (E.gep)   // undamped pencil: the basis lives in the lower block
+    RQ_CUDA(cudaMemsetAsync(P.V.p, 0, sizeof(double) * Np, s));
   W.normalise(0, false);
 
   // kept at a restart: the candidates plus two (measured: fewer operator
@@ -807,6 +831,11 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
     for (int j = k; j < m; ++j) W.step(j);
     RQ_CUDA(cudaEventRecord(W.rz[0], s));
     // the last allowed cycle always finishes; the others finish when converged
+    if (E.gep) {
+      k_symmetrize<<<(unsigned)((m * m + 255) / 256), 256, 0, s>>>(P.H.p, m + 1, m, lock);
+      RQ_CUDA(cudaGetLastError());
+      ++P.launches;
+    }
     launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, it >= max_restarts ? 1 : 2,
                 lock, sigma, tol, E.vscale, s);
     RQ_CUDA(cudaEventRecord(W.rz[1], s));
@@ -921,16 +950,29 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   // the last Ritz step wrote the eigenvectors of H for the candidate values
   // selection of the neig candidates nearest the target (Im > 0 first on
   // ties), and the certificate that no other eigenvalue is nearer
-  const int neig = E.neig;
+  int neig = E.neig;
   std::vector<int> order(nks);
   for (int i = 0; i < nks; ++i) order[i] = i;
   auto dist = [&](int i) { return std::hypot(h_out.lam[2 * i] - E.target, h_out.lam[2 * i + 1]); };
   auto cls = [&](int i) { double im = h_out.lam[2 * i + 1]; return im > 0 ? 0 : (im == 0 ? 1 : 2); };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    double da = dist(a), db = dist(b);
-    if (da != db) return da < db;
-    return cls(a) < cls(b);
-  });
+  if (E.gep) {
+    // undamped pencil: the candidates with mu in [lo, hi), ascending
+    std::vector<int> in;
+    for (int i = 0; i < nks; ++i)
+      if (h_out.lam[2 * i] >= E.lo && h_out.lam[2 * i] < E.hi) in.push_back(i);
+    std::stable_sort(in.begin(), in.end(),
+                     [&](int a, int b) { return h_out.lam[2 * a] < h_out.lam[2 * b]; });
+    P.gep_inside = (int)in.size();
+    neig = (int)std::min<size_t>(in.size(), (size_t)E.neig);
+    for (int q = 0; q < neig; ++q) order[q] = in[q];
+    P.info.certified = 0;
+  } else {
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      double da = dist(a), db = dist(b);
+      if (da != db) return da < db;
+      return cls(a) < cls(b);
+    });
+  }
   bool all_conv = true;
   for (int i = 0; i < nks; ++i) all_conv = all_conv && (h_out.est[i] <= tol);
   int sel_conv = 0;
@@ -941,7 +983,10 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   }
   double margin = -1.0;
   bool cert = false;
-  if (!E.in_region) {
+  if (E.gep) {
+    cert = all_conv;   // the count check is the caller's (rigaqep_eigs_undamped)
+    margin = 0.0;
+  } else if (!E.in_region) {
     cert = all_conv;
     margin = 0.0;
   } else if (all_conv && E.shift >= 0.0 && E.target >= E.shift && P.sigma_min >= 0.0) {
@@ -957,6 +1002,16 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   }
   P.info.certified = cert ? 1 : 0;
   P.info.cert_margin = margin;
+  if (neig == 0) {   // undamped pencil: no candidate inside the interval
+    RQ_CUDA(cudaEventRecord(P.ev1, s));
+    RQ_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+    P.info.eigs_ms = ms;
+    P.info.n_launches = P.launches;
+    *n_conv = 0;
+    return;
+  }
   std::vector<double> lam_sel(2 * neig);
   DBuf<double> Ysel;
   Ysel.alloc(2 * (size_t)m * neig);
@@ -971,7 +1026,10 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   {
     size_t smem = sizeof(double) * 2 * (size_t)m * neig;
     smem_at_least((const void*)k_eigvec, smem);
-    k_eigvec<<<(unsigned)((N + 127) / 128), 128, smem, s>>>(P.V.p, ld, m, Ysel.p, neig, P.perm.p, X, N);
+    // the eigenvector is the upper block of the QEP basis, the lower one of
+    // the undamped pencil's
+    const double* Vb = E.gep ? P.V.p + basis_np(L.N) : P.V.p;
+    k_eigvec<<<(unsigned)((N + 127) / 128), 128, smem, s>>>(Vb, ld, m, Ysel.p, neig, P.perm.p, X, N);
     RQ_CUDA(cudaGetLastError());
   }
   DBuf<double> stats;
@@ -983,9 +1041,21 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   RQ_CUDA(cudaGetLastError());
   int qb = 2 * P.nsm;
   dim3 gq(qb, neig);
-  k_qres<<<gq, 256, 0, s>>>(P.rowptr.p, P.col.p, P.K.p, P.M.p, P.C.p, X, lambda, N, P.part.p);
+  // residual of the QEP at lambda, or of the undamped pencil: lambda = i sqrt(mu)
+  // makes K + lambda^2 M = K - mu M, with the damping term dropped
+  const double* lres = lambda;
+  DBuf<double> lam_gep;
+  if (E.gep) {
+    std::vector<double> lg(2 * (size_t)neig, 0.0);
+    for (int q = 0; q < neig; ++q) lg[2 * q + 1] = std::sqrt(std::max(0.0, lam_sel[2 * q]));
+    lam_gep.upload(lg, s);
+    lres = lam_gep.p;
+  }
+  k_qres<<<gq, 256, 0, s>>>(P.rowptr.p, P.col.p, P.K.p, P.M.p, P.C.p, X, lres, N, P.part.p,
+                            E.gep ? 0.0 : 1.0);
   RQ_CUDA(cudaGetLastError());
-  k_eta<<<1, 64, 0, s>>>(P.part.p, qb, lambda, P.info.norm_K, P.info.norm_M, P.info.norm_C, eta, neig);
+  k_eta<<<1, 128, 0, s>>>(P.part.p, qb, lres, P.info.norm_K, P.info.norm_M,
+                          E.gep ? 0.0 : P.info.norm_C, eta, neig);
   RQ_CUDA(cudaGetLastError());
   P.launches += 5;
   RQ_CUDA(cudaEventRecord(P.ev1, s));

@@ -26,7 +26,7 @@ EXPORTS = [
     "rigaqep_symbolic_create", "rigaqep_symbolic_sizes", "rigaqep_symbolic_export",
     "rigaqep_symbolic_counts",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
-    "rigaqep_front_gemm", "rigaqep_set_wait_limit",
+    "rigaqep_front_gemm", "rigaqep_set_wait_limit", "rigaqep_inertia", "rigaqep_eigs_undamped",
 ]
 
 
@@ -111,6 +111,9 @@ def load():
         "rigaqep_symbolic_export": [P, P, P, P, P, P, P, P, P],
         "rigaqep_batch_eigs": [ctypes.POINTER(P), I32, ctypes.POINTER(BatchJob), I32, I32],
         "rigaqep_front_gemm": [I32, I32, I32, I32, P, P, P, V],
+        "rigaqep_inertia": [P, D, ctypes.POINTER(I64)],
+        "rigaqep_eigs_undamped": [P, D, D, I32, ctypes.POINTER(EigsOpts), P, P, P, P,
+                                  ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -288,6 +291,32 @@ class Problem:
         _check(self.lib.rigaqep_grad_damping_noalloc(self._h, neig, _ptr(lam_r), _ptr(X_r),
                                                      _ptr(out)))
         return torch.view_as_complex(out)
+
+    # -- undamped pencil K x = mu M x
+    def inertia(self, mu):
+        """Number of eigenvalues of K x = mu' M x below mu (Sylvester)."""
+        n = ctypes.c_int64(0)
+        _check(self.lib.rigaqep_inertia(self._h, float(mu), ctypes.byref(n)))
+        return n.value
+
+    def eigs_undamped(self, mu_lo, mu_hi, nmax=90, m=None, tol=1e-10, max_restarts=1000, seed=1,
+                      v1=None):
+        """Eigenpairs of K x = mu M x with mu in [mu_lo, mu_hi):
+        (mu (n,), X (n, N) real, resid (n,), count, certified)."""
+        torch = self._torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        mu = torch.empty(max(nmax, 1), dtype=torch.float64, device=dev)
+        X = torch.empty((max(nmax, 1), self.N), dtype=torch.float64, device=dev)
+        res = torch.empty(max(nmax, 1), dtype=torch.float64, device=dev)
+        opts = eigs_opts(1, m or 0, tol, max_restarts, seed)
+        opts.krylov_dim = m or 0
+        nf, cnt, cert = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(self.lib.rigaqep_eigs_undamped(self._h, float(mu_lo), float(mu_hi), int(nmax),
+                                              ctypes.byref(opts), _ptr(v1), _ptr(mu), _ptr(X),
+                                              _ptr(res), ctypes.byref(nf), ctypes.byref(cnt),
+                                              ctypes.byref(cert)))
+        n = nf.value
+        return mu[:n], X[:n], res[:n], cnt.value, cert.value
 
     # -- introspection
     def info(self):

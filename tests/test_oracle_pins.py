@@ -18,6 +18,7 @@ from oracle.nd import symbolic, nd_boxes
 from oracle.multifrontal import factorize, PivotError
 from oracle import qep
 from oracle.adjoint import damping_gradient, element_quadratic_forms
+from oracle import gep
 from paper_2112_14064_gb300 import workloads
 from eigmatch import multiset_max_rel
 
@@ -486,6 +487,39 @@ def test_scaled_pencil_same_eigenvalues():
                         sigma_min=sig.min())
     assert r.certified
     assert multiset_max_rel(_dense_nearest(A, 300.0, 10), r.lam) < 1e-10
+
+
+@pytest.mark.parametrize("ne,p,block", [(16, 2, 4), (12, 3, 0)])
+def test_inertia_counts_eigenvalues_below(ne, p, block):
+    """Sylvester's law (Section 4.1.4): the negative pivots of the no-pivot
+    LDL^T of K - mu M count the eigenvalues of K x = mu' M x below mu,
+    compared with LAPACK's symmetric-definite solver."""
+    A = assemble(ne, p, block, np.zeros(ne * ne))
+    sym = symbolic(A.n1, A.space.c0_dofs, p, A.indptr, A.indices, use_c0=block > 0)
+    mu_all = sla.eigh(A.K.toarray(), A.M.toarray(), eigvals_only=True)
+    for mu in (1.0, 30.0, 123.4, 700.0, 5000.0):
+        assert gep.inertia(sym, A.K, A.M, mu) == int((mu_all < mu).sum()), mu
+
+
+def test_lanczos_slice_against_dense():
+    """Spectrum slicing: the eigenvalues in [100, 400) (with the x <-> y
+    double eigenvalues of the square) by inertia counts and shift-and-invert
+    Lanczos at the midpoint, against LAPACK; the slice is certified and every
+    pair has a residual below 1e-10.  When Lanczos is asked for one pair
+    fewer than the inertia count, the count check fails and the slice is
+    not certified (a missed eigenvalue is caught)."""
+    A = assemble(16, 2, 4, np.zeros(256))
+    sym = symbolic(A.n1, A.space.c0_dofs, 2, A.indptr, A.indices)
+    mu_all = sla.eigh(A.K.toarray(), A.M.toarray(), eigvals_only=True)
+    v1 = workloads.start_vector(1, A.N)
+    mus, X, count, cert = gep.slice(sym, A.K, A.M, 100.0, 400.0, 40, v1)
+    ref = mu_all[(mu_all >= 100.0) & (mu_all < 400.0)]
+    assert cert and count == len(ref) == len(mus)
+    assert multiset_max_rel(ref, mus) < 1e-10
+    assert max(gep.residual(A.K, A.M, m_, x) for m_, x in zip(mus, X)) <= 1e-10
+    mus, X, count, cert = gep.slice(sym, A.K, A.M, 100.0, 400.0, 40, v1, extra=-1)
+    assert count == len(ref) and len(mus) == count - 1
+    assert not cert
 
 
 # ---------------------------------------------------------------- gradient
