@@ -176,6 +176,10 @@ typedef struct {
   int64_t factor_flops_exact; /* sum_j (c_j^2 + 2 c_j) with the exact column counts: the
                                  algorithmic factorisation flops (-1 before analyze) */
   double scale_factor;        /* varsigma of the last eigs (1 when it was not scaled) */
+  int64_t tc_wide_levels;     /* TF32/BF16 factor: bit l set when tree level l computes its
+                                 L21 product in 128-column tiles (else 64), as chosen by the
+                                 library's autotuner (both timed on the first tensor-core
+                                 factorisation of the mesh in the process); -1 otherwise */
 } rigaqep_info;
 
 /* Create a handle and assemble K, M, C (original DOF order, one CSR

@@ -263,6 +263,13 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     P.fact_fp32 = fp32;
     P.fact_prec = precision;
     P.fact_gep = false;
+    P.info.tc_wide_levels = -1;
+    if (precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR) {
+      int64_t mask = 0;
+      for (size_t l = 0; l < P.tc.n35.size() && l < 63; ++l)
+        if (P.tc.n35[l] == 128) mask |= (int64_t)1 << l;
+      P.info.tc_wide_levels = mask;
+    }
     P.n_ir = 0;
     P.info.n_ir = 0;
     P.info.ir_residual = 0.0;

@@ -1258,6 +1258,7 @@ void launch_factor(Problem& P, double sigma, int precision) {
   if (precision != RIGAQEP_FP64) {
     const bool tc = precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR;
     launch_factor_t<float>(P, sigma * sigma, sigma, tc);
+    if (tc) tc_tuning_done(P);
   } else {
     launch_factor_t<double>(P, sigma * sigma, sigma);
   }

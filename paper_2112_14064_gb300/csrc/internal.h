@@ -154,9 +154,11 @@ static_assert(sizeof(TcFront) == 64, "TcFront layout");
 struct TcPlan {
   bool ready = false, bf16 = false;
   DBuf<TcFront> fr;
-  DBuf<int32_t> stage, t3, t45;         // stage items, tiles of (3), tiles of (4) and (5)
-  std::vector<int32_t> stage_lvl, t3_lvl, t45_lvl;
+  DBuf<int32_t> stage, t3, t3w, t45;    // stage items, tiles of (3) (N = 64, 128), of (4)+(5)
+  std::vector<int32_t> stage_lvl, t3_lvl, t3w_lvl, t45_lvl;
   std::vector<int32_t> n35, kbmax;      // per level: N of product (3); K-blocks
+  bool tuned = false;                   // n35 chosen by the autotuner (this or an earlier handle)
+  std::vector<std::pair<float, float>> tune_ms;   // timings of N = 64 / 128 when tuned here
   DBuf<unsigned char> hi, lo;           // the two staged planes (split terms)
   DBuf<float> scale;                    // per-front power of two (BF16)
   CUtensorMap maps[4];                  // hi/lo planes, boxes of 128 and 64 rows
@@ -274,6 +276,9 @@ void prepare_factor(Problem& P, int precision);
 // tensor-core products of the front factorisation (tcfront.cu)
 void tc_plan(Problem& P, bool bf16);
 void launch_tc_level(Problem& P, int level);
+void tc_tuning_done(Problem& P);
+bool tc_tuning_lookup(const Plan& L, bool bf16, std::vector<int32_t>& n35);
+void tc_tuning_store(const Plan& L, bool bf16, const std::vector<int32_t>& n35);
 void tc_plain_gemm(int m, int n, int K, const float* A, const float* B, float* C, bool bf16,
                    cudaStream_t s);
 // relative residuals of FP64 refinement steps 1, 2, ... with the FP32 factor

@@ -37,6 +37,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cstring>
 #include <mutex>
 
@@ -539,7 +541,30 @@ void make_tmap_rows(CUtensorMap* map, void* base, bool bf16, uint64_t rows, uint
 
 int kblocks(int K, bool bf16) { return (K + (bf16 ? 64 : 32) - 1) / (bf16 ? 64 : 32); }
 
+// Front-tile autotuner: the width N of the product (3) tiles (64 or 128
+// columns) of every level, chosen by timing both on the first factorisation
+// of a mesh and precision in the process, then reused.
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, std::vector<int32_t>> g_tune;
+
+std::array<int, 6> tune_key(const Plan& L, bool bf16) {
+  return {L.ne, L.p, L.block, L.nq, L.leaf_min, bf16 ? 1 : 0};
+}
+
 }  // namespace
+
+bool tc_tuning_lookup(const Plan& L, bool bf16, std::vector<int32_t>& n35) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(L, bf16));
+  if (it == g_tune.end()) return false;
+  n35 = it->second;
+  return true;
+}
+
+void tc_tuning_store(const Plan& L, bool bf16, const std::vector<int32_t>& n35) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(L, bf16)] = n35;
+}
 
 // Plan of the tensor-core products for precision `bf16` (false: TF32):
 // staged-operand offsets of every front (rows counted from the start of its
@@ -549,19 +574,20 @@ void tc_plan(Problem& P, bool bf16) {
   Plan& L = P.plan;
   if (P.tc.ready && P.tc.bf16 == bf16) return;
   std::vector<TcFront> fr(L.nsuper);
-  std::vector<int32_t> stage, t3, t45;
+  std::vector<int32_t> stage, t3, t3w, t45;
   P.tc.stage_lvl.assign(L.nlevels + 1, 0);
   P.tc.t3_lvl.assign(L.nlevels + 1, 0);
+  P.tc.t3w_lvl.assign(L.nlevels + 1, 0);
   P.tc.t45_lvl.assign(L.nlevels + 1, 0);
   P.tc.n35.assign(L.nlevels, 64);
+  P.tc.tune_ms.assign(L.nlevels, {0.f, 0.f});
   P.tc.kbmax.assign(L.nlevels, 1);
   int64_t rows_max = 0;
   for (int l = 0; l < L.nlevels; ++l) {
     int64_t row = 0;
     int kmax = 0;
     for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) kmax = std::max(kmax, L.sptr[L.lvl_nodes[q] + 1] - L.sptr[L.lvl_nodes[q]]);
-    const int n35 = kmax <= 64 ? 64 : 128;
-    P.tc.n35[l] = n35;
+    P.tc.n35[l] = kmax <= 64 ? 64 : 128;   // until the autotuner has timed both
     P.tc.kbmax[l] = kblocks(kmax, bf16);
     for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
       const int s = L.lvl_nodes[q];
@@ -586,7 +612,8 @@ void tc_plan(Problem& P, bool bf16) {
           for (int r = 0; r < k; r += 32) stage.insert(stage.end(), {s, 2, b, r});
         }
         for (int I = 0; I < u; I += 128) {
-          for (int J = 0; J < k; J += n35) t3.insert(t3.end(), {s, I, J, 0});
+          for (int J = 0; J < k; J += 64) t3.insert(t3.end(), {s, I, J, 0});
+          for (int J = 0; J < k; J += 128) t3w.insert(t3w.end(), {s, I, J, 0});
           for (int J = 0; J <= I; J += 128) t45.insert(t45.end(), {s, I, J, 4});
           for (int J = 0; J < k; J += 128) t45.insert(t45.end(), {s, I, J, 5});
         }
@@ -597,6 +624,7 @@ void tc_plan(Problem& P, bool bf16) {
     rows_max = std::max(rows_max, row);
     P.tc.stage_lvl[l + 1] = (int32_t)(stage.size() / 4);
     P.tc.t3_lvl[l + 1] = (int32_t)(t3.size() / 4);
+    P.tc.t3w_lvl[l + 1] = (int32_t)(t3w.size() / 4);
     P.tc.t45_lvl[l + 1] = (int32_t)(t45.size() / 4);
   }
   cudaStream_t s = P.stream;
@@ -604,6 +632,9 @@ void tc_plan(Problem& P, bool bf16) {
   RQ_CUDA(cudaMemcpyAsync(P.tc.fr.p, fr.data(), fr.size() * sizeof(TcFront), cudaMemcpyHostToDevice, s));
   P.tc.stage.upload(stage, s);
   P.tc.t3.upload(t3, s);
+  P.tc.t3w.upload(t3w, s);
+  // tile widths chosen earlier for this mesh and precision, if any
+  P.tc.tuned = tc_tuning_lookup(L, bf16, P.tc.n35);
   P.tc.t45.upload(t45, s);
   const uint64_t rows = (uint64_t)std::max<int64_t>(rows_max, 128);
   P.tc.hi.alloc(rows * 128);
@@ -644,18 +675,50 @@ void launch_tc_level(Problem& P, int l) {
   ++P.launches;
   const int kbm = P.tc.kbmax[l];
   const int b3 = P.tc.t3_lvl[l], c3 = P.tc.t3_lvl[l + 1] - b3;
+  const int b3w = P.tc.t3w_lvl[l], c3w = P.tc.t3w_lvl[l + 1] - b3w;
   const int b45 = P.tc.t45_lvl[l], c45 = P.tc.t45_lvl[l + 1] - b45;
   const CUtensorMap* mp = P.tc.maps;
-  if (bf16) {
-    if (P.tc.n35[l] == 64) launch_gemm<__nv_bfloat16, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    else launch_gemm<__nv_bfloat16, 128, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    launch_gemm<__nv_bfloat16, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
+  auto product3 = [&](int n) {
+    if (bf16) {
+      if (n == 64) launch_gemm<__nv_bfloat16, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
+      else launch_gemm<__nv_bfloat16, 128, 3>(A, mp, P.tc.t3w.p, b3w, c3w, kbm, s);
+    } else {
+      if (n == 64) launch_gemm<float, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
+      else launch_gemm<float, 128, 3>(A, mp, P.tc.t3w.p, b3w, c3w, kbm, s);
+    }
+  };
+  if (!P.tc.tuned) {
+    // autotuner: time both tile widths (the product is idempotent: the second
+    // run rewrites the same staged L21 and Z), keep the faster
+    cudaEvent_t e[3];
+    for (auto& ev : e) RQ_CUDA(cudaEventCreate(&ev));
+    RQ_CUDA(cudaEventRecord(e[0], s));
+    product3(64);
+    RQ_CUDA(cudaEventRecord(e[1], s));
+    product3(128);
+    RQ_CUDA(cudaEventRecord(e[2], s));
+    RQ_CUDA(cudaEventSynchronize(e[2]));
+    float t64 = 0.f, t128 = 0.f;
+    RQ_CUDA(cudaEventElapsedTime(&t64, e[0], e[1]));
+    RQ_CUDA(cudaEventElapsedTime(&t128, e[1], e[2]));
+    for (auto& ev : e) RQ_CUDA(cudaEventDestroy(ev));
+    P.tc.n35[l] = t128 < t64 ? 128 : 64;
+    P.tc.tune_ms[l] = {t64, t128};
+    P.launches += 2;
   } else {
-    if (P.tc.n35[l] == 64) launch_gemm<float, 64, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    else launch_gemm<float, 128, 3>(A, mp, P.tc.t3.p, b3, c3, kbm, s);
-    launch_gemm<float, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
+    product3(P.tc.n35[l]);
+    ++P.launches;
   }
-  P.launches += 2;
+  if (bf16) launch_gemm<__nv_bfloat16, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
+  else launch_gemm<float, 128, 45>(A, mp, P.tc.t45.p, b45, c45, kbm, s);
+  ++P.launches;
+}
+
+// After the first tensor-core factorisation of a mesh: keep its tile widths.
+void tc_tuning_done(Problem& P) {
+  if (P.tc.tuned) return;
+  P.tc.tuned = true;
+  tc_tuning_store(P.plan, P.tc.bf16, P.tc.n35);
 }
 
 // Plain product C = A B^T (A m x K, B n x K, C m x n, all row-major FP32 on

@@ -71,7 +71,8 @@ class Info(ctypes.Structure):
                    ("ritz_phase_cycles", ctypes.c_double * 6),
                    ("n_ir", ctypes.c_int64), ("ir_residual", ctypes.c_double),
                    ("reused_candidates", ctypes.c_int64), ("nnz_L_exact", ctypes.c_int64),
-                   ("factor_flops_exact", ctypes.c_int64), ("scale_factor", ctypes.c_double)])
+                   ("factor_flops_exact", ctypes.c_int64), ("scale_factor", ctypes.c_double),
+                   ("tc_wide_levels", ctypes.c_int64)])
 
     def as_dict(self):
         d = {n: getattr(self, n) for n, _ in self._fields_}

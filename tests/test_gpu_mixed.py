@@ -124,3 +124,23 @@ def test_mixed_against_fp64_full_size(rq, prec):
     assert same_multiset(a, b, 1e-9)
     assert eta.max().item() <= 1e-10
     pr.close()
+
+
+@pytest.mark.parametrize("prec", ["TF32_IR", "BF16_IR"])
+def test_tile_autotuner_choice_is_reused(rq, prec):
+    """The first tensor-core factorisation of a mesh times both tile widths
+    of the L21 product per level and keeps the faster; a second handle of the
+    same mesh reuses the choice, and both factors give the same solves."""
+    c = dict(workloads.CONFIGS["p3_64_b16"])
+    sig = workloads.sigma_e(c)
+    out = []
+    for _ in range(2):
+        pr = rq.Problem(c["ne"], c["p"], c["block"], sig).analyze()
+        b = torch.from_numpy(np.random.default_rng(9).standard_normal(pr.N)).cuda()
+        pr.factor(0.0, getattr(rq, prec))
+        inf = pr.info()
+        assert inf["tc_wide_levels"] >= 0
+        out.append((inf["tc_wide_levels"], pr.solve(b).cpu().numpy()))
+        pr.close()
+    assert out[0][0] == out[1][0]
+    assert np.abs(out[0][1] - out[1][1]).max() <= 1e-12 * np.abs(out[0][1]).max()
