@@ -112,7 +112,20 @@ typedef enum {
  *    Re lambda in [-max sigma_e / 2, -min sigma_e / 2] (Rayleigh quotients of
  *    the QEP with K, M SPD and C = sum sigma_e M_e, sigma_e >= 0) and real
  *    ones are <= 0, which bounds their distance to the target from below. */
-enum { RIGAQEP_SHIFT_AT_TARGET = 0, RIGAQEP_SHIFT_IN_REGION = 1 };
+enum { RIGAQEP_SHIFT_AT_TARGET = 0, RIGAQEP_SHIFT_IN_REGION = 1, RIGAQEP_SHIFT_COMPLEX = 2 };
+/* RIGAQEP_SHIFT_COMPLEX (2): the shift is the complex number s = opts->shift +
+ *    i opts->shift_imag (shift_imag > 0; Section 4.1.1 allows s in C; with
+ *    s = i sqrt(sigma) the eigenvalues nearest s are the modes of angular
+ *    frequency near sqrt(sigma)).  Q(s) is factorised as a complex symmetric
+ *    LDL^T (FP64), and the Krylov iteration runs on the real operator
+ *    Re((A - s B)^{-1} B), whose eigenvalue for an eigenvalue lambda of the
+ *    pencil is (1/(lambda - s) + 1/(lambda - conj s)) / 2; each converged one
+ *    gives two roots of a quadratic, and the eigenvector decides between them
+ *    (the smaller backward error).  The neig eigenvalues nearest s among the
+ *    ncand converged candidates (0 selects 2 neig + 4: the iteration also
+ *    converges the conjugates near conj s) are returned, nearest first; the
+ *    `sigma` argument of rigaqep_eigs is not used, and info.certified is 0
+ *    (no distance certificate).  FP64 only. */
 typedef struct {
   int32_t krylov_dim;
   int32_t max_restarts;
@@ -123,6 +136,7 @@ typedef struct {
   double shift;
   int32_t ncand;         /* pairs converged around the shift (0 selects neig) */
   int32_t scaling;       /* 1: solve the scaled pencil of Remark 4 (below); 0: unscaled */
+  double shift_imag;     /* imaginary part of the shift (RIGAQEP_SHIFT_COMPLEX) */
 } rigaqep_eigs_opts;
 /* Scaling (paper, Remark 4): with varsigma = sqrt(max|K_ij| / max|M_ij|)
  * (the "infinity norm" of the paper is the largest absolute entry), the
@@ -209,6 +223,21 @@ rigaqep_status rigaqep_analyze(rigaqep_problem* prob);
  * improving; RIGAQEP_ERR_REFINEMENT if the refinement does not contract.
  * Defined by: Algorithm 2 ("Factorize Q(s)"), Section 4.2.1. */
 rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t precision);
+
+/* Complex-symmetric LDL^T of Q(s) = s^2 M + s C + K at s = sr + i si (FP64
+ * complex, no pivoting; every leading block of Q(s) is non-singular when
+ * si != 0 and all sigma_e > 0, its imaginary part si (C + 2 sr M) being
+ * definite for sr >= 0), replacing the handle's factor; then
+ * rigaqep_solve_complex.  RIGAQEP_ERR_PIVOT on a zero pivot.
+ * Defined by: Algorithm 2 ("Factorize Q(s)") with s in C (Section 4.1.1). */
+rigaqep_status rigaqep_factor_complex(rigaqep_problem* prob, double sr, double si);
+
+/* x = Q(s)^{-1} b with the complex factor: b, x device arrays of N complex
+ * values (interleaved re, im; original DOF order), nrhs right-hand sides
+ * (column-major N x nrhs complex); b and x may alias.
+ * Defined by: Section 4.2.2 (forward/backward elimination). */
+rigaqep_status rigaqep_solve_complex(rigaqep_problem* prob, const double* b, double* x,
+                                     int32_t nrhs);
 
 /* x = Q(sigma)^{-1} b for nrhs right-hand sides (device, original DOF order,
  * column-major N x nrhs; b and x may alias; both may be NULL when nrhs = 0).

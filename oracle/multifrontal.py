@@ -36,7 +36,8 @@ class Factor:
         Backward: x_s -= L21^T x_struct, L11^T x_s = x_s, root first.
         """
         sym = self.sym
-        x = np.asarray(b, dtype=np.float64)[sym.perm].copy()
+        dt = np.result_type(self.D.dtype, np.asarray(b).dtype)
+        x = np.asarray(b, dtype=dt)[sym.perm].copy()
         for s in range(sym.nsuper):
             a, e = sym.sptr[s], sym.sptr[s + 1]
             k = e - a
@@ -72,14 +73,16 @@ def factorize(sym, Q, indefinite=False):
     ns = sym.nsuper
     children = sym.children()
     Lblocks = [None] * ns
-    D = np.zeros(N)
+    cplx = np.iscomplexobj(Q.data)
+    dt = np.complex128 if cplx else np.float64
+    D = np.zeros(N, dtype=dt)
     upd = [None] * ns
     for s in range(ns):
         a, e = int(sym.sptr[s]), int(sym.sptr[s + 1])
         k = e - a
         st = sym.struct(s)
         idx = np.concatenate([np.arange(a, e), st])
-        F = np.zeros((len(idx), len(idx)))
+        F = np.zeros((len(idx), len(idx)), dtype=dt)
         # original entries of the pivot columns (symmetric: both triangles)
         for t in range(k):
             old = sym.perm[a + t]
@@ -103,7 +106,10 @@ def factorize(sym, Q, indefinite=False):
         # partial LDL^T of the k pivot columns
         for t in range(k):
             d = F[t, t]
-            if indefinite:
+            if cplx:   # complex symmetric (unconjugated) LDL^T
+                if not (d != 0.0 and np.isfinite(d)):
+                    raise PivotError(f"zero pivot at supernode {s}")
+            elif indefinite:
                 if not (d != 0.0 and np.isfinite(d)):
                     raise PivotError(f"zero pivot at supernode {s}")
             elif not d > 0.0:

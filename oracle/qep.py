@@ -97,13 +97,16 @@ class EigsResult:
 
 
 def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=None,
-         ncand=None, sigma_min=None):
+         ncand=None, sigma_min=None, op=None):
     """Algorithm 2 with CGS2 and Krylov--Schur restarts.
 
     solve(b) must return Q(s)^{-1} b (the factorised shifted pencil).
     v1: start vector of length 2N (original DOF order).
     target/ncand/sigma_min: the target/shift split described above (target
     None: the shift is the target and ncand = neig).
+    op: another operator on 2N vectors in place of Eq. (BlockOperatorVector)
+    (the complex-shift real operator); lambda is then s + 1/theta of its
+    Ritz values theta (see eigs_complex_shift).
     """
     N = M.shape[0]
     ncand = neig if ncand is None else ncand
@@ -119,7 +122,7 @@ def eigs(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, target=No
     steps = []      # basis index j of every operator application, in order
     for it in range(max_restarts + 1):
         for j in range(k, m):
-            r = apply_operator(V[:, j], s, M, C, solve)
+            r = apply_operator(V[:, j], s, M, C, solve) if op is None else op(V[:, j])
             n_apply += 1
             steps.append(j)
             for _ in range(2):                      # CGS2
@@ -277,3 +280,39 @@ def eigs_scaled(K, C, M, s, neig, m, solve, v1, tol=1e-10, max_restarts=1000, ta
     r.eta = np.array([backward_error(l, x, K, C, M) for l, x in zip(r.lam, r.X)])
     r.scale = vs
     return r
+
+
+def eigs_complex_shift(K, C, M, s, neig, m, solve, v1, ncand=None, tol=1e-10,
+                       max_restarts=1000):
+    """Eigenpairs nearest a complex shift s (Section 4.1.1 lets s lie in C).
+
+    solve(b) returns Q(s)^{-1} b for complex b (the complex symmetric factor).
+    The recurrence runs on the real operator
+        R v = Re(L(s)^{-1} B v) = ((A - s B)^{-1} + (A - conj(s) B)^{-1}) B v / 2
+    (Parlett and Saad's real form of a complex shift-and-invert), whose
+    eigenvalue for an eigenvalue lambda of the pencil is
+        psi = (1/(lambda - s) + 1/(lambda - conj s)) / 2
+            = (lambda - a) / ((lambda - s)(lambda - conj s)),  a = Re s.
+    The ncand Ritz values of largest modulus (eigenvalues nearest s or conj s)
+    are converged; each gives the two roots of
+        psi l^2 - (2 a psi + 1) l + psi |s|^2 + a = 0,
+    of which the one with the smaller backward error (same eigenvector
+    x = V_u y) is the eigenvalue.  The neig nearest s are returned."""
+    ncand = 2 * neig + 4 if ncand is None else ncand
+    op = lambda v: np.real(apply_operator(v.astype(complex), s, M, C, solve))  # noqa: E731
+    r = eigs(K, C, M, 0.0, ncand, m, solve, v1, tol=tol, max_restarts=max_restarts, op=op)
+    a, s2 = s.real, abs(s) ** 2
+    lam, eta = [], []
+    for theta_inv, x in zip(r.lam, r.X):
+        psi = 1.0 / theta_inv
+        roots = np.roots([psi, -(2 * a * psi + 1), psi * s2 + a])
+        errs = [backward_error(l, x, K, C, M) for l in roots]
+        j = int(np.argmin(errs))
+        lam.append(roots[j])
+        eta.append(errs[j])
+    lam, eta = np.array(lam), np.array(eta)
+    order = np.lexsort((-lam.imag, np.abs(lam - s)))[:neig]
+    out = EigsResult(lam[order], r.X[order], eta[order], r.n_conv, r.n_restarts, r.n_apply,
+                     r.n_vv)
+    out.certified = False
+    return out

@@ -54,6 +54,33 @@ void need(bool cond, rigaqep_status code, const char* msg) {
   if (!cond) throw rq::Error(code, msg);
 }
 
+// complex-symmetric LDL^T of Q(sr + i si) into the handle's complex factor
+void factor_complex(rq::Problem& P, double sr, double si) {
+  P.factored = false;
+  P.cand_valid = false;
+  RQ_CUDA(cudaMemsetAsync(P.status.p, 0, sizeof(rq::DevStatus), P.stream));
+  RQ_CUDA(cudaEventRecord(P.ev0, P.stream));
+  rq::launch_factor_complex(P, sr, si);
+  RQ_CUDA(cudaEventRecord(P.ev1, P.stream));
+  rq::DevStatus st;
+  RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
+  RQ_CUDA(cudaStreamSynchronize(P.stream));
+  float ms = 0.f;
+  RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+  P.info.factor_ms = ms;
+  if (st.pivot_fail)
+    throw rq::Error(RIGAQEP_ERR_PIVOT, "zero pivot in supernode " + std::to_string(st.pivot_fail - 1) +
+                                           " of the complex factor");
+  P.fact_fp32 = false;
+  P.fact_prec = RIGAQEP_FP64;
+  P.fact_gep = false;
+  P.fact_cplx = true;
+  P.fact_sigma = sr;
+  P.fact_sigma_i = si;
+  P.n_ir = 0;
+  P.factored = true;
+}
+
 bool valid_precision(int32_t p) {
   return p == RIGAQEP_FP64 || p == RIGAQEP_TF32_IR || p == RIGAQEP_FP32_IR || p == RIGAQEP_BF16_IR;
 }
@@ -263,6 +290,7 @@ rigaqep_status rigaqep_factor(rigaqep_problem* prob, double sigma, int32_t preci
     P.fact_fp32 = fp32;
     P.fact_prec = precision;
     P.fact_gep = false;
+    P.fact_cplx = false;
     P.info.tc_wide_levels = -1;
     if (precision == RIGAQEP_TF32_IR || precision == RIGAQEP_BF16_IR) {
       int64_t mask = 0;
@@ -311,6 +339,7 @@ rigaqep_status rigaqep_solve(rigaqep_problem* prob, const double* b, double* x, 
     rq::Problem& P = prob->impl;
     rq::StreamScope scope(P.stream);
     need(P.factored, RIGAQEP_ERR_STATE, "rigaqep_factor must run before rigaqep_solve");
+    need(!P.fact_cplx, RIGAQEP_ERR_STATE, "the factor is complex: use rigaqep_solve_complex");
     int64_t N = P.plan.N;
     // Q is symmetric, so the transposed solve uses the same factors and path.
     for (int c = 0; c < nrhs; ++c) {
@@ -341,10 +370,19 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     E.neig = neig;
     E.target = sigma;
     E.in_region = opts && opts->shift_mode == RIGAQEP_SHIFT_IN_REGION;
-    need(!opts || opts->shift_mode == RIGAQEP_SHIFT_AT_TARGET || E.in_region, RIGAQEP_ERR_ARG,
-         "unknown shift_mode");
-    E.shift = E.in_region ? opts->shift : sigma;
+    E.cplx = opts && opts->shift_mode == RIGAQEP_SHIFT_COMPLEX;
+    need(!opts || opts->shift_mode == RIGAQEP_SHIFT_AT_TARGET || E.in_region || E.cplx,
+         RIGAQEP_ERR_ARG, "unknown shift_mode");
+    E.shift = (E.in_region || E.cplx) ? opts->shift : sigma;
     E.ncand = (E.in_region && opts->ncand > 0) ? opts->ncand : neig;
+    if (E.cplx) {
+      need(std::isfinite(opts->shift) && std::isfinite(opts->shift_imag) && opts->shift_imag > 0.0,
+           RIGAQEP_ERR_ARG, "the complex shift needs a finite shift and shift_imag > 0");
+      E.shift_i = opts->shift_imag;
+      E.target = E.shift;
+      E.ncand = opts->ncand > 0 ? opts->ncand : 2 * neig + 4;
+      sigma = 1.0;   // the target argument is not used in this mode
+    }
     E.m = opts && opts->krylov_dim > 0 ? opts->krylov_dim : std::min(rq::kMaxKrylov, 2 * E.ncand + 20);
     E.max_restarts = opts && opts->max_restarts > 0 ? opts->max_restarts : 1000;
     E.tol = opts && opts->tol > 0 ? opts->tol : 1e-10;
@@ -361,8 +399,14 @@ rigaqep_status rigaqep_eigs(rigaqep_problem* prob, int32_t neig, double sigma,
     need(E.m <= 2 * P.plan.N, RIGAQEP_ERR_ARG, "krylov_dim exceeds 2N");
     need(sigma > 0.0, RIGAQEP_ERR_ARG, "the target must be real and positive");
     need(!E.in_region || E.shift == E.shift, RIGAQEP_ERR_ARG, "shift is NaN");
+    need(!E.cplx || (prec == RIGAQEP_FP64 && !(opts && opts->scaling)), RIGAQEP_ERR_ARG,
+         "the complex shift runs in FP64 without scaling");
     P.launches = 0;
-    if (!P.factored || P.fact_gep || P.fact_sigma != E.shift || P.fact_prec != prec) {
+    if (E.cplx) {
+      if (!P.factored || !P.fact_cplx || P.fact_sigma != E.shift || P.fact_sigma_i != E.shift_i)
+        factor_complex(P, E.shift, E.shift_i);
+    } else if (!P.factored || P.fact_gep || P.fact_cplx || P.fact_sigma != E.shift ||
+               P.fact_prec != prec) {
       rigaqep_status fs = rigaqep_factor(prob, E.shift, prec);
       if (fs != RIGAQEP_OK) throw rq::Error(fs, g_last_error);
     }
@@ -630,6 +674,7 @@ int64_t factor_gep(rq::Problem& P, double mu) {
   P.fact_fp32 = false;
   P.fact_prec = RIGAQEP_FP64;
   P.fact_gep = true;
+  P.fact_cplx = false;
   P.fact_sigma = mu;
   P.n_ir = 0;
   P.factored = true;
@@ -726,5 +771,41 @@ rigaqep_status rigaqep_eigs_undamped(rigaqep_problem* prob, double mu_lo, double
                                 (size_t)P.plan.N * nf, cudaMemcpyDeviceToDevice, P.stream));
     }
     RQ_CUDA(cudaStreamSynchronize(P.stream));
+  });
+}
+
+rigaqep_status rigaqep_factor_complex(rigaqep_problem* prob, double sr, double si) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    need(std::isfinite(sr) && std::isfinite(si), RIGAQEP_ERR_ARG, "the shift must be finite");
+    rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
+    need(P.analyzed, RIGAQEP_ERR_STATE, "rigaqep_analyze must run before rigaqep_factor_complex");
+    factor_complex(P, sr, si);
+  });
+}
+
+rigaqep_status rigaqep_solve_complex(rigaqep_problem* prob, const double* b, double* x,
+                                     int32_t nrhs) {
+  return guard([&] {
+    need(prob != nullptr, RIGAQEP_ERR_ARG, "problem is NULL");
+    need(nrhs >= 0, RIGAQEP_ERR_ARG, "nrhs must be >= 0");
+    need(nrhs == 0 || (b != nullptr && x != nullptr), RIGAQEP_ERR_ARG, "NULL argument");
+    rq::Problem& P = prob->impl;
+    rq::StreamScope scope(P.stream);
+    need(P.factored && P.fact_cplx, RIGAQEP_ERR_STATE,
+         "rigaqep_factor_complex must run before rigaqep_solve_complex");
+    const int64_t N = P.plan.N;
+    for (int c = 0; c < nrhs; ++c) {
+      // gather/scatter the (re, im) pairs as 16-byte elements in the ND order
+      rq::launch_gather2(P.perm.p, b + 2 * N * c, (double*)P.cx.y.p, N, P.stream);
+      rq::launch_fb_complex(P, P.cx.y.p, P.fact_sigma, P.fact_sigma_i, nullptr, nullptr, nullptr);
+      rq::launch_scatter2(P.perm.p, (const double*)P.cx.y.p, x + 2 * N * c, N, P.stream);
+    }
+    rq::DevStatus st;
+    RQ_CUDA(cudaMemcpyAsync(&st, P.status.p, sizeof(st), cudaMemcpyDeviceToHost, P.stream));
+    RQ_CUDA(cudaStreamSynchronize(P.stream));
+    if (st.timeout)
+      throw rq::Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the FB work items ran out");
   });
 }

@@ -32,6 +32,9 @@
 #include "internal.h"
 
 #include <cooperative_groups.h>
+#include <type_traits>
+
+#include "cplx.cuh"
 
 #include <cmath>
 
@@ -57,6 +60,9 @@ struct FrontArgs {
   int indef;   // 1: pivots of either sign (count the negative ones), 0: SPD
 };
 
+// complex storage (double2 pairs) as the kernels' scalar type
+inline zd* zp(double2* p) { return reinterpret_cast<zd*>(p); }
+
 template <class T>
 FrontArgs<T> front_args(Problem& P);
 template <>
@@ -64,6 +70,12 @@ FrontArgs<double> front_args<double>(Problem& P) {
   return FrontArgs<double>{P.sptr.p,      P.upd_ptr.p, P.upd_idx.p, P.relmap.p, P.child_ptr.p,
                            P.child_idx.p, P.lvl_nodes.p, P.loff.p,  P.uoff.p,   P.Lval.p,
                            P.Uval.p,      P.Dinv.p,    P.Dval.p,    P.status.p, 0};
+}
+template <>
+FrontArgs<zd> front_args<zd>(Problem& P) {
+  return FrontArgs<zd>{P.sptr.p,      P.upd_ptr.p,   P.upd_idx.p, P.relmap.p, P.child_ptr.p,
+                       P.child_idx.p, P.lvl_nodes.p, P.loff.p,    P.uoff.p,   zp(P.cx.Lval.p),
+                       zp(P.cx.Uval.p), zp(P.cx.Dinv.p), zp(P.cx.Dval.p), P.status.p, 0};
 }
 template <>
 FrontArgs<float> front_args<float>(Problem& P) {
@@ -82,7 +94,8 @@ FrontArgs<float> front_args<float>(Problem& P) {
 template <class T>
 __global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, int nsplit,
                                  const int32_t* rowptr_n, const int32_t* fpos, const double* Kn,
-                                 const double* Mn, const double* Cn, double s2, double s1) {
+                                 const double* Mn, const double* Cn, double s2, double s1,
+                                 double s2i, double s1i) {
   const int f = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
   int s = A.lvl_nodes[lvl_begin + f];
   int a = A.sptr[s], k = A.sptr[s + 1] - a;
@@ -103,7 +116,8 @@ __global__ void k_front_assemble(FrontArgs<T> A, int lvl_begin, int nsplit,
     int j = a + t;
     for (int32_t q = rowptr_n[j] + lane; q < rowptr_n[j + 1]; q += 32) {
       int pos = fpos[q];
-      if (pos >= 0) L[pos + F * t] = (T)(s2 * Mn[q] + s1 * Cn[q] + Kn[q]);
+      if (pos >= 0)
+        L[pos + F * t] = from_parts<T>(s2 * Mn[q] + s1 * Cn[q] + Kn[q], s2i * Mn[q] + s1i * Cn[q]);
     }
   }
   __syncthreads();
@@ -157,10 +171,10 @@ __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
   for (int t = 0; t < k; ++t) {
     if (threadIdx.x == 0) {
       T d = L[t + F * t];
-      if (A.indef ? !(d != T(0) && isfinite((double)d)) : !(d > T(0))) {
+      if (pivot_bad(d, A.indef)) {
         atomicCAS(&A.status->pivot_fail, 0, s + 1);
         d = T(1);  // keep going with a harmless value; the host reports the failure
-      } else if (d < T(0)) {
+      } else if (pivot_negative(d)) {
         atomicAdd(&A.status->neg_pivots, 1);
       }
       dsh = d;
@@ -216,6 +230,8 @@ __global__ void k_pivot_factor(FrontArgs<T> A, const int32_t* fronts) {
 constexpr int kClusterCTAs = 8;
 constexpr int kClusterMinK = 64;    // pivot blocks from this size use a cluster
 constexpr int kClusterMaxK = 800;   // up to this size (k x 32 panel in shared memory)
+constexpr int kClusterMaxKc = 384;  // the same for the complex factor (16-byte scalars)
+constexpr size_t kSmemOptIn = 227 * 1024;   // largest dynamic shared memory of a CTA
 
 template <class T>
 __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int32_t* fronts) {
@@ -248,10 +264,10 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
       for (int t = 0; t < jb; ++t) {
         if (tid == 0) {
           T d = Y[t + R * t];
-          if (A.indef ? !(d != T(0) && isfinite((double)d)) : !(d > T(0))) {
+          if (pivot_bad(d, A.indef)) {
             atomicCAS(&A.status->pivot_fail, 0, s + 1);
             d = T(1);  // keep going with a harmless value; the host reports the failure
-          } else if (d < T(0)) {
+          } else if (pivot_negative(d)) {
             atomicAdd(&A.status->neg_pivots, 1);
           }
           dv[t] = d;
@@ -493,6 +509,12 @@ FBArgs<double> fb_args<double>(Problem& P) {
                         P.zbuf.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 template <>
+FBArgs<zd> fb_args<zd>(Problem& P) {
+  return FBArgs<zd>{P.upd_idx.p,      P.fb_gptr.p,     P.fb_gsrc.p,     zp(P.cx.Lval.p),
+                    zp(P.cx.Dinv.p),  zp(P.cx.yvec.p), zp(P.cx.zbuf.p),
+                    (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
+}
+template <>
 FBArgs<float> fb_args<float>(Problem& P) {
   return FBArgs<float>{P.upd_idx.p, P.fb_gptr.p, P.fb_gsrc.p, P.Lval32.p, P.Dinv32.p, P.yvec32.p,
                        P.zbuf32.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
@@ -613,10 +635,32 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, con
 // are added at the end in warp order.  Levels with few items (the top of the
 // tree, long panels) use eight warps per item, the others four.  Optionally
 // writes r_u = -x, r_l = sigma r_u + v_u.
+// Operator outputs of the backward sweep from the solution entry x of
+// Q x = y: real scalars r_u = -uscale x, r_l = -sigma x + v_u; complex shift
+// s = sigma + i sigma_i (the real part of the complex operator):
+// r_u = -Re x, r_l = Re(-s x) + v_u.
+template <class T>
+__device__ __forceinline__ void op_out(T sum, double sigma, double sigma_i, double uscale,
+                                       const typename RealOf<T>::type* vu,
+                                       typename RealOf<T>::type* ru, typename RealOf<T>::type* rl,
+                                       int64_t cc) {
+  using R = typename RealOf<T>::type;
+  if constexpr (std::is_same<T, zd>::value) {
+    ru[cc] = -sum.re;
+    rl[cc] = -(sigma * sum.re - sigma_i * sum.im) + vu[cc];
+  } else {
+    (void)sigma_i;
+    ru[cc] = (R)(uscale * (double)(-sum));
+    rl[cc] = (R)(sigma * (double)(-sum)) + vu[cc];
+  }
+}
+
 template <class T, int NW>
 __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, double sigma,
-                                            const T* vu, T* ru, T* rl,
-                                            T* smem, double uscale) {
+                                            const typename RealOf<T>::type* vu,
+                                            typename RealOf<T>::type* ru,
+                                            typename RealOf<T>::type* rl,
+                                            T* smem, double uscale, double sigma_i) {
   T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
   __shared__ T gs[NW][32];
   __shared__ T red[NW][32];
@@ -668,22 +712,20 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
     for (int w = 0; w < NW; ++w) sum += red[w][l];
     int cc = a + c0 + l;
     x[cc] = sum;
-    if (ru) {
-      ru[cc] = (T)(uscale * (double)(-sum));
-      rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
-    }
+    if (ru) op_out<T>(sum, sigma, sigma_i, uscale, vu, ru, rl, cc);
   }
   __syncthreads();
 }
 
 template <class T, int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_fb_bwd(FBArgs<T> A, int item_begin, T* x,
-                                                   double sigma, const T* vu, T* ru,
-                                                   T* rl, double uscale) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1)
+    k_fb_bwd(FBArgs<T> A, int item_begin, T* x, double sigma,
+             const typename RealOf<T>::type* vu, typename RealOf<T>::type* ru,
+             typename RealOf<T>::type* rl, double uscale, double sigma_i) {
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   T* bwd_smem = reinterpret_cast<T*>(dyn_smem);
-  fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem, uscale);
+  fb_bwd_item<T, NW>(A, item_begin + blockIdx.x, x, sigma, vu, ru, rl, bwd_smem, uscale, sigma_i);
 }
 
 // ---- dependency-driven sweeps of the upper tree levels ----
@@ -902,8 +944,11 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
 // entries of the ancestors are read after the wait.
 template <class T>
 __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item, T* x,
-                                                double sigma, const T* vu, T* ru, T* rl, T* smem,
+                                                double sigma, const typename RealOf<T>::type* vu,
+                                                typename RealOf<T>::type* ru,
+                                                typename RealOf<T>::type* rl, T* smem,
                                                 double uscale) {
+  const double sigma_i = 0.0;   // the dependency-driven sweeps serve the real factors
   constexpr int NW = 8;
   T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
   __shared__ T gs[NW][32];
@@ -974,10 +1019,7 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     for (int w = 0; w < NW; ++w) sum += red[w][l];
     const int cc = a + c0 + l;
     x[cc] = sum;
-    if (ru) {
-      ru[cc] = (T)(uscale * (double)(-sum));
-      rl[cc] = (T)(sigma * (double)(-sum)) + vu[cc];
-    }
+    if (ru) op_out<T>(sum, sigma, sigma_i, uscale, vu, ru, rl, cc);
   }
   __syncthreads();
 }
@@ -1091,6 +1133,16 @@ __global__ void k_gather(const int32_t* idx, const double* src, double* dst, int
   if (i < n) dst[i] = src[idx[i]];
 }
 
+__global__ void k_gather2(const int32_t* idx, const double2* src, double2* dst, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void k_scatter2(const int32_t* idx, const double2* src, double2* dst, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[idx[i]] = src[i];
+}
+
 __global__ void k_scatter(const int32_t* idx, const double* src, double* dst, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) dst[idx[i]] = src[i];
@@ -1119,6 +1171,14 @@ void factor_configure(size_t smem_max) {
     smem_at_least((const void*)k_fb_fwd<double, 4>, smem_max);
     smem_at_least((const void*)k_fb_fwd<float, 4>, smem_max / 2);
   }
+}
+
+// largest dynamic shared memory of a forward sweep item in FP64 (the
+// gathered right-hand side of the largest pivot block)
+size_t smem_fwd_max(const Problem& P) {
+  int k = 1;
+  for (int v : P.lvl_maxK) k = std::max(k, v);
+  return sizeof(double) * (size_t)k;
 }
 
 void factor_plan(Problem& P) {
@@ -1154,10 +1214,29 @@ void factor_plan(Problem& P) {
     }
   }
   P.piv_fronts.upload(pf, P.stream);
+  // the complex factor's pivot blocks: its 32-column cluster panel holds
+  // twice the bytes, so blocks of more than kClusterMaxKc pivots go to the
+  // one-CTA kernel
+  {
+    std::vector<int32_t> pc;
+    P.cx.piv_lvl.assign(2 * L.nlevels + 1, 0);
+    for (int l = 0; l < L.nlevels; ++l)
+      for (int big = 0; big < 2; ++big) {
+        for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
+          int sn = L.lvl_nodes[q];
+          int k = L.sptr[sn + 1] - L.sptr[sn];
+          bool isbig = k >= kClusterMinK && k <= kClusterMaxKc;
+          if (isbig == (big == 1)) pc.push_back(sn);
+        }
+        P.cx.piv_lvl[2 * l + big + 1] = (int32_t)pc.size();
+      }
+    P.cx.piv_fronts.upload(pc, P.stream);
+  }
   {
     size_t cs = sizeof(double) * 32 * (size_t)kClusterMaxK;
     smem_at_least((const void*)k_pivot_cluster<double>, cs);
     smem_at_least((const void*)k_pivot_cluster<float>, cs / 2);
+    smem_at_least((const void*)k_pivot_cluster<zd>, sizeof(zd) * 32 * (size_t)kClusterMaxKc);
   }
   P.Dval.alloc(L.N);
   size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
@@ -1166,16 +1245,32 @@ void factor_plan(Problem& P) {
   size_t piv = sizeof(double) * (size_t)L.max_front;
   if (piv > 48 * 1024) smem_at_least((const void*)k_pivot_factor<double>, piv);
   if (piv / 2 > 48 * 1024) smem_at_least((const void*)k_pivot_factor<float>, piv / 2);
+  // the complex kernels' row panels and pivot staging hold k complex values
+  // per row (k = the largest pivot block)
+  const size_t kmax = smem_fwd_max(P) / sizeof(double);
+  const size_t zrows = sizeof(zd) * 16 * kmax, zpiv = sizeof(zd) * kmax;
+  if (zrows > 48 * 1024 && zrows <= kSmemOptIn)
+    smem_at_least((const void*)k_panel_rows<zd>, zrows);
+  if (zpiv > 48 * 1024 && zpiv <= kSmemOptIn) smem_at_least((const void*)k_pivot_factor<zd>, zpiv);
+  smem_at_least((const void*)k_fb_bwd<zd, 8>, bwd_smem<zd>(8));
+  if (2 * smem_fwd_max(P) > 48 * 1024)
+    smem_at_least((const void*)k_fb_fwd<zd, 1>, 2 * smem_fwd_max(P));
+  if (2 * smem_fwd_max(P) > 48 * 1024)
+    smem_at_least((const void*)k_fb_fwd<zd, 4>, 2 * smem_fwd_max(P));
 }
 
 // tc: the products after the pivot blocks (L21, the Schur update, W) run on
 // the tensor cores (tcfront.cu) instead of k_panel_rows / k_schur_tile
 template <class T>
-void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool indef = false) {
+void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool indef = false,
+                     double cMi = 0.0, double cCi = 0.0) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FrontArgs<T> A = front_args<T>(P);
   A.indef = indef ? 1 : 0;
+  constexpr bool cplx = std::is_same<T, zd>::value;
+  const int32_t* piv_fronts = cplx ? P.cx.piv_fronts.p : P.piv_fronts.p;
+  const std::vector<int32_t>& piv_lvl = cplx ? P.cx.piv_lvl : P.piv_lvl;
   const int4* rows = (const int4*)P.row_items.p;
   const int4* tiles = (const int4*)P.tile_items.p;
   for (int l = 0; l < L.nlevels; ++l) {
@@ -1183,13 +1278,13 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
     // several CTAs per front on levels with few fronts (about two CTAs per SM)
     const int nsplit = std::max(1, std::min(P.lvl_maxF[l] / 32, (2 * P.nsm + cnt - 1) / cnt));
     k_front_assemble<T><<<cnt * nsplit, 256, 0, s>>>(A, b, nsplit, P.rowptr_n.p, P.fpos.p, P.Kn.p,
-                                                     P.Mn.p, P.Cn.p, cM, cC);
+                                                     P.Mn.p, P.Cn.p, cM, cC, cMi, cCi);
     RQ_CUDA(cudaGetLastError());
-    const int nsm = P.piv_lvl[2 * l + 1] - P.piv_lvl[2 * l];
-    const int nbig = P.piv_lvl[2 * l + 2] - P.piv_lvl[2 * l + 1];
+    const int nsm = piv_lvl[2 * l + 1] - piv_lvl[2 * l];
+    const int nbig = piv_lvl[2 * l + 2] - piv_lvl[2 * l + 1];
     if (nsm > 0) {
       k_pivot_factor<T><<<nsm, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(
-          A, P.piv_fronts.p + P.piv_lvl[2 * l]);
+          A, piv_fronts + piv_lvl[2 * l]);
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
@@ -1197,7 +1292,8 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(nbig * kClusterCTAs));
       cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = sizeof(T) * 32 * (size_t)P.lvl_maxK[l];
+      cfg.dynamicSmemBytes =
+          sizeof(T) * 32 * (size_t)std::min(P.lvl_maxK[l], cplx ? kClusterMaxKc : kClusterMaxK);
       cfg.stream = s;
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1206,7 +1302,7 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      const int32_t* fl = P.piv_fronts.p + P.piv_lvl[2 * l + 1];
+      const int32_t* fl = piv_fronts + piv_lvl[2 * l + 1];
       RQ_CUDA(cudaLaunchKernelEx(&cfg, k_pivot_cluster<T>, A, fl));
       ++P.launches;
     }
@@ -1266,6 +1362,21 @@ void launch_factor(Problem& P, double sigma, int precision) {
 
 void launch_factor_gep(Problem& P, double mu) {
   launch_factor_t<double>(P, -mu, 0.0, false, true);
+}
+
+// Q(s) = K + s C + s^2 M at s = sr + i si, complex symmetric LDL^T (FP64)
+void launch_factor_complex(Problem& P, double sr, double si) {
+  Plan& L = P.plan;
+  if (P.cx.Lval.n < (size_t)L.l_total) {   // complex factor storage on first use
+    P.cx.Lval.alloc(L.l_total);
+    P.cx.Uval.alloc(L.u_total);
+    P.cx.Dinv.alloc(L.N);
+    P.cx.Dval.alloc(L.N);
+    P.cx.yvec.alloc(L.upd_idx.size());
+    P.cx.zbuf.alloc(L.N);
+    P.cx.y.alloc(L.N);
+  }
+  launch_factor_t<zd>(P, sr * sr - si * si, sr, false, false, 2.0 * sr * si, si);
 }
 
 void fb_plan(Problem& P) {
@@ -1350,11 +1461,15 @@ void fb_plan(Problem& P) {
 }
 
 template <class T>
-void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl, double uscale = 1.0) {
+void launch_fb_t(Problem& P, T* xn, double sigma, const typename RealOf<T>::type* vu,
+                 typename RealOf<T>::type* ru, typename RealOf<T>::type* rl, double uscale = 1.0,
+                 double sigma_i = 0.0) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
   FBArgs<T> A = fb_args<T>(P);
-  const int ldep = std::min(kDepLevel, L.nlevels);   // levels below run one launch each
+  constexpr bool cplx = std::is_same<T, zd>::value;
+  // levels below ldep run one launch each (all levels for the complex factor)
+  const int ldep = cplx ? L.nlevels : std::min(kDepLevel, L.nlevels);
   FBDep D{P.fb_parent.p, P.fb_kid_items.p, P.fb_bwd_items.p, P.fb_counters.p,
           P.fb_counters.p + L.nsuper, P.fb_counters.p + 2 * L.nsuper, ++P.fb_epoch, P.status.p};
   for (int l = 0; l < ldep; ++l) {
@@ -1366,7 +1481,7 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl, dou
       launch_pdl(k_fb_fwd<T, 1>, dim3(ic), dim3(256), sm, s, A, ib, (const T*)xn);
     ++P.launches;
   }
-  if (ldep < L.nlevels) {
+  if constexpr (!cplx) if (ldep < L.nlevels) {
     const int ib = P.fwd_lvl[ldep], ic = P.fwd_lvl[L.nlevels] - ib;
     const size_t sm = sizeof(T) * (size_t)P.dep_maxK;
     launch_pdl(k_fb_fwd_dep<T>, dim3((unsigned)std::min(ic, P.dep_grid_fwd)), dim3(256), sm, s, A,
@@ -1380,12 +1495,16 @@ void launch_fb_t(Problem& P, T* xn, double sigma, const T* vu, T* ru, T* rl, dou
   }
   for (int l = ldep - 1; l >= 0; --l) {
     int ib = P.bwd_lvl[l], ic = P.bwd_lvl[l + 1] - ib;
-    if (ic < 2 * P.nsm)
+    bool wide = ic < 2 * P.nsm;
+    if constexpr (cplx) wide = true;   // eight warps per item (the complex blocks use more registers)
+    if (wide) {
       launch_pdl(k_fb_bwd<T, 8>, dim3(ic), dim3(256), bwd_smem<T>(8), s, A, ib, xn, sigma, vu, ru,
-                 rl, uscale);
-    else
-      launch_pdl(k_fb_bwd<T, 4>, dim3(ic), dim3(128), bwd_smem<T>(4), s, A, ib, xn, sigma, vu, ru,
-                 rl, uscale);
+                 rl, uscale, sigma_i);
+    } else {
+      if constexpr (!cplx)
+        launch_pdl(k_fb_bwd<T, 4>, dim3(ic), dim3(128), bwd_smem<T>(4), s, A, ib, xn, sigma, vu,
+                   ru, rl, uscale, sigma_i);
+    }
     ++P.launches;
   }
 }
@@ -1422,6 +1541,11 @@ void launch_fb_ir(Problem& P, double* xn, double sigma, const double* vu, double
     RQ_CUDA(cudaGetLastError());
     P.launches += 1;
   }
+}
+
+void launch_fb_complex(Problem& P, void* xn, double sr, double si, const double* vu, double* ru,
+                       double* rl) {
+  launch_fb_t<zd>(P, static_cast<zd*>(xn), sr, vu, ru, rl, 1.0, si);
 }
 
 void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* ru, double* rl,
@@ -1484,6 +1608,16 @@ void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n
                                                           dst + (int64_t)c * n, n);
     RQ_CUDA(cudaGetLastError());
   }
+}
+
+void launch_gather2(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s) {
+  k_gather2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(idx, (const double2*)src, (double2*)dst, n);
+  RQ_CUDA(cudaGetLastError());
+}
+
+void launch_scatter2(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s) {
+  k_scatter2<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(idx, (const double2*)src, (double2*)dst, n);
+  RQ_CUDA(cudaGetLastError());
 }
 
 void launch_scatter(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s) {

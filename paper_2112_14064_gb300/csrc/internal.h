@@ -178,6 +178,10 @@ struct EigsParams {
   // the operator is (K - shift M)^{-1} M, the candidates in [lo, hi) are returned
   bool gep = false;
   double lo = 0.0, hi = 0.0;
+  // complex shift s = shift + i shift_i (real operator Re((A - s B)^{-1} B);
+  // the selection is nearest s)
+  bool cplx = false;
+  double shift_i = 0.0;
 };
 
 struct Problem {
@@ -218,6 +222,14 @@ struct Problem {
   bool fact_fp32 = false;       // the current factor is stored in FP32 (FP32, TF32 or BF16 fronts)
   int32_t fact_prec = RIGAQEP_FP64;   // precision of the current factor
   TcPlan tc;                    // tensor-core products (TF32 / BF16 fronts)
+  // complex-shift factor (complex FP64 scalars, 16 bytes each; cplx.cuh)
+  struct Complex {
+    DBuf<double2> Lval, Uval, Dinv, Dval, yvec, zbuf, y;
+    DBuf<int32_t> piv_fronts;
+    std::vector<int32_t> piv_lvl;
+  } cx;
+  bool fact_cplx = false;       // the current factor is the complex one (shift fact_sigma + i fact_sigma_i)
+  double fact_sigma_i = 0.0;
   int n_ir = 0;                 // refinement steps per solve with the FP32 factor
   DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
   DBuf<int32_t> piv_fronts;     // per level: small pivot blocks, then cluster-sized ones
@@ -270,6 +282,12 @@ void launch_factor(Problem& P, double sigma, int precision);
 // LDL^T of K - mu M in FP64 with pivots of either sign (the undamped
 // pencil's spectrum slicing): status->neg_pivots counts the negative ones
 void launch_factor_gep(Problem& P, double mu);
+// complex symmetric LDL^T of Q(sr + i si) (FP64 complex)
+void launch_factor_complex(Problem& P, double sr, double si);
+// complex FB solve in place on xn (N complex, interleaved, ND order); with vu
+// the operator outputs of the complex shift: r_u = -Re x, r_l = Re(-s x) + v_u
+void launch_fb_complex(Problem& P, void* xn, double sr, double si, const double* vu, double* ru,
+                       double* rl);
 // buffers and tensor-core plan of a precision, on first use (host work and
 // allocations that rigaqep_factor keeps outside its timed region)
 void prepare_factor(Problem& P, int precision);
@@ -296,6 +314,9 @@ void launch_fb(Problem& P, double* xn, double sigma, const double* vu, double* r
 void launch_gather(const int32_t* idx, const double* src, double* dst, int64_t n, int32_t ld_in,
                    int32_t ncol, cudaStream_t s);
 void launch_scatter(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);
+// the same for complex vectors (n pairs re, im)
+void launch_gather2(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);
+void launch_scatter2(const int32_t* idx, const double* src, double* dst, int64_t n, cudaStream_t s);
 // Krylov pieces
 void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
               double* eta, int* n_conv);

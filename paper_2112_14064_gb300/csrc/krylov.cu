@@ -20,6 +20,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <complex>
+
 #include "internal.h"
 #include "tma.cuh"
 
@@ -63,6 +65,40 @@ __device__ __forceinline__ Sell sell_slice(const int32_t* off, int64_t ns, int64
     q.wd = (off[sl + 1] - q.o0) >> 5;
   }
   return q;
+}
+
+// Complex shift s = s_r + i s_i: the right-hand side y = s M v_u + C v_u +
+// M v_l of the operator is complex, y = (M w + C v_u) + i s_i (M v_u) with
+// w = s_r v_u + v_l (k_scale); written interleaved (re, im) for the complex
+// FB solve.
+__global__ void __launch_bounds__(kSellBlock) k_spmv_op_c(
+    const int32_t* off, int64_t ns, const int32_t* col, const double* Ms, const double* Cs,
+    const double* vu, const double* w, double si, double* y, int64_t N) {
+  pdl_trigger();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = warp % kSplit;
+  const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
+  const Sell q = sell_slice(off, ns, r);
+  const int64_t e0 = q.o0 + lane;
+  pdl_wait();
+  double acc = 0.0, acm = 0.0;
+#pragma unroll 2
+  for (int k = sub; k < q.wd; k += kSplit) {
+    const int64_t e = e0 + 32 * (int64_t)k;
+    const int32_t c = col[e];
+    const double m = Ms[e], u = vu[c];
+    acc = fma(m, w[c], acc);
+    acc = fma(Cs[e], u, acc);
+    acm = fma(m, u, acm);
+  }
+  __shared__ double red[kSellBlock / 32][32];
+  __shared__ double red2[kSellBlock / 32][32];
+  red[warp][lane] = acc;
+  red2[warp][lane] = acm;
+  __syncthreads();
+  if (sub == 0 && r < N) {
+    y[2 * r] = sell_combine(red, warp, lane);
+    y[2 * r + 1] = si * sell_combine(red2, warp, lane);
+  }
 }
 
 // y_i = sum_q M_iq w_q + C_iq vu_q with w = s vu + vl (formed by k_scale when
@@ -675,6 +711,7 @@ struct Work {
   // FB outputs r_u = -fb_uscale x, r_l = -fb_sigma x + v_u: the QEP operator
   // (sigma, vscale), or r_l = x, r_u = 0 for the undamped pencil (-1, 0)
   double fb_sigma = 0.0, fb_uscale = 1.0;
+  double shift_i = 0.0;   // imaginary part of a complex shift (0: real operator)
   int64_t n_apply = 0, n_spmv = 0, n_vv = 0;
   // FB timing: event pairs around every FB solve of one restart cycle
   std::vector<cudaEvent_t> ev;
@@ -733,14 +770,25 @@ struct Work {
     double* v = col(j);
     double* r = col(j + 1);
     const int64_t ns = (N + 31) / 32;
-    launch_pdl(k_spmv_op, dim3((unsigned)((ns + kSlicesPerBlock - 1) / kSlicesPerBlock)),
-               dim3(kSellBlock), 0, s, P.sell_off.p,
-               ns, P.sell_col.p, P.sell_M.p, P.sell_C.p, (const double*)v, (const double*)P.wop.p,
-               P.yop.p, N);
-    n_spmv += 3;
-    RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
-    launch_fb(P, P.yop.p, fb_sigma, v, r, r + Np, fb_uscale);
-    RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+    if (shift_i != 0.0) {
+      // complex shift: Re((A - s B)^{-1} B v) through the complex factor
+      launch_pdl(k_spmv_op_c, dim3((unsigned)((ns + kSlicesPerBlock - 1) / kSlicesPerBlock)),
+                 dim3(kSellBlock), 0, s, P.sell_off.p, ns, P.sell_col.p, P.sell_M.p, P.sell_C.p,
+                 (const double*)v, (const double*)P.wop.p, shift_i, (double*)P.cx.y.p, N);
+      n_spmv += 4;
+      RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+      launch_fb_complex(P, P.cx.y.p, sigma, shift_i, v, r, r + Np);
+      RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+    } else {
+      launch_pdl(k_spmv_op, dim3((unsigned)((ns + kSlicesPerBlock - 1) / kSlicesPerBlock)),
+                 dim3(kSellBlock), 0, s, P.sell_off.p,
+                 ns, P.sell_col.p, P.sell_M.p, P.sell_C.p, (const double*)v, (const double*)P.wop.p,
+                 P.yop.p, N);
+      n_spmv += 3;
+      RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+      launch_fb(P, P.yop.p, fb_sigma, v, r, r + Np, fb_uscale);
+      RQ_CUDA(cudaEventRecord(ev[ev_used++], s));
+    }
     ++n_apply;
     for (int pass = 0; pass < 2; ++pass) {
       dots(j, r, r + Np);   // V_u^T r_u + W^T r_l
@@ -769,6 +817,7 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
   W.fb_sigma = E.gep ? -1.0 : sigma;
   W.fb_uscale = E.gep ? 0.0 : E.vscale;
   if (E.gep) W.sigma = 0.0;   // w = 0 * v_u + v_l: the operator input is v_l alone
+  W.shift_i = E.cplx ? E.shift_i : 0.0;
   W.fb_events(m + 1);
   RQ_CUDA(cudaEventCreate(&W.rz[0]));
   RQ_CUDA(cudaEventCreate(&W.rz[1]));
@@ -836,8 +885,10 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
+    // complex shift: the Ritz values theta of the real operator map to the
+    // eigenvalues through a quadratic (eigs_run); the step reports 1 / theta
     launch_ritz(P.H.p, Hn.p, Qb.p, P.Y.p, P.ritz.p, m, nks, kwant, it >= max_restarts ? 1 : 2,
-                lock, sigma, tol, E.vscale, s);
+                lock, E.cplx ? 0.0 : sigma, tol, E.cplx ? 1.0 : E.vscale, s);
     RQ_CUDA(cudaEventRecord(W.rz[1], s));
     ++P.launches;
     RQ_CUDA(cudaMemcpyAsync(&h_out, P.ritz.p, sizeof(RitzOut), cudaMemcpyDeviceToHost, s));
@@ -926,6 +977,111 @@ void make_tmap_f64(CUtensorMap* map, const double* base, uint64_t rows, uint64_t
   if (r != CUDA_SUCCESS) throw Error(RIGAQEP_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
 
+// Complex shift s (Section 4.1.1 allows s in C): the Krylov iteration ran on
+// the real operator R = Re((A - s B)^{-1} B) = ((A - s B)^{-1} + (A - conj(s)
+// B)^{-1}) B / 2, whose eigenvalue for an eigenpair (lambda, z) of the pencil
+// is psi = (1/(lambda - s) + 1/(lambda - conj s)) / 2 = (lambda - a) /
+// ((lambda - s)(lambda - conj s)), a = Re s.  Each converged psi gives two
+// candidate eigenvalues, the roots of psi l^2 - (2 a psi + 1) l + psi |s|^2 +
+// a = 0; the eigenvector x = V_u y decides between them (the root with the
+// smaller QEP backward error).  The neig eigenvalues nearest s are returned.
+void finish_complex(Problem& P, const EigsParams& E, double* lambda, double* X, double* eta,
+                    int* n_conv) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int m = E.m, nc = E.ncand, neig = E.neig;
+  const int64_t N = L.N, ld = basis_ld(L.N);
+  const RitzOut& h = P.cand;
+  const std::complex<double> sh(E.shift, E.shift_i);
+  const double a = E.shift, s2 = std::norm(sh);
+  std::vector<double> r1(2 * (size_t)nc), r2(2 * (size_t)nc);
+  for (int i = 0; i < nc; ++i) {
+    const std::complex<double> psi = 1.0 / std::complex<double>(h.lam[2 * i], h.lam[2 * i + 1]);
+    const std::complex<double> qa = psi, qb = -(2.0 * a * psi + 1.0), qc = psi * s2 + a;
+    const std::complex<double> d = std::sqrt(qb * qb - 4.0 * qa * qc);
+    const std::complex<double> x1 = (-qb + d) / (2.0 * qa), x2 = (-qb - d) / (2.0 * qa);
+    r1[2 * i] = x1.real();
+    r1[2 * i + 1] = x1.imag();
+    r2[2 * i] = x2.real();
+    r2[2 * i + 1] = x2.imag();
+  }
+  DBuf<double> Xa, l1, l2, e1, e2, stats;
+  Xa.alloc(2 * (size_t)N * nc);
+  {
+    size_t smem = sizeof(double) * 2 * (size_t)m * nc;
+    smem_at_least((const void*)k_eigvec, smem);
+    k_eigvec<<<(unsigned)((N + 127) / 128), 128, smem, s>>>(P.V.p, ld, m, P.Y.p, nc, P.perm.p,
+                                                           Xa.p, N);
+    RQ_CUDA(cudaGetLastError());
+  }
+  stats.alloc(4 * (size_t)nc);
+  k_colstats<<<nc, 1024, 0, s>>>(Xa.p, N, stats.p);
+  RQ_CUDA(cudaGetLastError());
+  k_colnormalise<<<dim3((unsigned)((N + 255) / 256), nc), 256, 0, s>>>(Xa.p, N, stats.p);
+  RQ_CUDA(cudaGetLastError());
+  l1.upload(r1, s);
+  l2.upload(r2, s);
+  e1.alloc(nc);
+  e2.alloc(nc);
+  const int qb = 2 * P.nsm;
+  for (int pass = 0; pass < 2; ++pass) {
+    k_qres<<<dim3(qb, nc), 256, 0, s>>>(P.rowptr.p, P.col.p, P.K.p, P.M.p, P.C.p, Xa.p,
+                                       pass ? l2.p : l1.p, N, P.part.p, 1.0);
+    RQ_CUDA(cudaGetLastError());
+    k_eta<<<1, 128, 0, s>>>(P.part.p, qb, pass ? l2.p : l1.p, P.info.norm_K, P.info.norm_M,
+                            P.info.norm_C, pass ? e2.p : e1.p, nc);
+    RQ_CUDA(cudaGetLastError());
+  }
+  P.launches += 7;
+  std::vector<double> h1(nc), h2(nc);
+  RQ_CUDA(cudaMemcpyAsync(h1.data(), e1.p, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaMemcpyAsync(h2.data(), e2.p, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  std::vector<std::complex<double>> lam(nc);
+  std::vector<double> et(nc);
+  for (int i = 0; i < nc; ++i) {
+    const bool first = h1[i] <= h2[i];
+    lam[i] = first ? std::complex<double>(r1[2 * i], r1[2 * i + 1])
+                   : std::complex<double>(r2[2 * i], r2[2 * i + 1]);
+    et[i] = first ? h1[i] : h2[i];
+  }
+  std::vector<int> order(nc);
+  for (int i = 0; i < nc; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const double dx = std::abs(lam[x] - sh), dy = std::abs(lam[y] - sh);
+    if (dx != dy) return dx < dy;
+    return lam[x].imag() > lam[y].imag();
+  });
+  std::vector<double> lsel(2 * (size_t)neig), esel(neig);
+  int conv = 0;
+  for (int q = 0; q < neig; ++q) {
+    const int i = order[q];
+    lsel[2 * q] = lam[i].real();
+    lsel[2 * q + 1] = lam[i].imag();
+    esel[q] = et[i];
+    conv += h.est[i] <= E.tol ? 1 : 0;
+    RQ_CUDA(cudaMemcpyAsync(X + 2 * N * (int64_t)q, Xa.p + 2 * N * (int64_t)i,
+                            sizeof(double) * 2 * N, cudaMemcpyDeviceToDevice, s));
+  }
+  RQ_CUDA(cudaMemcpyAsync(lambda, lsel.data(), sizeof(double) * 2 * neig, cudaMemcpyHostToDevice, s));
+  RQ_CUDA(cudaMemcpyAsync(eta, esel.data(), sizeof(double) * neig, cudaMemcpyHostToDevice, s));
+  RQ_CUDA(cudaEventRecord(P.ev1, s));
+  DevStatus dst{};
+  RQ_CUDA(cudaMemcpyAsync(&dst, P.status.p, sizeof(dst), cudaMemcpyDeviceToHost, s));
+  RQ_CUDA(cudaStreamSynchronize(s));
+  if (dst.internal)
+    throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait for a TMA copy of the basis ran out");
+  if (dst.timeout)
+    throw Error(RIGAQEP_ERR_TIMEOUT, "a bounded wait between the FB work items ran out");
+  float ms = 0.f;
+  RQ_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+  P.info.eigs_ms = ms;
+  P.info.n_launches = P.launches;
+  P.info.certified = 0;   // no distance certificate for a complex shift
+  P.info.cert_margin = -1.0;
+  *n_conv = conv;
+}
+
 void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda, double* X,
               double* eta, int* n_conv) {
   Plan& L = P.plan;
@@ -945,6 +1101,10 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   } else {
     P.cand_valid = false;
     krylov_schur(P, E, v1);
+  }
+  if (E.cplx) {
+    finish_complex(P, E, lambda, X, eta, n_conv);
+    return;
   }
   const RitzOut& h_out = P.cand;
   // the last Ritz step wrote the eigenvectors of H for the candidate values

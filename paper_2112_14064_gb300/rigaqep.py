@@ -27,6 +27,7 @@ EXPORTS = [
     "rigaqep_symbolic_counts",
     "rigaqep_symbolic_destroy", "rigaqep_last_error", "rigaqep_destroy", "rigaqep_batch_eigs",
     "rigaqep_front_gemm", "rigaqep_set_wait_limit", "rigaqep_inertia", "rigaqep_eigs_undamped",
+    "rigaqep_factor_complex", "rigaqep_solve_complex",
 ]
 
 
@@ -49,7 +50,7 @@ class EigsOpts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("shift_mode", ctypes.c_int32),
                 ("shift", ctypes.c_double), ("ncand", ctypes.c_int32),
-                ("scaling", ctypes.c_int32)]
+                ("scaling", ctypes.c_int32), ("shift_imag", ctypes.c_double)]
 
 
 class BatchJob(ctypes.Structure):
@@ -113,6 +114,8 @@ def load():
         "rigaqep_batch_eigs": [ctypes.POINTER(P), I32, ctypes.POINTER(BatchJob), I32, I32],
         "rigaqep_front_gemm": [I32, I32, I32, I32, P, P, P, V],
         "rigaqep_inertia": [P, D, ctypes.POINTER(I64)],
+        "rigaqep_factor_complex": [P, D, D],
+        "rigaqep_solve_complex": [P, P, P, I32],
         "rigaqep_eigs_undamped": [P, D, D, I32, ctypes.POINTER(EigsOpts), P, P, P, P,
                                   ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)],
     }
@@ -293,6 +296,20 @@ class Problem:
                                                      _ptr(out)))
         return torch.view_as_complex(out)
 
+    # -- complex shift
+    def factor_complex(self, s):
+        """Complex symmetric LDL^T of Q(s) for a complex shift s."""
+        _check(self.lib.rigaqep_factor_complex(self._h, float(s.real), float(s.imag)))
+        return self
+
+    def solve_complex(self, b):
+        """x = Q(s)^{-1} b with the complex factor; b: complex128 CUDA tensor (N,)."""
+        torch = self._torch
+        br = torch.view_as_real(b.contiguous().to(torch.complex128)).contiguous()
+        x = torch.empty_like(br)
+        _check(self.lib.rigaqep_solve_complex(self._h, _ptr(br), _ptr(x), 1))
+        return torch.view_as_complex(x)
+
     # -- undamped pencil K x = mu M x
     def inertia(self, mu):
         """Number of eigenvalues of K x = mu' M x below mu (Sylvester)."""
@@ -351,10 +368,15 @@ class Problem:
 def eigs_opts(neig, m=None, tol=1e-10, max_restarts=1000, seed=1, shift=None, ncand=None,
               precision=FP64, scaling=False):
     """rigaqep_eigs_opts with the defaults of Problem.eigs."""
+    if isinstance(shift, complex):   # complex shift: the neig eigenvalues nearest it
+        nc = 2 * neig + 4 if ncand is None else ncand
+        m = m or min(96, 2 * nc + 20)
+        return EigsOpts(m, max_restarts, tol, seed, precision, 2, shift.real, nc,
+                        1 if scaling else 0, shift.imag)
     nc = neig if ncand is None else ncand
     m = m or min(96, 2 * nc + 20)
     return EigsOpts(m, max_restarts, tol, seed, precision, 0 if shift is None else 1,
-                    0.0 if shift is None else float(shift), nc, 1 if scaling else 0)
+                    0.0 if shift is None else float(shift), nc, 1 if scaling else 0, 0.0)
 
 
 def batch_eigs(problems, jobs, nthreads=0, raise_on_error=True):

@@ -522,6 +522,31 @@ def test_lanczos_slice_against_dense():
     assert not cert
 
 
+@pytest.mark.parametrize("shift", [1j * np.sqrt(300.0), 0.2 + 1j * np.sqrt(120.0)])
+def test_complex_shift_against_dense(shift):
+    """Section 4.1.1's complex shift: the complex symmetric LDL^T solves
+    Q(s) x = b, and the real-operator Krylov-Schur with the quadratic
+    back-mapping returns the eigenvalues of the dense pencil nearest s
+    (LAPACK's QZ, multiset 1e-10)."""
+    c = workloads.CONFIGS["tiny"]
+    A = assemble(c["ne"], c["p"], c["block"], workloads.sigma_e(c))
+    sym = symbolic(A.n1, A.space.c0_dofs, c["p"], A.indptr, A.indices)
+    Q = (A.K + shift * A.C + shift * shift * A.M).tocsr()
+    F = factorize(sym, Q)
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(A.N) + 1j * rng.standard_normal(A.N)
+    assert np.linalg.norm(Q @ F.solve(b) - b) <= 1e-13 * np.linalg.norm(b)
+    r = qep.eigs_complex_shift(A.K, A.C, A.M, shift, 10, 40, F.solve,
+                               workloads.start_vector(1, 2 * A.N))
+    N = A.N
+    K, C, M = A.K.toarray(), A.C.toarray(), A.M.toarray()
+    I, Z = np.eye(N), np.zeros((N, N))
+    w = sla.eig(np.block([[Z, I], [-K, -C]]), np.block([[I, Z], [Z, M]]), right=False)
+    ref = w[np.lexsort((-w.imag, np.abs(w - shift)))][:10]
+    assert multiset_max_rel(ref, r.lam) < 1e-10
+    assert np.all(r.eta <= 1e-10)
+
+
 # ---------------------------------------------------------------- gradient
 def test_gradient_sum_rule_proportional():
     """P-2: with C = cM, sum_e dlambda/dsigma_e = -lambda / (2 lambda + c),
