@@ -110,14 +110,14 @@ class Clocks(threading.Thread):
 
 
 def fb_source_hash():
-    """sha256 of the FB kernels' source text (the two sweep kernels and their
-    launcher in factor.cu): the committed DRAM counters stay valid while it
+    """sha256 of the FB kernels' source text (the sweep kernels and their
+    launchers in factor.cu): the committed DRAM counters stay valid while it
     is unchanged."""
     src = open(os.path.join(ROOT, "paper_2112_14064_gb300", "csrc", "factor.cu")).read()
     a = src.index("// Forward sweep, one work item")
     b = src.index("__global__ void k_gather")
-    c = src.index("void launch_fb(")
-    d = src.index("\n}\n", c) + 3
+    c = src.index("void launch_fb_t(")
+    d = src.index("\n}\n", src.index("void launch_fb(")) + 3
     return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()
 
 
@@ -432,6 +432,57 @@ def iga_leg(inf_riga, riga_ms, flush, stream, barrier):
                 "step_time": ent["ms_per_step"] / r["ms_per_step"]}}
 
 
+def variants_leg(flush, stream, barrier):
+    """The headline mesh (p = 3, 256 x 256, blocks of 16) solved two other
+    ways: the 20 pairs nearest the complex shift i sqrt(500) through the
+    complex symmetric factor of Q(s) and the real operator Re((A - sB)^-1 B)
+    (one step = analyze + complex factor + eigs), and every undamped
+    eigenvalue mu = omega^2 of K x = mu M x in [500, 1000) with its count
+    certified by two inertias (one step = analyze + two indefinite factors +
+    shift-invert Lanczos)."""
+    import torch
+    from paper_2112_14064_gb300 import rigaqep, workloads
+    cfg = workloads.CONFIGS[WORKLOAD]
+    sig_d = torch.from_numpy(workloads.sigma_e(cfg)).cuda()
+    shift = 1j * np.sqrt(500.0)
+
+    def cstep():
+        pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
+        lam, X, eta, nconv, st = pr.eigs(cfg["neig"], 1.0, m=96, shift=shift, seed=1,
+                                         raise_on_noconv=False)
+        inf = pr.info()
+        pr.close()
+        return lam, eta, inf
+
+    def ustep():
+        pr = rigaqep.Problem(cfg["ne"], cfg["p"], cfg["block"], sig_d).analyze()
+        out = pr.eigs_undamped(500.0, 1000.0, seed=1)
+        pr.close()
+        return out
+
+    cstep()
+    barrier()
+    times, outs = _timed(cstep, 2, flush, stream)
+    lam, eta, inf = outs[-1]
+    good = sum(int((e <= ETA_MAX).sum().item()) for _, e, _ in outs)
+    cx = {"shift": "i*sqrt(500)", "neig": cfg["neig"], "value": 1e3 * good / sum(times),
+          "unit": UNIT, "ms_per_step": sum(times) / len(times), "steps": len(times),
+          "factor_ms": inf["factor_ms"], "fb_ms": inf["fb_ms"], "n_apply": inf["n_apply"],
+          "eigs_ms": inf["eigs_ms"], "max_eta": float(eta.max().item()),
+          "max_rel_imag_offset": float(np.max(np.abs(lam.cpu().numpy().imag - np.sqrt(500.0)))
+                                       / np.sqrt(500.0))}
+    ustep()
+    barrier()
+    times, outs = _timed(ustep, 2, flush, stream)
+    mu, X, res, count, cert = outs[-1]
+    good = sum(int((r <= ETA_MAX).sum().item()) if c == 1 else 0 for _, _, r, _, c in outs)
+    ud = {"interval": [500.0, 1000.0], "count": int(count), "certified": int(cert),
+          "value": 1e3 * good / sum(times), "unit": "undamped eigenpairs/s",
+          "ms_per_step": sum(times) / len(times), "steps": len(times),
+          "max_residual": float(res.max().item()) if len(mu) else 0.0}
+    return {"workload": WORKLOAD, "complex_shift": cx, "undamped_slice": ud}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -551,6 +602,7 @@ def run_ours(args):
         legs["workload_mixed"] = workload_mixed_leg(flush, stream, barrier)
         legs["workload_grad"] = workload_grad_leg(flush, stream, barrier)
         legs["iga"] = iga_leg(infos[-1], total_ms / args.steps, flush, stream, barrier)
+        legs["variants"] = variants_leg(flush, stream, barrier)
 
     # max over ranks
     t = torch.tensor([total_ms, float(sum(e2e_ms))], dtype=torch.float64, device=dev)

@@ -642,6 +642,74 @@ __global__ void k_gden_final(const double* part, int nblk, int neig, double* den
 
 // G[t, e] = -l_t q_{t,e} / den_t with q = x_e^T (mx (x) my) x_e over the
 // element's (p+1)^2 functions (Dirichlet functions carry no DOF)
+// k_grad for a fixed p + 1 = NP: the element form x_e^T (my (x) mx) x_e as
+// sum_{b,d} my[b,d] (X^T (mx X))[b,d] (X the NP x NP block of x on the
+// element, complex, unconjugated) in registers: 6 NP^3 FMAs instead of the
+// NP^4 of the direct double sum.
+template <int NP>
+__global__ void __launch_bounds__(128) k_grad_p(const double* X, const double* lam,
+                                                const double* den, const double* m1,
+                                                const int* first_fn, int ne, int n1, int64_t N,
+                                                int neig, double* G) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ne2 = (int64_t)ne * ne;
+  if (tid >= ne2 * neig) return;
+  const int t = (int)(tid / ne2);
+  const int64_t e = tid % ne2;
+  const int ex = (int)(e % ne), ey = (int)(e / ne);
+  const double* x = X + 2 * N * t;
+  double xr[NP][NP], xi[NP][NP];
+  const int fx = first_fn[ex] - 1, fy = first_fn[ey] - 1;
+#pragma unroll
+  for (int a = 0; a < NP; ++a)
+#pragma unroll
+    for (int b = 0; b < NP; ++b) {
+      const int dx = fx + a, dy = fy + b;
+      const bool in = dx >= 0 && dx < n1 && dy >= 0 && dy < n1;
+      const int64_t d = in ? dx + (int64_t)n1 * dy : 0;
+      xr[a][b] = in ? __ldg(x + 2 * d) : 0.0;
+      xi[a][b] = in ? __ldg(x + 2 * d + 1) : 0.0;
+    }
+  const double* mx = m1 + (int64_t)ex * NP * NP;
+  const double* my = m1 + (int64_t)ey * NP * NP;
+  double qr = 0.0, qi = 0.0;
+#pragma unroll
+  for (int d = 0; d < NP; ++d) {
+    // column d of T = mx X
+    double tr[NP], ti[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      double sr = 0.0, si = 0.0;
+#pragma unroll
+      for (int c = 0; c < NP; ++c) {
+        const double m = __ldg(mx + a * NP + c);
+        sr = fma(m, xr[c][d], sr);
+        si = fma(m, xi[c][d], si);
+      }
+      tr[a] = sr;
+      ti[a] = si;
+    }
+#pragma unroll
+    for (int b = 0; b < NP; ++b) {
+      double wr = 0.0, wi = 0.0;   // W[b][d] = sum_a X[a][b] T[a][d]
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        wr = fma(xr[a][b], tr[a], fma(-xi[a][b], ti[a], wr));
+        wi = fma(xr[a][b], ti[a], fma(xi[a][b], tr[a], wi));
+      }
+      const double mbd = __ldg(my + b * NP + d);
+      qr = fma(mbd, wr, qr);
+      qi = fma(mbd, wi, qi);
+    }
+  }
+  const double lr = lam[2 * t], li = lam[2 * t + 1];
+  const double nr = -(lr * qr - li * qi), ni = -(lr * qi + li * qr);
+  const double dr = den[2 * t], di = den[2 * t + 1];
+  const double dd = dr * dr + di * di;
+  G[2 * (e + ne2 * t)] = (nr * dr + ni * di) / dd;
+  G[2 * (e + ne2 * t) + 1] = (ni * dr - nr * di) / dd;
+}
+
 __global__ void k_grad(const double* X, const double* lam, const double* den, const double* m1,
                        const int* first_fn, int ne, int p, int n1, int64_t N, int neig,
                        double* G) {
@@ -1233,6 +1301,26 @@ void eigs_run(Problem& P, const EigsParams& E, const double* v1, double* lambda,
   *n_conv = sel_conv;
 }
 
+namespace {
+// the element gradients of every pair (templated kernels for p = 2..5)
+void launch_grad(Problem& P, int neig, const double* lambda, const double* X, const double* den,
+                 double* G) {
+  Plan& L = P.plan;
+  cudaStream_t s = P.stream;
+  const int64_t tot = (int64_t)L.ne * L.ne * neig;
+  const unsigned g = (unsigned)((tot + 127) / 128);
+  switch (L.p + 1) {
+    case 3: k_grad_p<3><<<g, 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne, L.n1, L.N, neig, G); break;
+    case 4: k_grad_p<4><<<g, 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne, L.n1, L.N, neig, G); break;
+    case 5: k_grad_p<5><<<g, 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne, L.n1, L.N, neig, G); break;
+    case 6: k_grad_p<6><<<g, 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne, L.n1, L.N, neig, G); break;
+    default:
+      k_grad<<<g, 128, 0, s>>>(X, lambda, den, P.m1.p, P.first_fn.p, L.ne, L.p, L.n1, L.N, neig, G);
+  }
+  RQ_CUDA(cudaGetLastError());
+}
+}  // namespace
+
 void grad_run(Problem& P, int neig, const double* lambda, const double* X, double* G) {
   Plan& L = P.plan;
   cudaStream_t s = P.stream;
@@ -1246,10 +1334,7 @@ void grad_run(Problem& P, int neig, const double* lambda, const double* X, doubl
   RQ_CUDA(cudaGetLastError());
   k_gden_final<<<1, 64, 0, s>>>(part.p, nb, neig, den.p);
   RQ_CUDA(cudaGetLastError());
-  int64_t tot = (int64_t)L.ne * L.ne * neig;
-  k_grad<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(X, lambda, den.p, P.m1.p, P.first_fn.p, L.ne,
-                                                       L.p, L.n1, N, neig, G);
-  RQ_CUDA(cudaGetLastError());
+  launch_grad(P, neig, lambda, X, den.p, G);
   RQ_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -209,6 +209,22 @@ def test_gradient_matches_oracle(rq):
     pr.close()
 
 
+@pytest.mark.parametrize("p,ne,block", [(2, 12, 0), (3, 12, 4), (4, 10, 5), (5, 8, 4),
+                                         (6, 8, 4), (7, 8, 8)])
+def test_gradient_every_degree(rq, p, ne, block):
+    """Element gradients at each degree (register kernels for p = 2..5, the
+    generic one otherwise) against the oracle's on the same eigenpairs."""
+    c = _cfg("tiny", p=p, ne=ne, block=block, neig=6, m=30)
+    A, _ = _oracle(c)
+    pr = _problem(rq, c)
+    lam, X, *_ = pr.eigs(c["neig"], c["shift"], m=c["m"], seed=1)
+    G = pr.grad_damping(lam, X).cpu().numpy()
+    ref = damping_gradient(c["ne"], c["p"], c["block"], lam.cpu().numpy(), X.cpu().numpy(),
+                           A.C, A.M)
+    assert np.abs(G - ref).max() <= 1e-10 * np.abs(ref).max()
+    pr.close()
+
+
 def test_gradient_sum_rule_constant_damping(rq):
     cst = 0.4
     c = _cfg("tiny", sigma_law="constant", value=cst)
