@@ -520,6 +520,32 @@ FBArgs<float> fb_args<float>(Problem& P) {
                        P.zbuf32.p, (const int4*)P.fwd_items.p, (const int4*)P.bwd_items.p};
 }
 
+// Children's update entries of one front position, gathered in list
+// (child) order onto acc: the list is [g0, g1) of gsrc, and its first two
+// source indices sa, sb (-1 past the end) are static, so callers load them
+// before they wait for the vectors; then both values load together.
+struct GatherPos {
+  int g0, g1, sa, sb;
+};
+template <class T>
+__device__ __forceinline__ GatherPos gather_plan(const FBArgs<T>& A, int gpos) {
+  GatherPos q;
+  q.g0 = A.gptr[gpos];
+  q.g1 = A.gptr[gpos + 1];
+  q.sa = q.g0 < q.g1 ? A.gsrc[q.g0] : -1;
+  q.sb = q.g0 + 1 < q.g1 ? A.gsrc[q.g0 + 1] : -1;
+  return q;
+}
+template <class T>
+__device__ __forceinline__ T gather_sum(const FBArgs<T>& A, T acc, const GatherPos& q) {
+  const T va = q.sa >= 0 ? __ldcg(A.yvec + q.sa) : T(0);
+  const T vb = q.sb >= 0 ? __ldcg(A.yvec + q.sb) : T(0);
+  if (q.sa >= 0) acc += va;
+  if (q.sb >= 0) acc += vb;
+  for (int g = q.g0 + 2; g < q.g1; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
+  return acc;
+}
+
 // Forward sweep, one work item = up to 32 RC consecutive rows of one front's
 // panel P = [inv(L11); W], W = L21 inv(L11):
 //   xg  = x_s + (children's update vectors at the pivot rows)
@@ -562,27 +588,25 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   T v[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) v[t] = pr[F * min(cb + t, cl)];
+  // the gather lists are static too: this thread's first pivot position and
+  // its update row (if any) are planned before the wait
+  const bool kids = i2.z != 0;   // the front has children's update entries
+  const bool yrow = threadIdx.x < nr && r0 + (int)threadIdx.x >= k;
+  GatherPos gp{0, 0, -1, -1}, gy{0, 0, -1, -1};
+  if (kids && (int)threadIdx.x < k) gp = gather_plan(A, gbase + threadIdx.x);
+  if (kids && yrow) gy = gather_plan(A, gbase + r0 + threadIdx.x);
   // the panels and item descriptors were written before this sweep; the
   // vectors below come from the previous kernels of the stream
   pdl_wait();
   // right-hand side plus the children's update vectors, summed per front
   // position in child order (deterministic, no write conflicts)
-  const bool kids = i2.z != 0;   // the front has children's update entries
-  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+  if ((int)threadIdx.x < k) xg[threadIdx.x] = gather_sum(A, __ldcg(xin + a + threadIdx.x), gp);
+  for (int t = threadIdx.x + blockDim.x; t < k; t += blockDim.x) {
     T acc = __ldcg(xin + a + t);
-    if (kids)
-      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g)
-        acc += __ldcg(A.yvec + A.gsrc[g]);
+    if (kids) acc = gather_sum(A, acc, gather_plan(A, gbase + t));
     xg[t] = acc;
   }
-  if (threadIdx.x < nr && r0 + (int)threadIdx.x >= k) {
-    int pos = r0 + threadIdx.x;
-    T acc = T(0);
-    if (kids)
-      for (int g = A.gptr[gbase + pos]; g < A.gptr[gbase + pos + 1]; ++g)
-        acc += __ldcg(A.yvec + A.gsrc[g]);
-    yadd[threadIdx.x] = acc;
-  }
+  if (yrow) yadd[threadIdx.x] = gather_sum(A, T(0), gy);
   __syncthreads();
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   for (int c = cb;;) {
@@ -676,11 +700,13 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
   // the first block's panel entries were written before this sweep: load them
   // before waiting for the previous kernels (zbuf and x come from those)
   T v[32];
+  int xi0 = -1;   // first block: solution index of an update row (static)
   {
     const int64_t i = c0 + 32 * warp + lane;
     const T* pr = P + (i < F ? i : F - 1);
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = pr[F * min(q, nc - 1)];
+    if (i < F && i >= k) xi0 = st[i - k];
   }
   pdl_wait();
   bool first = true;
@@ -688,7 +714,7 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
     int64_t i = r0 + lane;
     int64_t ic = i < F ? i : F - 1;
     T g = T(0);
-    if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
+    if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + (first ? xi0 : st[i - k]));
     const T* pr = P + ic;
     if (!first) {
 #pragma unroll
@@ -842,51 +868,37 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[c][t] = pr[F * min(cb + 8 * c + t, cl)];
   const bool kids = i2.z != 0;
-  // this thread's gather positions (at most two before the wait)
+  // this thread's gather positions (at most two before the wait): the
+  // right-hand side and the first two source indices of each list
   T xr[2];
-  int g0[2], g1[2];
+  GatherPos gp[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int t = threadIdx.x + 256 * h;
     xr[h] = T(0);
-    g0[h] = g1[h] = 0;
+    gp[h] = GatherPos{0, 0, -1, -1};
     if (t < k) {
       xr[h] = __ldcg(xin + a + t);
-      if (kids) {
-        g0[h] = A.gptr[gbase + t];
-        g1[h] = A.gptr[gbase + t + 1];
-      }
+      if (kids) gp[h] = gather_plan(A, gbase + t);
     }
   }
-  int y0 = 0, y1 = 0;
   const bool yrow = threadIdx.x < nr && r0 + (int)threadIdx.x >= k;
-  if (yrow && kids) {
-    y0 = A.gptr[gbase + r0 + threadIdx.x];
-    y1 = A.gptr[gbase + r0 + threadIdx.x + 1];
-  }
+  GatherPos gy{0, 0, -1, -1};
+  if (yrow && kids) gy = gather_plan(A, gbase + r0 + threadIdx.x);
   // the children's update vectors are complete
   if (threadIdx.x == 0) dep_wait(D.kdone + s, D.epoch * (unsigned)D.kid_items[s], D.status);
   __syncthreads();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int t = threadIdx.x + 256 * h;
-    if (t < k) {
-      T acc = xr[h];
-      for (int g = g0[h]; g < g1[h]; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
-      xg[t] = acc;
-    }
+    if (t < k) xg[t] = gather_sum(A, xr[h], gp[h]);
   }
   for (int t = threadIdx.x + 512; t < k; t += blockDim.x) {
     T acc = __ldcg(xin + a + t);
-    if (kids)
-      for (int g = A.gptr[gbase + t]; g < A.gptr[gbase + t + 1]; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
+    if (kids) acc = gather_sum(A, acc, gather_plan(A, gbase + t));
     xg[t] = acc;
   }
-  if (yrow) {
-    T acc = T(0);
-    for (int g = y0; g < y1; ++g) acc += __ldcg(A.yvec + A.gsrc[g]);
-    yadd[threadIdx.x] = acc;
-  }
+  if (yrow) yadd[threadIdx.x] = gather_sum(A, T(0), gy);
   __syncthreads();
   T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   int c = cb;

@@ -664,20 +664,37 @@ __host__ __device__ inline size_t batch_bytes(int m) {
   return kReflOff + sizeof(Refl) * (size_t)kBulges * (size_t)(m + 4 * kBulges);
 }
 
+// The deflation point of the active window [lock, hi]: the largest
+// l in (lock, hi] whose subdiagonal entry is negligible against its two
+// diagonal neighbours (|T(l, l-1)| <= eps (|T(l-1, l-1)| + |T(l, l)|)), or
+// lock if there is none.  One subdiagonal entry per thread and a block
+// maximum: each test is four FP64 instructions, which a scan down the
+// window would chain once per row.  Returns the same value to every thread.
+__device__ int deflation_point(const Smem& S, int lock, int hi, double tn, int lane) {
+  __shared__ int wmax[NT / 32];
+  int best = lock;
+  for (int i = lock + 1 + lane; i <= hi; i += NT) {
+    double sc = fabs(TT(i - 1, i - 1)) + fabs(TT(i, i));
+    if (sc == 0.0) sc = tn;
+    if (fabs(TT(i, i - 1)) <= kEps * sc) best = i;   // i increases: the last hit is the largest
+  }
+  best = __reduce_max_sync(0xffffffffu, best);
+  if ((lane & 31) == 0) wmax[lane >> 5] = best;
+  __syncthreads();
+  int l = wmax[0];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) l = max(l, wmax[w]);
+  __syncthreads();
+  return l;
+}
+
 __device__ int francis(Smem& S, int m, int lane, int& sweeps, int lock, Queue& Q) {
   double tn = frob(S, m, lane);
   if (tn == 0.0) tn = 1.0;
   int hi = m - 1, its = 0, total = 0, status = 0;
   const int warp = lane >> 5, wl = lane & 31;
   while (hi >= lock) {
-    int l = hi;
-    while (l > lock) {
-      double sc = fabs(TT(l - 1, l - 1)) + fabs(TT(l, l));
-      if (sc == 0.0) sc = tn;
-      if (fabs(TT(l, l - 1)) <= kEps * sc) break;
-      --l;
-    }
-    __syncthreads();
+    const int l = hi > lock ? deflation_point(S, lock, hi, tn, lane) : lock;
     if (l > lock && lane == 0) TT(l, l - 1) = 0.0;
     __syncthreads();
     if (l == hi) { --hi; its = 0; continue; }
@@ -1175,13 +1192,22 @@ __device__ void ritz_main(const RitzArgs& R, Smem& S, Queue& Q, double* wbuf, in
   // ranks by |lambda - s| = 1/|theta|, Im lambda > 0 first on ties
   // (lambda - s = 1/theta, so Im lambda has the sign of -Im theta)
   // |lambda - s| = 1/|theta|: nearer means larger |theta|^2
+  // |theta|^2 of every position (S.v is free after the QR) and its class
+  // (Im theta < 0, = 0, > 0) in S.cflag (reset below); the comparisons are
+  // then integer ones: non-negative doubles order as their bit patterns
   for (int i = lane; i < m; i += NT) {
-    double ti = S.wr[i] * S.wr[i] + S.wi[i] * S.wi[i];
-    int ci = S.wi[i] < 0.0 ? 0 : (S.wi[i] == 0.0 ? 1 : 2);
+    S.v[i] = S.wr[i] * S.wr[i] + S.wi[i] * S.wi[i];
+    const long long b = __double_as_longlong(S.wi[i]);
+    S.cflag[i] = (b << 1) == 0 ? 1 : (b < 0 ? 0 : 2);
+  }
+  __syncthreads();
+  for (int i = lane; i < m; i += NT) {
+    const long long ti = __double_as_longlong(S.v[i]);
+    const int ci = S.cflag[i];
     int rk = 0;
     for (int q = 0; q < m; ++q) {
-      double tq = S.wr[q] * S.wr[q] + S.wi[q] * S.wi[q];
-      int cq = S.wi[q] < 0.0 ? 0 : (S.wi[q] == 0.0 ? 1 : 2);
+      const long long tq = __double_as_longlong(S.v[q]);
+      const int cq = S.cflag[q];
       if (tq > ti || (tq == ti && (cq < ci || (cq == ci && q < i)))) ++rk;
     }
     S.rank[i] = rk;
