@@ -595,6 +595,9 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   GatherPos gp{0, 0, -1, -1}, gy{0, 0, -1, -1};
   if (kids && (int)threadIdx.x < k) gp = gather_plan(A, gbase + threadIdx.x);
   if (kids && yrow) gy = gather_plan(A, gbase + r0 + threadIdx.x);
+  // this thread's pivot (if its row is one), needed after the reduction
+  const T dinv = (int)threadIdx.x < nr && r0 + (int)threadIdx.x < k ? A.Dinv[a + r0 + threadIdx.x]
+                                                                     : T(0);
   // the panels and item descriptors were written before this sweep; the
   // vectors below come from the previous kernels of the stream
   pdl_wait();
@@ -635,7 +638,7 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
     T dot = T(0);
 #pragma unroll
     for (int pp = 0; pp < NP; ++pp) dot += part[pp * RC + lrc][ll];
-    if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
+    if (i < k) A.zbuf[a + i] = dot * dinv;
     else A.yvec[i1.w + (i - k)] = yadd[l] - dot;
   }
   __syncthreads();
@@ -663,6 +666,17 @@ __global__ void __launch_bounds__(256) k_fb_fwd(FBArgs<T> A, int item_begin, con
 // Q x = y: real scalars r_u = -uscale x, r_l = -sigma x + v_u; complex shift
 // s = sigma + i sigma_i (the real part of the complex operator):
 // r_u = -Re x, r_l = Re(-s x) + v_u.
+// The same with v_u[cc] already loaded (vuc; real factors only).
+template <class T>
+__device__ __forceinline__ void op_out_v(T sum, double sigma, double uscale,
+                                         typename RealOf<T>::type vuc,
+                                         typename RealOf<T>::type* ru, typename RealOf<T>::type* rl,
+                                         int64_t cc) {
+  using R = typename RealOf<T>::type;
+  ru[cc] = (R)(uscale * (double)(-sum));
+  rl[cc] = (R)(sigma * (double)(-sum)) + vuc;
+}
+
 template <class T>
 __device__ __forceinline__ void op_out(T sum, double sigma, double sigma_i, double uscale,
                                        const typename RealOf<T>::type* vu,
@@ -709,6 +723,9 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
     if (i < F && i >= k) xi0 = st[i - k];
   }
   pdl_wait();
+  // this thread's entry of v_u, for r_l after the reduction
+  typename RealOf<T>::type vuc = 0;
+  if (ru && (int)threadIdx.x < nc) vuc = vu[a + c0 + threadIdx.x];
   bool first = true;
   for (int64_t r0 = c0 + 32 * warp; r0 < F; r0 += 32 * NW) {
     int64_t i = r0 + lane;
@@ -738,7 +755,11 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
     for (int w = 0; w < NW; ++w) sum += red[w][l];
     int cc = a + c0 + l;
     x[cc] = sum;
-    if (ru) op_out<T>(sum, sigma, sigma_i, uscale, vu, ru, rl, cc);
+    if constexpr (std::is_same<T, zd>::value) {
+      if (ru) op_out<T>(sum, sigma, sigma_i, uscale, vu, ru, rl, cc);
+    } else {
+      if (ru) op_out_v<T>(sum, sigma, uscale, vuc, ru, rl, cc);
+    }
   }
   __syncthreads();
 }
@@ -885,6 +906,8 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
   const bool yrow = threadIdx.x < nr && r0 + (int)threadIdx.x >= k;
   GatherPos gy{0, 0, -1, -1};
   if (yrow && kids) gy = gather_plan(A, gbase + r0 + threadIdx.x);
+  const T dinv = (int)threadIdx.x < nr && r0 + (int)threadIdx.x < k ? A.Dinv[a + r0 + threadIdx.x]
+                                                                     : T(0);
   // the children's update vectors are complete
   if (threadIdx.x == 0) dep_wait(D.kdone + s, D.epoch * (unsigned)D.kid_items[s], D.status);
   __syncthreads();
@@ -943,7 +966,7 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
     T dot = T(0);
 #pragma unroll
     for (int pp = 0; pp < NP; ++pp) dot += part[pp * RC + lrc][ll];
-    if (i < k) A.zbuf[a + i] = dot * A.Dinv[a + i];
+    if (i < k) A.zbuf[a + i] = dot * dinv;
     else A.yvec[i1.w + (i - k)] = yadd[l] - dot;
   }
   __syncthreads();
@@ -960,7 +983,6 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
                                                 typename RealOf<T>::type* ru,
                                                 typename RealOf<T>::type* rl, T* smem,
                                                 double uscale) {
-  const double sigma_i = 0.0;   // the dependency-driven sweeps serve the real factors
   constexpr int NW = 8;
   T(*tile)[32][33] = reinterpret_cast<T(*)[32][33]>(smem);
   __shared__ T gs[NW][32];
@@ -990,6 +1012,9 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
       else xi[b] = st[i - k];
     }
   }
+  // this thread's entry of v_u (written before the launch), for r_l
+  typename RealOf<T>::type vuc = 0;
+  if (ru && (int)threadIdx.x < nc) vuc = vu[a + c0 + threadIdx.x];
   const int pa = D.parent[s];
   if (threadIdx.x == 0 && pa >= 0)
     dep_wait(D.bdone + pa, D.epoch * (unsigned)D.bwd_items[pa], D.status);
@@ -1031,7 +1056,7 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     for (int w = 0; w < NW; ++w) sum += red[w][l];
     const int cc = a + c0 + l;
     x[cc] = sum;
-    if (ru) op_out<T>(sum, sigma, sigma_i, uscale, vu, ru, rl, cc);
+    if (ru) op_out_v<T>(sum, sigma, uscale, vuc, ru, rl, cc);
   }
   __syncthreads();
 }

@@ -206,12 +206,18 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
   double acc[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+  // this lane's entry of x for tile t (the next tile's load is issued a tile
+  // ahead, so that its latency overlaps the current tile's products)
+  auto xval = [&](int t) -> double {
+    const int64_t i = (int64_t)t * kTileRows + rs + lane;
+    return t < ntile ? (i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0)) : 0.0;
+  };
+  double x = xval(blockIdx.x);
   int it = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++it) {
     const int s = it & 1;
     const double* cur = s ? stage1 : stage0;
-    const int64_t i = (int64_t)t * kTileRows + rs + lane;
-    const double x = i < Np ? xa[i] : (i < rows ? xb[i - Np] : 0.0);
+    const double xn = xval(t + (int)gridDim.x);
     const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((it >> 1) & 1), kTmaWaitLimit));
     if (!ok) abort_flag = 1;
     if (abort_flag) break;
@@ -220,6 +226,7 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
     else if (g == 3) dots_acc<3>(acc, tile, x);
     else if (g == 2) dots_acc<2>(acc, tile, x);
     else if (g == 1) dots_acc<1>(acc, tile, x);
+    x = xn;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
     if (threadIdx.x == 0) {
