@@ -546,6 +546,54 @@ __device__ __forceinline__ T gather_sum(const FBArgs<T>& A, T acc, const GatherP
   return acc;
 }
 
+// Adds v[t] x[t] for t < nt (nt warp-uniform, at most 8; x in shared
+// memory, read only below nt) to the warp's partial sums.  In FP64 the
+// products past nt are not issued, since each FP64 warp instruction holds
+// the SM sub-partition's FP64 pipe for 64 cycles whatever its lanes do, and
+// one accumulator suffices, since a dependent FP64 FMA waits no longer than
+// that issue interval.  Other types keep four accumulators and zero weights.
+template <class T>
+__device__ __forceinline__ void chunk_acc(T (&s)[4], const T* v, const T* x, int nt) {
+  if constexpr (std::is_same<T, double>::value) {
+    double a = s[0];
+    if (nt >= 8) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) a = fma(v[t], x[t], a);
+    } else {
+      switch (nt) {
+        case 7: a = fma(v[6], x[6], a); [[fallthrough]];
+        case 6: a = fma(v[5], x[5], a); [[fallthrough]];
+        case 5: a = fma(v[4], x[4], a); [[fallthrough]];
+        case 4: a = fma(v[3], x[3], a); [[fallthrough]];
+        case 3: a = fma(v[2], x[2], a); [[fallthrough]];
+        case 2: a = fma(v[1], x[1], a); [[fallthrough]];
+        case 1: a = fma(v[0], x[0], a); [[fallthrough]];
+        default: break;
+      }
+    }
+    s[0] = a;
+  } else {
+    T w[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) w[t] = t < nt ? x[t] : T(0);
+    s[0] += v[0] * w[0];
+    s[1] += v[1] * w[1];
+    s[2] += v[2] * w[2];
+    s[3] += v[3] * w[3];
+    s[0] += v[4] * w[4];
+    s[1] += v[5] * w[5];
+    s[2] += v[6] * w[6];
+    s[3] += v[7] * w[7];
+  }
+}
+template <class T>
+__device__ __forceinline__ T chunk_total(const T (&s)[4]) {
+  if constexpr (std::is_same<T, double>::value)
+    return s[0];
+  else
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 // Forward sweep, one work item = up to 32 RC consecutive rows of one front's
 // panel P = [inv(L11); W], W = L21 inv(L11):
 //   xg  = x_s + (children's update vectors at the pivot rows)
@@ -611,25 +659,15 @@ __device__ __forceinline__ void fb_fwd_item(const FBArgs<T>& A, int item, const 
   }
   if (yrow) yadd[threadIdx.x] = gather_sum(A, T(0), gy);
   __syncthreads();
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  T sacc[4] = {T(0), T(0), T(0), T(0)};
   for (int c = cb;;) {
-    T w[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
-    s0 += v[0] * w[0];
-    s1 += v[1] * w[1];
-    s2 += v[2] * w[2];
-    s3 += v[3] * w[3];
-    s0 += v[4] * w[4];
-    s1 += v[5] * w[5];
-    s2 += v[6] * w[6];
-    s3 += v[7] * w[7];
+    chunk_acc(sacc, v, xg + c, min(8, ce - c));
     c += 8;
     if (c >= ce) break;
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = pr[F * min(c + t, cl)];
   }
-  part[warp][lane] = (s0 + s1) + (s2 + s3);
+  part[warp][lane] = chunk_total(sacc);
   __syncthreads();
   if (threadIdx.x < nr) {
     const int l = threadIdx.x;
@@ -693,6 +731,20 @@ __device__ __forceinline__ void op_out(T sum, double sigma, double sigma_i, doub
   }
 }
 
+// acc + sum_{t < nrow} trow[t] g[t] over a staged 32-row block of which
+// the first nrow rows (warp-uniform) lie inside the front: the products of
+// the rows past its end are zero and, in FP64, cost full issue slots.
+template <class T>
+__device__ __forceinline__ T block_acc(T acc, const T* trow, const T* g, int nrow) {
+  if (nrow >= 32) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc += trow[t] * g[t];
+  } else {
+    for (int t = 0; t < nrow; ++t) acc += trow[t] * g[t];
+  }
+  return acc;
+}
+
 template <class T, int NW>
 __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, double sigma,
                                             const typename RealOf<T>::type* vu,
@@ -742,8 +794,7 @@ __device__ __forceinline__ void fb_bwd_item(const FBArgs<T>& A, int item, T* x, 
 #pragma unroll
     for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[q];
     __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+    acc = block_acc(acc, tile[warp][lane], gs[warp], (int)min((int64_t)32, F - r0));
     __syncwarp();
   }
   red[warp][lane] = acc;
@@ -923,41 +974,20 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
   }
   if (yrow) yadd[threadIdx.x] = gather_sum(A, T(0), gy);
   __syncthreads();
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  T sacc[4] = {T(0), T(0), T(0), T(0)};
   int c = cb;
 #pragma unroll
   for (int ch = 0; ch < kPreChunks; ++ch) {
-    if (c < ce) {
-      T w[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
-      s0 += v[ch][0] * w[0];
-      s1 += v[ch][1] * w[1];
-      s2 += v[ch][2] * w[2];
-      s3 += v[ch][3] * w[3];
-      s0 += v[ch][4] * w[4];
-      s1 += v[ch][5] * w[5];
-      s2 += v[ch][6] * w[6];
-      s3 += v[ch][7] * w[7];
-    }
+    if (c < ce) chunk_acc(sacc, v[ch], xg + c, min(8, ce - c));
     c += 8;
   }
   for (; c < ce; c += 8) {   // columns beyond the preloaded chunks (largest fronts only)
-    T vv[8], w[8];
+    T vv[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) vv[t] = pr[F * min(c + t, cl)];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) w[t] = c + t < ce ? xg[c + t] : T(0);
-    s0 += vv[0] * w[0];
-    s1 += vv[1] * w[1];
-    s2 += vv[2] * w[2];
-    s3 += vv[3] * w[3];
-    s0 += vv[4] * w[4];
-    s1 += vv[5] * w[5];
-    s2 += vv[6] * w[6];
-    s3 += vv[7] * w[7];
+    chunk_acc(sacc, vv, xg + c, min(8, ce - c));
   }
-  part[warp][lane] = (s0 + s1) + (s2 + s3);
+  part[warp][lane] = chunk_total(sacc);
   __syncthreads();
   if (threadIdx.x < nr) {
     const int l = threadIdx.x;
@@ -1024,13 +1054,13 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
   // rest streamed
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
-    if (c0 + 32 * warp + 32 * NW * b < F) {
+    const int64_t rb = c0 + 32 * warp + 32 * NW * b;
+    if (rb < F) {
       gs[warp][lane] = xi[b] >= 0 ? -__ldcg(x + xi[b]) : zv[b];
 #pragma unroll
       for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[b][q];
       __syncwarp();
-#pragma unroll
-      for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+      acc = block_acc(acc, tile[warp][lane], gs[warp], (int)min((int64_t)32, F - rb));
       __syncwarp();
     }
   }
@@ -1043,8 +1073,7 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     for (int q = 0; q < 32; ++q) tile[warp][q][lane] = pr[F * min(q, nc - 1)];
     gs[warp][lane] = g;
     __syncwarp();
-#pragma unroll
-    for (int t = 0; t < 32; ++t) acc += tile[warp][lane][t] * gs[warp][t];
+    acc = block_acc(acc, tile[warp][lane], gs[warp], (int)min((int64_t)32, F - r0));
     __syncwarp();
   }
   red[warp][lane] = acc;
