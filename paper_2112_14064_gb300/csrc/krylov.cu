@@ -46,6 +46,7 @@ namespace {
 constexpr int kSplit = 4;
 constexpr int kSellBlock = 256;
 constexpr int kSlicesPerBlock = kSellBlock / 32 / kSplit;
+constexpr int kSellUnroll = 4;   // slots of a thread's row loaded together
 static_assert(kSlicesPerBlock >= 1, "a block covers whole slices");
 // sum of the kSplit partial sums of row `lane` of the slice whose first warp is w0
 __device__ __forceinline__ double sell_combine(const double (*red)[32], int w0, int lane) {
@@ -113,13 +114,31 @@ __global__ void __launch_bounds__(kSellBlock) k_spmv_op(
   const Sell q = sell_slice(off, ns, r);
   const int64_t e0 = q.o0 + lane;
   pdl_wait();
+  // kSellUnroll slots per step, every load of a step issued before its
+  // products, so that the column-index loads and then the gathers overlap
   double acc = 0.0;
-#pragma unroll 2
-  for (int k = sub; k < q.wd; k += kSplit) {
-    const int64_t e = e0 + 32 * (int64_t)k;
-    const int32_t c = col[e];
-    acc = fma(Ms[e], w[c], acc);
-    acc = fma(Cs[e], vu[c], acc);
+  for (int k = sub; k < q.wd; k += kSellUnroll * kSplit) {
+    int32_t c[kSellUnroll];
+    double mv[kSellUnroll], cv[kSellUnroll], wv[kSellUnroll], uv[kSellUnroll];
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t) {
+      const int kk = k + t * kSplit;
+      const int64_t e = e0 + 32 * (int64_t)min(kk, q.wd - 1);
+      c[t] = col[e];
+      mv[t] = Ms[e];
+      cv[t] = Cs[e];
+    }
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t) {
+      wv[t] = w[c[t]];
+      uv[t] = vu[c[t]];
+    }
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t)
+      if (k + t * kSplit < q.wd) {
+        acc = fma(mv[t], wv[t], acc);
+        acc = fma(cv[t], uv[t], acc);
+      }
   }
   __shared__ double red[kSellBlock / 32][32];
   red[warp][lane] = acc;
@@ -318,10 +337,20 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
   const int64_t e0 = q.o0 + lane;
   pdl_wait();
   double acc = 0.0;
-#pragma unroll 2
-  for (int k = sub; k < q.wd; k += kSplit) {
-    const int64_t e = e0 + 32 * (int64_t)k;
-    acc = fma(Ms[e], zl[col[e]], acc);
+  for (int k = sub; k < q.wd; k += kSellUnroll * kSplit) {   // as in k_spmv_op
+    int32_t c[kSellUnroll];
+    double mv[kSellUnroll], zv[kSellUnroll];
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t) {
+      const int64_t e = e0 + 32 * (int64_t)min(k + t * kSplit, q.wd - 1);
+      c[t] = col[e];
+      mv[t] = Ms[e];
+    }
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t) zv[t] = zl[c[t]];
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t)
+      if (k + t * kSplit < q.wd) acc = fma(mv[t], zv[t], acc);
   }
   __shared__ double red[kSellBlock / 32][32];
   __shared__ double bs[kSlicesPerBlock];
