@@ -232,6 +232,9 @@ constexpr int kClusterMinK = 64;    // pivot blocks from this size use a cluster
 constexpr int kClusterMaxK = 800;   // up to this size (k x 32 panel in shared memory)
 constexpr int kClusterMaxKc = 384;  // the same for the complex factor (16-byte scalars)
 constexpr size_t kSmemOptIn = 227 * 1024;   // largest dynamic shared memory of a CTA
+// largest row panel of k_panel_rows in shared memory (its static tiles take
+// the rest of the opt-in size)
+constexpr size_t kPanelSmemMax = 200 * 1024;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int32_t* fronts) {
@@ -384,9 +387,11 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
 // 16 x 32 tiles of the rows are staged in shared memory (coalesced loads).
 template <class T>
 __global__ void __launch_bounds__(256) k_panel_rows(FrontArgs<T> A, const int4* items, int item_begin,
-                                                    int mode) {
+                                                    int mode, T* gout, int kstride) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  T* out = reinterpret_cast<T*>(dyn_smem);   // 16 x k, row-major
+  // 16 x k, row-major: in shared memory, or (pivot blocks too wide for it)
+  // in this item's slice of a global buffer
+  T* out = gout ? gout + (size_t)blockIdx.x * 16 * (size_t)kstride : reinterpret_cast<T*>(dyn_smem);
   __shared__ T ta[16][33];            // rows x c
   __shared__ T tb[32][33];            // c x j  (or j x c)
   int4 it = items[item_begin + blockIdx.x];
@@ -1305,9 +1310,20 @@ void factor_plan(Problem& P) {
     smem_at_least((const void*)k_pivot_cluster<zd>, sizeof(zd) * 32 * (size_t)kClusterMaxKc);
   }
   P.Dval.alloc(L.N);
-  size_t smem = sizeof(double) * 16 * (size_t)std::max(1, (int)L.max_front);
+  // row panels: 16 x k per item in shared memory, else a global buffer for
+  // the levels whose pivot blocks are wider (sized for 16-byte scalars)
+  const size_t kpan = smem_fwd_max(P) / sizeof(double);
+  size_t smem = std::min(sizeof(double) * 16 * kpan, kPanelSmemMax);
   if (smem > 48 * 1024) smem_at_least((const void*)k_panel_rows<double>, smem);
   if (smem / 2 > 48 * 1024) smem_at_least((const void*)k_panel_rows<float>, smem / 2);
+  {
+    size_t need = 0;
+    for (int l = 0; l < L.nlevels; ++l)
+      if (sizeof(zd) * 16 * (size_t)P.lvl_maxK[l] > kPanelSmemMax)   // the widest scalar
+        need = std::max(need, (size_t)(P.row_lvl[l + 1] - P.row_lvl[l]) * 16 *
+                                  (size_t)P.lvl_maxK[l] * 2);
+    if (need > 0) P.panel_scratch.alloc(need);
+  }
   size_t piv = sizeof(double) * (size_t)L.max_front;
   if (piv > 48 * 1024) smem_at_least((const void*)k_pivot_factor<double>, piv);
   if (piv / 2 > 48 * 1024) smem_at_least((const void*)k_pivot_factor<float>, piv / 2);
@@ -1315,8 +1331,8 @@ void factor_plan(Problem& P) {
   // per row (k = the largest pivot block)
   const size_t kmax = smem_fwd_max(P) / sizeof(double);
   const size_t zrows = sizeof(zd) * 16 * kmax, zpiv = sizeof(zd) * kmax;
-  if (zrows > 48 * 1024 && zrows <= kSmemOptIn)
-    smem_at_least((const void*)k_panel_rows<zd>, zrows);
+  if (zrows > 48 * 1024)
+    smem_at_least((const void*)k_panel_rows<zd>, std::min(zrows, kPanelSmemMax));
   if (zpiv > 48 * 1024 && zpiv <= kSmemOptIn) smem_at_least((const void*)k_pivot_factor<zd>, zpiv);
   smem_at_least((const void*)k_fb_bwd<zd, 8>, bwd_smem<zd>(8));
   if (2 * smem_fwd_max(P) > 48 * 1024)
@@ -1379,9 +1395,15 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
     }
     int rb = P.row_lvl[l], rc = P.row_lvl[l + 1] - rb;
     int tb = P.tile_lvl[l], tc = P.tile_lvl[l + 1] - tb;
-    size_t smem = sizeof(T) * 16 * (size_t)std::max(1, P.lvl_maxK[l]);
+    const int kl = std::max(1, P.lvl_maxK[l]);
+    size_t smem = sizeof(T) * 16 * (size_t)kl;
+    T* gout = nullptr;   // pivot blocks too wide for shared memory: a global buffer
+    if (smem > kPanelSmemMax) {
+      gout = reinterpret_cast<T*>(P.panel_scratch.p);
+      smem = 0;
+    }
     if (rc > 0) {
-      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 0);            // L21
+      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 0, gout, kl);   // L21
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
@@ -1391,7 +1413,7 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
       ++P.launches;
     }
     if (rc > 0) {
-      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 1);            // W = L21 inv(L11)
+      k_panel_rows<T><<<rc, 256, smem, s>>>(A, rows, rb, 1, gout, kl);   // W = L21 inv(L11)
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
@@ -1493,6 +1515,12 @@ void fb_plan(Problem& P) {
     int fa = 0, ba = 0;
     P.dep_maxK = 1;
     for (int l = kDepLevel; l < L.nlevels; ++l) P.dep_maxK = std::max(P.dep_maxK, P.lvl_maxK[l]);
+    // the gathered right-hand side of the widest pivot block (above 48 KB on
+    // the largest meshes)
+    if (sizeof(double) * (size_t)P.dep_maxK > 48 * 1024)
+      smem_at_least((const void*)k_fb_fwd_dep<double>, sizeof(double) * (size_t)P.dep_maxK);
+    if (sizeof(float) * (size_t)P.dep_maxK > 48 * 1024)
+      smem_at_least((const void*)k_fb_fwd_dep<float>, sizeof(float) * (size_t)P.dep_maxK);
     RQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &fa, k_fb_fwd_dep<double>, 256, sizeof(double) * (size_t)P.dep_maxK));
     RQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ba, k_fb_bwd_dep<double>, 256,

@@ -214,6 +214,9 @@ struct Problem {
   DBuf<int64_t> loff, uoff;
   // numeric factor
   DBuf<double> Lval, Uval, Dinv, Dval;
+  // row panels of pivot blocks too wide for shared memory (16 rows x k per
+  // item of such a level, any scalar type; sized in doubles)
+  DBuf<double> panel_scratch;
   // FP32 factor (mixed precision: FP32 fronts, FP64 iterative refinement)
   DBuf<float> Lval32, Uval32, Dinv32, Dval32, yvec32, zbuf32, ir_r32;
   DBuf<double> ir_y;
