@@ -379,6 +379,265 @@ __global__ void __launch_bounds__(256) k_pivot_cluster(FrontArgs<T> A, const int
   }
 }
 
+// Pivot blocks wider than the cluster kernel holds (k x 32 panel beyond
+// shared memory), by 32-column blocks over many CTAs, one launch per step:
+//   LDL^T, for each block column J from the first:
+//     diag:   A_JJ = L_JJ D_J L_JJ^T (one CTA per front), X_JJ = inv(L_JJ)
+//             kept for the next step;
+//     panel:  L_IJ = A_IJ X_JJ^T D_J^{-1} for every 32-row block I below;
+//     update: A_IK -= L_IJ D_J L_KJ^T for the lower tiles I >= K below J;
+//   inv(L11), for each J from the last:
+//     inv:    X[I, J] = -(L_IJ + sum_{J < Q <= I} X_IQ L_QJ) X_JJ for the
+//             blocks I below J (X below J is final), into a buffer;
+//     store:  the buffer into column block J, X_JJ onto its diagonal block.
+// Each launch covers every wide front of the level (blockIdx.x = front); the
+// fronts' pivot blocks live in global memory (the panel storage), and the
+// kernel boundaries order the steps.  Entries above the diagonal are never
+// written (the FB's triangle relies on their being zero).
+constexpr int kWideB = 32;
+constexpr int kWideFromK = 256;   // pivot blocks above this size take the wide path (measured: faster than the cluster)
+
+template <class T>
+struct WideFront {
+  T* L;      // pivot block, column-major, leading dimension F
+  int64_t F;
+  int a, k;  // first pivot (global index) and pivot count
+};
+template <class T>
+__device__ __forceinline__ WideFront<T> wide_front(const FrontArgs<T>& A, const int32_t* fl, int f) {
+  const int s = fl[f];
+  WideFront<T> w;
+  w.a = A.sptr[s];
+  w.k = A.sptr[s + 1] - w.a;
+  w.F = w.k + (A.upd_ptr[s + 1] - A.upd_ptr[s]);
+  w.L = A.Lval + A.loff[s];
+  return w;
+}
+
+// inv of the unit lower 32 x 32 block bl (rows/cols < jb) into bx, by forward
+// elimination on the identity (all threads of the CTA)
+template <class T>
+__device__ void unit_lower_inverse(const T (*bl)[33], T (*bx)[33], int jb) {
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    bx[r][c] = r == c ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < jb; ++t) {
+    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+      const int r = q & 31, c = q >> 5;
+      if (r > t && r < jb && c <= t) bx[r][c] -= bl[r][t] * bx[t][c];
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_wide_diag(FrontArgs<T> A, const int32_t* fl, int j0,
+                                                   T* xjj) {
+  const WideFront<T> w = wide_front(A, fl, blockIdx.x);
+  if (j0 >= w.k) return;
+  const int jb = min(kWideB, w.k - j0);
+  __shared__ T bl[32][33], bx[32][33];
+  __shared__ T dsh, rdsh;
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    bl[r][c] = (r < jb && c < jb && r >= c) ? w.L[(j0 + r) + w.F * (j0 + c)] : T(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < jb; ++t) {
+    if (threadIdx.x == 0) {
+      T d = bl[t][t];
+      if (pivot_bad(d, A.indef)) {
+        atomicCAS(&A.status->pivot_fail, 0, fl[blockIdx.x] + 1);
+        d = T(1);  // keep going with a harmless value; the host reports the failure
+      } else if (pivot_negative(d)) {
+        atomicAdd(&A.status->neg_pivots, 1);
+      }
+      dsh = d;
+      rdsh = T(1) / d;
+      A.Dval[w.a + j0 + t] = d;
+      A.Dinv[w.a + j0 + t] = rdsh;
+    }
+    __syncthreads();
+    const T d = dsh, rd = rdsh;
+    if (threadIdx.x > t && threadIdx.x < jb) bl[threadIdx.x][t] *= rd;
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+      const int r = q & 31, c = q >> 5;
+      if (c > t && r >= c && r < jb) bl[r][c] -= bl[r][t] * (d * bl[c][t]);
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    if (r < jb && c < jb && r >= c) w.L[(j0 + r) + w.F * (j0 + c)] = r == c ? T(1) : bl[r][c];
+  }
+  unit_lower_inverse(bl, bx, jb);
+  T* X = xjj + (size_t)blockIdx.x * 32 * 32;
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) X[q] = bx[q & 31][q >> 5];
+}
+
+// L_IJ = A_IJ X_JJ^T D_J^{-1} for the 32-row block I = blockIdx.y below J
+template <class T>
+__global__ void __launch_bounds__(256) k_wide_panel(FrontArgs<T> A, const int32_t* fl, int j0,
+                                                    const T* xjj) {
+  const WideFront<T> w = wide_front(A, fl, blockIdx.x);
+  if (j0 >= w.k) return;
+  const int jb = min(kWideB, w.k - j0);
+  const int i0 = j0 + jb + kWideB * (int)blockIdx.y;
+  if (i0 >= w.k) return;
+  const int ib = min(kWideB, w.k - i0);
+  __shared__ T ya[32][33], bx[32][33];
+  __shared__ T dinv[32];
+  const T* X = xjj + (size_t)blockIdx.x * 32 * 32;
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    ya[r][c] = (r < ib && c < jb) ? w.L[(i0 + r) + w.F * (j0 + c)] : T(0);
+    bx[r][c] = X[q];
+  }
+  if (threadIdx.x < jb) dinv[threadIdx.x] = A.Dinv[w.a + j0 + threadIdx.x];
+  __syncthreads();
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;   // out[r][c] = dinv[c] sum_{t <= c} A[r][t] X[c][t]
+    if (r < ib && c < jb) {
+      T acc = T(0);
+      for (int t = 0; t <= c; ++t) acc += ya[r][t] * bx[c][t];
+      w.L[(i0 + r) + w.F * (j0 + c)] = acc * dinv[c];
+    }
+  }
+}
+
+// A_IK -= L_IJ D_J L_KJ^T for the lower tile (I, K) = tile blockIdx.y of the
+// trailing block below J (tiles numbered row by row: I(I+1)/2 + K)
+template <class T>
+__global__ void __launch_bounds__(256) k_wide_update(FrontArgs<T> A, const int32_t* fl, int j0) {
+  const WideFront<T> w = wide_front(A, fl, blockIdx.x);
+  if (j0 >= w.k) return;
+  const int jb = min(kWideB, w.k - j0);
+  const int t0 = j0 + jb, R = w.k - t0;
+  const int nt = (R + kWideB - 1) / kWideB;
+  const int tile = (int)blockIdx.y;
+  if (tile >= nt * (nt + 1) / 2) return;
+  int I = (int)((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+  while (I * (I + 1) / 2 > tile) --I;
+  while ((I + 1) * (I + 2) / 2 <= tile) ++I;
+  const int K = tile - I * (I + 1) / 2;
+  const int ri = t0 + kWideB * I, ck = t0 + kWideB * K;
+  __shared__ T li[32][33], lk[32][33];
+  __shared__ T dv[32];
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;   // c: panel column
+    li[r][c] = (ri + r < w.k && c < jb) ? w.L[(ri + r) + w.F * (j0 + c)] : T(0);
+    lk[r][c] = (ck + r < w.k && c < jb) ? w.L[(ck + r) + w.F * (j0 + c)] : T(0);
+  }
+  if (threadIdx.x < jb) dv[threadIdx.x] = A.Dval[w.a + j0 + threadIdx.x];
+  __syncthreads();
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    const int gr = ri + r, gc = ck + c;
+    if (gr < w.k && gc < w.k && gr >= gc) {
+      T acc = T(0);
+      for (int t = 0; t < jb; ++t) acc += li[r][t] * (dv[t] * lk[c][t]);
+      T* dst = w.L + gr + w.F * gc;
+      *dst = *dst - acc;
+    }
+  }
+}
+
+// X[I, J] for the 32-row block I = blockIdx.y below J into buf (rows x 32 per
+// front, row i - (j0 + jb) of the rest)
+template <class T>
+__global__ void __launch_bounds__(256) k_wide_inv(FrontArgs<T> A, const int32_t* fl, int j0, T* buf,
+                                                  int64_t bstride) {
+  const WideFront<T> w = wide_front(A, fl, blockIdx.x);
+  if (j0 >= w.k) return;
+  const int jb = min(kWideB, w.k - j0);
+  const int t0 = j0 + jb;
+  const int i0 = t0 + kWideB * (int)blockIdx.y;
+  if (i0 >= w.k) return;
+  __shared__ T bl[32][33], bx[32][33], xq[32][33], lq[32][33];
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q & 31, c = q >> 5;
+    bl[r][c] = (r < jb && c < r) ? w.L[(j0 + r) + w.F * (j0 + c)] : T(0);
+  }
+  __syncthreads();
+  unit_lower_inverse(bl, bx, jb);   // X_JJ
+  // z[r][c] = L[i0 + r, j0 + c] + sum_{t0 <= q < i0 + r} X[i0 + r, q] L[q, j0 + c]
+  const int r = threadIdx.x & 31, cg = threadIdx.x >> 5;   // row, columns cg, cg + 8, ...
+  T z[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = cg + 8 * u;
+    z[u] = (i0 + r < w.k && c < jb) ? w.L[(i0 + r) + w.F * (j0 + c)] : T(0);
+  }
+  for (int q0 = t0; q0 <= i0; q0 += kWideB) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+      const int rr = q & 31, cc = q >> 5;
+      // X[i0 + rr, q0 + cc]: strictly below the diagonal (the unit diagonal
+      // is the L term above)
+      const int gi = i0 + rr, gq = q0 + cc;
+      xq[rr][cc] = (gi < w.k && gq < gi) ? w.L[gi + w.F * gq] : T(0);
+      lq[rr][cc] = (q0 + rr < w.k && cc < jb) ? w.L[(q0 + rr) + w.F * (j0 + cc)] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = cg + 8 * u;
+      T acc = z[u];
+      for (int t = 0; t < 32; ++t) acc += xq[r][t] * lq[t][c];
+      z[u] = acc;
+    }
+  }
+  // out = -z X_JJ: out[r][c] = -sum_{t >= c} z[r][t] X_JJ[t][c]
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) xq[r][cg + 8 * u] = z[u];
+  __syncthreads();
+  T* out = buf + (size_t)blockIdx.x * bstride;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = cg + 8 * u;
+    if (i0 + r < w.k && c < jb) {
+      T o = T(0);
+      for (int t = c; t < jb; ++t) o += xq[r][t] * bx[t][c];
+      out[(size_t)(i0 + r - t0) * 32 + c] = -o;
+    }
+  }
+}
+
+// The buffer into column block J below its diagonal block, X_JJ onto it.
+template <class T>
+__global__ void __launch_bounds__(256) k_wide_store(FrontArgs<T> A, const int32_t* fl, int j0,
+                                                    const T* buf, int64_t bstride) {
+  const WideFront<T> w = wide_front(A, fl, blockIdx.x);
+  if (j0 >= w.k) return;
+  const int jb = min(kWideB, w.k - j0);
+  const int t0 = j0 + jb;
+  const int i0 = t0 + kWideB * ((int)blockIdx.y - 1);   // block y = 0: the diagonal block
+  const T* in = buf + (size_t)blockIdx.x * bstride;
+  if (blockIdx.y == 0) {
+    __shared__ T bl[32][33], bx[32][33];
+    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+      const int r = q & 31, c = q >> 5;
+      bl[r][c] = (r < jb && c < r) ? w.L[(j0 + r) + w.F * (j0 + c)] : T(0);
+    }
+    __syncthreads();
+    unit_lower_inverse(bl, bx, jb);
+    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+      const int r = q & 31, c = q >> 5;
+      if (r < jb && c < r) w.L[(j0 + r) + w.F * (j0 + c)] = bx[r][c];
+    }
+    return;
+  }
+  if (i0 >= w.k) return;
+  for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+    const int r = q >> 5, c = q & 31;
+    if (i0 + r < w.k && c < jb) w.L[(i0 + r) + w.F * (j0 + c)] = in[(size_t)(i0 + r - t0) * 32 + c];
+  }
+}
+
 // Row chunks of the update rows (items: front, first update row, rows <= 16):
 // mode 0: L21 = F21 inv(L11)^T D^{-1}   (X[i, j] = D_j^{-1} sum_{c<=j} F21[i,c] inv(L11)[j,c])
 // mode 1: W   = L21 inv(L11)            (W[i, j] = sum_{c>=j} L21[i,c] inv(L11)[c,j])
@@ -1270,39 +1529,39 @@ void factor_plan(Problem& P) {
   }
   P.row_items.upload(rows, P.stream);
   P.tile_items.upload(tiles, P.stream);
-  // pivot blocks of each level: small ones one CTA each, large ones a cluster
-  std::vector<int32_t> pf;
-  P.piv_lvl.assign(2 * L.nlevels + 1, 0);
-  for (int l = 0; l < L.nlevels; ++l) {
-    for (int big = 0; big < 2; ++big) {
-      for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
-        int sn = L.lvl_nodes[q];
-        int k = L.sptr[sn + 1] - L.sptr[sn];
-        bool isbig = k >= kClusterMinK && k <= kClusterMaxK;
-        if (isbig == (big == 1)) pf.push_back(sn);
-      }
-      P.piv_lvl[2 * l + big + 1] = (int32_t)pf.size();
-    }
-  }
-  P.piv_fronts.upload(pf, P.stream);
-  // the complex factor's pivot blocks: its 32-column cluster panel holds
-  // twice the bytes, so blocks of more than kClusterMaxKc pivots go to the
-  // one-CTA kernel
-  {
-    std::vector<int32_t> pc;
-    P.cx.piv_lvl.assign(2 * L.nlevels + 1, 0);
+  // pivot blocks of each level: small ones one CTA each, large ones a
+  // cluster, wider ones by the blocked multi-CTA kernels (k_wide_*); the
+  // complex factor's cluster panel holds twice the bytes, so its blocks of
+  // more than kClusterMaxKc pivots are wide
+  int wide_fronts = 0, wide_k = 0;
+  auto classify = [&](int kmax_cluster, std::vector<int32_t>& lv) {
+    std::vector<int32_t> out;
+    lv.assign(3 * L.nlevels + 1, 0);
     for (int l = 0; l < L.nlevels; ++l)
-      for (int big = 0; big < 2; ++big) {
+      for (int cls = 0; cls < 3; ++cls) {
+        int n = 0;
         for (int q = L.lvl_ptr[l]; q < L.lvl_ptr[l + 1]; ++q) {
           int sn = L.lvl_nodes[q];
           int k = L.sptr[sn + 1] - L.sptr[sn];
-          bool isbig = k >= kClusterMinK && k <= kClusterMaxKc;
-          if (isbig == (big == 1)) pc.push_back(sn);
+          const int c = k < kClusterMinK ? 0 : (k <= std::min(kmax_cluster, kWideFromK) ? 1 : 2);
+          if (c == cls) {
+            out.push_back(sn);
+            ++n;
+            if (cls == 2) wide_k = std::max(wide_k, k);
+          }
         }
-        P.cx.piv_lvl[2 * l + big + 1] = (int32_t)pc.size();
+        if (cls == 2) wide_fronts = std::max(wide_fronts, n);
+        lv[3 * l + cls + 1] = (int32_t)out.size();
       }
-    P.cx.piv_fronts.upload(pc, P.stream);
-  }
+    return out;
+  };
+  P.piv_fronts.upload(classify(kClusterMaxK, P.piv_lvl), P.stream);
+  P.cx.piv_fronts.upload(classify(kClusterMaxKc, P.cx.piv_lvl), P.stream);
+  // wide pivot blocks: X_JJ (32 x 32) and a rows x 32 buffer per front, in
+  // doubles for 16-byte scalars
+  P.wide_bstride = 32 * (int64_t)std::max(wide_k, 1);
+  if (wide_fronts > 0)
+    P.wide_scratch.alloc((size_t)wide_fronts * (32 * 32 + (size_t)P.wide_bstride) * 2);
   {
     size_t cs = sizeof(double) * 32 * (size_t)kClusterMaxK;
     smem_at_least((const void*)k_pivot_cluster<double>, cs);
@@ -1343,6 +1602,41 @@ void factor_plan(Problem& P) {
 
 // tc: the products after the pivot blocks (L21, the Schur update, W) run on
 // the tensor cores (tcfront.cu) instead of k_panel_rows / k_schur_tile
+// The wide pivot blocks of level l (the k_wide_* steps, every front of the
+// level in each launch).
+template <class T>
+void launch_wide_pivots(Problem& P, const FrontArgs<T>& A, const int32_t* fl, int nwide, int l) {
+  cudaStream_t s = P.stream;
+  const int kmax = P.lvl_maxK[l];
+  const int nb = (kmax + kWideB - 1) / kWideB;
+  T* xjj = reinterpret_cast<T*>(P.wide_scratch.p);
+  T* buf = xjj + (size_t)nwide * 32 * 32;
+  for (int J = 0; J < nb; ++J) {
+    const int j0 = J * kWideB;
+    const int nrb = nb - J - 1;   // 32-row blocks below J (largest front)
+    k_wide_diag<T><<<nwide, 256, 0, s>>>(A, fl, j0, xjj);
+    RQ_CUDA(cudaGetLastError());
+    if (nrb > 0) {
+      k_wide_panel<T><<<dim3(nwide, nrb), 256, 0, s>>>(A, fl, j0, xjj);
+      RQ_CUDA(cudaGetLastError());
+      k_wide_update<T><<<dim3(nwide, nrb * (nrb + 1) / 2), 256, 0, s>>>(A, fl, j0);
+      RQ_CUDA(cudaGetLastError());
+    }
+    P.launches += nrb > 0 ? 3 : 1;
+  }
+  for (int J = nb - 1; J >= 0; --J) {
+    const int j0 = J * kWideB;
+    const int nrb = nb - J - 1;
+    if (nrb > 0) {
+      k_wide_inv<T><<<dim3(nwide, nrb), 256, 0, s>>>(A, fl, j0, buf, P.wide_bstride);
+      RQ_CUDA(cudaGetLastError());
+    }
+    k_wide_store<T><<<dim3(nwide, nrb + 1), 256, 0, s>>>(A, fl, j0, buf, P.wide_bstride);
+    RQ_CUDA(cudaGetLastError());
+    P.launches += nrb > 0 ? 2 : 1;
+  }
+}
+
 template <class T>
 void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool indef = false,
                      double cMi = 0.0, double cCi = 0.0) {
@@ -1362,11 +1656,12 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
     k_front_assemble<T><<<cnt * nsplit, 256, 0, s>>>(A, b, nsplit, P.rowptr_n.p, P.fpos.p, P.Kn.p,
                                                      P.Mn.p, P.Cn.p, cM, cC, cMi, cCi);
     RQ_CUDA(cudaGetLastError());
-    const int nsm = piv_lvl[2 * l + 1] - piv_lvl[2 * l];
-    const int nbig = piv_lvl[2 * l + 2] - piv_lvl[2 * l + 1];
+    const int nsm = piv_lvl[3 * l + 1] - piv_lvl[3 * l];
+    const int nbig = piv_lvl[3 * l + 2] - piv_lvl[3 * l + 1];
+    const int nwide = piv_lvl[3 * l + 3] - piv_lvl[3 * l + 2];
     if (nsm > 0) {
       k_pivot_factor<T><<<nsm, 256, sizeof(T) * (size_t)P.lvl_maxK[l], s>>>(
-          A, piv_fronts + piv_lvl[2 * l]);
+          A, piv_fronts + piv_lvl[3 * l]);
       RQ_CUDA(cudaGetLastError());
       ++P.launches;
     }
@@ -1384,10 +1679,11 @@ void launch_factor_t(Problem& P, double cM, double cC, bool tc = false, bool ind
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      const int32_t* fl = piv_fronts + piv_lvl[2 * l + 1];
+      const int32_t* fl = piv_fronts + piv_lvl[3 * l + 1];
       RQ_CUDA(cudaLaunchKernelEx(&cfg, k_pivot_cluster<T>, A, fl));
       ++P.launches;
     }
+    if (nwide > 0) launch_wide_pivots<T>(P, A, piv_fronts + piv_lvl[3 * l + 2], nwide, l);
     ++P.launches;
     if (tc) {
       launch_tc_level(P, l);

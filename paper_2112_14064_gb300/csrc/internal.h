@@ -217,6 +217,10 @@ struct Problem {
   // row panels of pivot blocks too wide for shared memory (16 rows x k per
   // item of such a level, any scalar type; sized in doubles)
   DBuf<double> panel_scratch;
+  // pivot blocks wider than the cluster kernel: X_JJ and a rows x 32 buffer
+  // per front of a level (sized in doubles for 16-byte scalars)
+  DBuf<double> wide_scratch;
+  int64_t wide_bstride = 32;
   // FP32 factor (mixed precision: FP32 fronts, FP64 iterative refinement)
   DBuf<float> Lval32, Uval32, Dinv32, Dval32, yvec32, zbuf32, ir_r32;
   DBuf<double> ir_y;
@@ -236,7 +240,7 @@ struct Problem {
   int n_ir = 0;                 // refinement steps per solve with the FP32 factor
   DBuf<int32_t> row_items, tile_items;    // factor work items (front, a, b, 0)
   DBuf<int32_t> piv_fronts;     // per level: small pivot blocks, then cluster-sized ones
-  std::vector<int32_t> piv_lvl; // boundaries: level l small [2l, 2l+1), large [2l+1, 2l+2)
+  std::vector<int32_t> piv_lvl; // boundaries: level l small [3l, 3l+1), cluster [3l+1, 3l+2), wide [3l+2, 3l+3)
   std::vector<int32_t> row_lvl, tile_lvl;
   DBuf<double> yvec;            // FB update vectors (one per supernode, struct-sized)
   DBuf<double> xwork;           // FB work vector (N)
