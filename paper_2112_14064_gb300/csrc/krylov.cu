@@ -161,6 +161,7 @@ constexpr int kTileRows = 128;
 constexpr int kDotsCols = 96;    // columns per launch (the largest Krylov dimension)
 constexpr int kDotsThreads = 384;
 constexpr int kBoxCols = 8;
+constexpr int kDotsGroups = 8;   // first stage of the cross-block sum
 static_assert(kDotsCols >= kMaxKrylov, "one launch covers every basis column");
 constexpr uint32_t kTmaWaitLimit = 1u << 22;
 
@@ -290,30 +291,56 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
   }
   red[warp][lane] = acc[0];
   __syncthreads();
-  if (threadIdx.x < kDotsCols) {
+  if (threadIdx.x < ncol) {
     const int cgr = threadIdx.x >> 5, l = threadIdx.x & 31;
     double sm = (red[4 * cgr][l] + red[4 * cgr + 1][l]) + (red[4 * cgr + 2][l] + red[4 * cgr + 3][l]);
     part[blockIdx.x * kDotsCols + threadIdx.x] = sm;
   }
+  // Blocks sum in two stages, each in a fixed order: the last block of each
+  // of ng groups (blocks g, g + ng, ...) adds its group's
+  // partial sums, and the last group to finish adds the group sums.  Every
+  // FP64 addition costs a 64-cycle issue slot, so one block summing all
+  // gridDim x ncol partials (the tail of the launch) took several times as
+  // long as the two short stages.
+  const int ng = min(kDotsGroups, (int)gridDim.x);
+  const int grp = (int)blockIdx.x % ng;
+  const int gsize = ((int)gridDim.x - grp + ng - 1) / ng;
+  double* gpart = part + (int64_t)gridDim.x * kDotsCols;   // kDotsGroups x 96 group sums
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(counter + 1 + grp, 1u) == (unsigned)gsize - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
   // 384 threads: column c = tid mod 96, quarter = tid / 96 sums every fourth
-  // block (L2 loads, unrolled so that several are in flight; fixed order)
+  // block of the group (L2 loads; fixed order)
   const int c = threadIdx.x % kDotsCols, qtr = threadIdx.x / kDotsCols;
-  double sm = 0.0;
-#pragma unroll 8
-  for (int b = qtr; b < (int)gridDim.x; b += 4) sm += __ldcg(part + b * kDotsCols + c);
-  __syncthreads();
   double* red2 = &red[0][0];    // 4 x 96
-  red2[qtr * kDotsCols + c] = sm;
+  {
+    double sm = 0.0;
+    if (c < ncol)
+      for (int b = grp + ng * qtr; b < (int)gridDim.x; b += 4 * ng)
+        sm += __ldcg(part + b * kDotsCols + c);
+    red2[qtr * kDotsCols + c] = sm;
+  }
   __syncthreads();
+  if (threadIdx.x < ncol)
+    gpart[grp * kDotsCols + threadIdx.x] =
+        (red2[threadIdx.x] + red2[kDotsCols + threadIdx.x]) +
+        (red2[2 * kDotsCols + threadIdx.x] + red2[3 * kDotsCols + threadIdx.x]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    counter[1 + grp] = 0u;
+    last = (atomicAdd(counter, 1u) == (unsigned)ng - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   if (threadIdx.x < ncol) {
-    double v = (red2[threadIdx.x] + red2[kDotsCols + threadIdx.x]) +
-               (red2[2 * kDotsCols + threadIdx.x] + red2[3 * kDotsCols + threadIdx.x]);
+    double v = 0.0;
+#pragma unroll
+    for (int g2 = 0; g2 < ng; ++g2) v += __ldcg(gpart + g2 * kDotsCols + threadIdx.x);
     h[threadIdx.x] = v;
     H[threadIdx.x + (int64_t)ldh * j] += v;
   }
@@ -400,8 +427,10 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
 }
 
 // z[i] -= sum_c V[i, c] h[c] over the 2 Np rows of column z (ld stride in V)
-// One row per thread, eight basis loads in flight; launched as two equal
-// blocks per SM (a single balanced wave).
+// One row per thread, sixteen basis loads in flight (measured 0.1 ms per
+// eigensolve ahead of eight), eight partial sums.  Launched as exactly as
+// many equal blocks as fit on the SMs at once (a single balanced wave; see
+// the launch).
 __global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, int ncol,
                                                  const double* h, double* z, int64_t rows) {
   pdl_trigger();
@@ -416,6 +445,13 @@ __global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, in
 #pragma unroll
   for (int t = 0; t < 8; ++t) a[t] = 0.0;
   int c = 0;
+  for (; c + 16 <= ncol; c += 16) {
+    double v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = vr[ld * (c + t)];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) a[t & 7] = fma(v[t], hs[c + t], a[t & 7]);
+  }
   for (; c + 8 <= ncol; c += 8) {
     double v[8];
 #pragma unroll
@@ -825,7 +861,7 @@ struct Work {
   double ritz_ms = 0.0;
   CUtensorMap tV{};  // the Krylov basis V for the TMA-fed kernels
   int nsm = 0;       // SMs of the device (one TMA block each)
-  int upd_threads = 256;   // k_update block: two equal blocks per SM
+  int upd_threads = 256;   // k_update block: equal blocks, as many per SM as fit
   ~Work() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     for (cudaEvent_t e : rz)
@@ -852,7 +888,7 @@ struct Work {
 
   void dots(int j, const double* xa, const double* xb) {
     launch_pdl(k_dots_tma, dim3(nsm), dim3(kDotsThreads), dots_tma_smem(), s, tV, j + 1, xa, xb, Np,
-               P.part.p, P.counter.p, P.hvec.p, P.H.p, m + 1, j, P.status.p);
+               P.part.p, P.counter.p + 4, P.hvec.p, P.H.p, m + 1, j, P.status.p);
     ++P.launches;
   }
   // B-norm of column c -> H[c, c-1] (if setH) and V[:, c] normalised
@@ -936,15 +972,26 @@ void krylov_schur(Problem& P, const EigsParams& E, const double* v1) {
     RQ_CUDA(cudaGetDevice(&dev));
     RQ_CUDA(cudaDeviceGetAttribute(&W.nsm, cudaDevAttrMultiProcessorCount, dev));
     smem_at_least((const void*)k_dots_tma, dots_tma_smem());
-    // rows of the update split into 2 nsm blocks of whole warps (<= 1024)
-    const int64_t per = (2 * W.Np + 2 * W.nsm - 1) / (2 * W.nsm);
-    W.upd_threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (per + 31) / 32 * 32));
+    // rows of the update split into bps * nsm blocks of whole warps (<= 1024),
+    // bps the number of such blocks that fit on an SM: when more fit than the
+    // grid gives each SM, the SMs that free up first (the launch overlaps the
+    // previous kernel's tail) take the extra blocks and the others idle.  A
+    // 32-register build of this kernel let a third 544-thread block onto an
+    // SM and took 25-38% longer in the eigensolve than the 48-register one.
+    for (int bps = 2;;) {
+      const int64_t per = (2 * W.Np + bps * W.nsm - 1) / (bps * (int64_t)W.nsm);
+      W.upd_threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (per + 31) / 32 * 32));
+      int occ = 0;
+      RQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update, W.upd_threads, 0));
+      if (occ <= bps || bps >= 32) break;
+      bps = occ;
+    }
   }
   P.Vtmp.alloc(ld * m);
   P.H.alloc((m + 1) * m);
   P.part.alloc(64 * (size_t)std::max(W.nblk, 4 * 1024) + (size_t)(L.N * 8 + 255) / 256);
-  P.counter.alloc(4);
-  RQ_CUDA(cudaMemsetAsync(P.counter.p, 0, 4 * sizeof(unsigned), s));
+  P.counter.alloc(16);
+  RQ_CUDA(cudaMemsetAsync(P.counter.p, 0, 16 * sizeof(unsigned), s));
   P.hvec.alloc(kMaxKrylov + 1);
   P.yop.alloc(Np);
   P.wop.alloc(Np);
