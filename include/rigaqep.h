@@ -165,7 +165,8 @@ typedef struct {
   double norm_K, norm_M, norm_C;  /* max-row-sum norms */
   double factor_ms;      /* device time of the last rigaqep_factor */
   double eigs_ms;        /* device time of the last rigaqep_eigs */
-  double fb_ms;          /* device time of its FB solves (CUDA events around each) */
+  double fb_ms;          /* device time of its FB solves: CUDA events around every
+                            eighth solve, their mean times n_apply */
   int64_t certified;     /* 1: no eigenvalue outside the converged candidates can be nearer
                             the target than the returned pairs, given that the candidates
                             include every eigenvalue within their largest distance to the
