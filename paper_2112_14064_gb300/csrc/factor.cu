@@ -997,16 +997,22 @@ __device__ __forceinline__ void op_out(T sum, double sigma, double sigma_i, doub
 
 // acc + sum_{t < nrow} trow[t] g[t] over a staged 32-row block of which
 // the first nrow rows (warp-uniform) lie inside the front: the products of
-// the rows past its end are zero and, in FP64, cost full issue slots.
-template <class T>
+// the rows past its end are zero and, in FP64, cost full issue slots.  R: the
+// rows a lane covers in a full block (32, or 16 with two lanes per column).
+template <class T, int R = 32>
 __device__ __forceinline__ T block_acc(T acc, const T* trow, const T* g, int nrow) {
-  if (nrow >= 32) {
+  if (nrow >= R) {
 #pragma unroll
-    for (int t = 0; t < 32; ++t) acc += trow[t] * g[t];
+    for (int t = 0; t < R; ++t) acc += trow[t] * g[t];
   } else {
     for (int t = 0; t < nrow; ++t) acc += trow[t] * g[t];
   }
   return acc;
+}
+
+template <class T>
+__device__ __forceinline__ T shfl_down_t(T v, int d) {
+  return __shfl_down_sync(0xffffffffu, v, d);
 }
 
 template <class T, int NW>
@@ -1174,6 +1180,7 @@ __device__ __forceinline__ void dep_finish_launch(unsigned* ticket) {
 // the gather indices) is loaded before the block waits for the children, so
 // that only the children's update values are read after the wait.
 constexpr int kPreChunks = 5;
+constexpr int kBwdHalfRows = 192;   // fronts whose backward items take at most 16 columns
 
 template <class T, int RC>
 __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item,
@@ -1270,8 +1277,14 @@ __device__ __forceinline__ void fb_fwd_item_pre(const FBArgs<T>& A, const FBDep&
 // fb_bwd_item with eight warps; the panel blocks (up to two per warp), the
 // pivot-row values of the forward sweep and the indices of the update rows
 // are loaded before the block waits for its parent; only the solution
-// entries of the ancestors are read after the wait.
-template <class T>
+// entries of the ancestors are read after the wait.  NC = 32: lane c forms
+// column c's dot product over the 32 rows of a staged block.  NC = 16 (items
+// of at most 16 columns, made for the wide fronts at the top of the tree,
+// whose items are bound by their own FP64 issue): lanes c and c + 16 each
+// take half of the block's rows of column c, so every FP64 instruction still
+// does 32 products and an item costs half the instructions; the two halves
+// meet in one shuffle at the end.
+template <class T, int NC>
 __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep& D, int item, T* x,
                                                 double sigma, const typename RealOf<T>::type* vu,
                                                 typename RealOf<T>::type* ru,
@@ -1289,8 +1302,11 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
   const T* P = A.Lval + ((int64_t)(uint32_t)i2.x | ((int64_t)i2.y << 32)) + F * c0;
   const int32_t* st = A.upd_idx + i1.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this lane's column and first row of a staged block when computing
+  const int ccol = NC == 32 ? lane : (lane & 15);
+  const int hrow = NC == 32 ? 0 : 16 * (lane >> 4);
   // blocks 0 and 1 of this warp: rows c0 + 32 warp + lane + 256 b
-  T v[2][32];
+  T v[2][NC];
   T zv[2];
   int xi[2];   // update rows: index into x (-1: pivot row or past the front)
 #pragma unroll
@@ -1298,7 +1314,7 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     const int64_t i = c0 + 32 * warp + lane + 32 * NW * b;
     const T* pr = P + (i < F ? i : F - 1);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) v[b][q] = pr[F * min(q, nc - 1)];
+    for (int q = 0; q < NC; ++q) v[b][q] = pr[F * min(q, nc - 1)];
     zv[b] = T(0);
     xi[b] = -1;
     if (i < F) {
@@ -1314,6 +1330,12 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     dep_wait(D.bdone + pa, D.epoch * (unsigned)D.bwd_items[pa], D.status);
   __syncthreads();
   T acc = T(0);
+  // rows of a staged block at rb inside the front, counted from this lane's
+  // first row (the products of the rows past the end are zero and, in FP64,
+  // cost full issue slots)
+  auto nrows = [&](int64_t rb) {
+    return (int)max((int64_t)0, min((int64_t)(NC == 32 ? 32 : 16), F - rb - hrow));
+  };
   // blocks 0 and 1 from the preloaded registers (compile-time indices), the
   // rest streamed
 #pragma unroll
@@ -1322,9 +1344,9 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     if (rb < F) {
       gs[warp][lane] = xi[b] >= 0 ? -__ldcg(x + xi[b]) : zv[b];
 #pragma unroll
-      for (int q = 0; q < 32; ++q) tile[warp][q][lane] = v[b][q];
+      for (int q = 0; q < NC; ++q) tile[warp][q][lane] = v[b][q];
       __syncwarp();
-      acc = block_acc(acc, tile[warp][lane], gs[warp], (int)min((int64_t)32, F - rb));
+      acc = block_acc<T, NC == 32 ? 32 : 16>(acc, tile[warp][ccol] + hrow, gs[warp] + hrow, nrows(rb));
       __syncwarp();
     }
   }
@@ -1334,12 +1356,13 @@ __device__ __forceinline__ void fb_bwd_item_pre(const FBArgs<T>& A, const FBDep&
     if (i < F) g = i < k ? __ldcg(A.zbuf + a + i) : -__ldcg(x + st[i - k]);
     const T* pr = P + (i < F ? i : F - 1);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) tile[warp][q][lane] = pr[F * min(q, nc - 1)];
+    for (int q = 0; q < NC; ++q) tile[warp][q][lane] = pr[F * min(q, nc - 1)];
     gs[warp][lane] = g;
     __syncwarp();
-    acc = block_acc(acc, tile[warp][lane], gs[warp], (int)min((int64_t)32, F - r0));
+    acc = block_acc<T, NC == 32 ? 32 : 16>(acc, tile[warp][ccol] + hrow, gs[warp] + hrow, nrows(r0));
     __syncwarp();
   }
+  if constexpr (NC == 16) acc += shfl_down_t(acc, 16);
   red[warp][lane] = acc;
   __syncthreads();
   if (threadIdx.x < nc) {
@@ -1377,7 +1400,7 @@ __global__ void __launch_bounds__(256) k_fb_fwd_dep(FBArgs<T> A, FBDep D, int it
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const int32_t* order,
+__global__ void __launch_bounds__(256, 1) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const int32_t* order,
                                                     int n_items, T* x, double sigma, const T* vu,
                                                     T* ru, T* rl, double uscale) {
   pdl_trigger();
@@ -1389,7 +1412,10 @@ __global__ void __launch_bounds__(256) k_fb_bwd_dep(FBArgs<T> A, FBDep D, const 
     if (t >= n_items) break;
     const int item = order[t];
     const int s = A.bwd_items[3 * (int64_t)item].x;
-    fb_bwd_item_pre<T>(A, D, item, x, sigma, vu, ru, rl, smem, uscale);
+    if (A.bwd_items[3 * (int64_t)item].z <= 16)
+      fb_bwd_item_pre<T, 16>(A, D, item, x, sigma, vu, ru, rl, smem, uscale);
+    else
+      fb_bwd_item_pre<T, 32>(A, D, item, x, sigma, vu, ru, rl, smem, uscale);
     if (threadIdx.x == 0) red_release_add(D.bdone + s, 1u);
   }
   dep_finish_launch(D.ticket);
@@ -1799,8 +1825,13 @@ void fb_plan(Problem& P) {
       for (int r = 0; r < k + u; r += rows)
         fwd.insert(fwd.end(), {s, r, std::min(rows, k + u - r), a, k, u, gbase[s], L.upd_ptr[s],
                                lo, hi, nkid, P.fwd_rc[l]});
-      for (int c = 0; c < k; c += 32)
-        bwd.insert(bwd.end(), {s, c, std::min(32, k - c), a, k, u, L.upd_ptr[s], 0, lo, hi, 0, 0});
+      // backward items of 32 pivot columns; in the dependency-driven levels
+      // the fronts of at least kBwdHalfRows rows take items of at most 16
+      // (balanced), which the sweep runs with two lanes per column
+      const int bw = l >= kDepLevel && k + u >= kBwdHalfRows ? (k + (k + 15) / 16 - 1) / ((k + 15) / 16)
+                                                             : 32;
+      for (int c = 0; c < k; c += bw)
+        bwd.insert(bwd.end(), {s, c, std::min(bw, k - c), a, k, u, L.upd_ptr[s], 0, lo, hi, 0, 0});
     }
     P.fwd_lvl[l + 1] = (int32_t)(fwd.size() / 12);
     P.bwd_lvl[l + 1] = (int32_t)(bwd.size() / 12);
