@@ -230,9 +230,19 @@ class Problem:
     def solve(self, b, out=None, transpose=0):
         """x = Q(sigma)^{-1} b for a float64 CUDA tensor b of shape (N,) or (nrhs, N)."""
         torch = self._torch
+        if b.dtype != torch.float64 or b.device.type != "cuda":
+            raise ValueError("b must be a float64 CUDA tensor")
+        if not ((b.dim() == 1 and b.shape[0] == self.N) or (b.dim() == 2 and b.shape[1] == self.N)):
+            raise ValueError(f"b must have shape ({self.N},) or (nrhs, {self.N})")
         b = b.contiguous()
         nrhs = 1 if b.dim() == 1 else b.shape[0]
-        x = torch.empty_like(b) if out is None else out
+        if out is None:
+            x = torch.empty_like(b)
+        else:
+            if (out.dtype != torch.float64 or out.device != b.device or not out.is_contiguous()
+                    or tuple(out.shape) != tuple(b.shape)):
+                raise ValueError("out must be a contiguous float64 tensor shaped and placed like b")
+            x = out
         _check(self.lib.rigaqep_solve(self._h, _ptr(b), _ptr(x), nrhs, transpose))
         return x
 
@@ -254,6 +264,8 @@ class Problem:
         opts = eigs_opts(neig, m, tol, max_restarts, seed, shift, ncand, precision, scaling)
         if v1 is not None:
             v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
+            if v1.numel() != 2 * self.N:
+                raise ValueError(f"v1 must have 2N = {2 * self.N} entries")
         st = self.lib.rigaqep_eigs(self._h, neig, float(sigma), ctypes.byref(opts), _ptr(v1),
                                    _ptr(lam), _ptr(X), _ptr(eta), ctypes.byref(nconv))
         if st != 0 and not (st == 7 and not raise_on_noconv):
@@ -263,6 +275,12 @@ class Problem:
     def grad_damping(self, lam, X):
         """d lambda_k / d sigma_e, complex tensor of shape (neig, ne*ne)."""
         torch = self._torch
+        if lam.dtype != torch.complex128 or X.dtype != torch.complex128:
+            raise ValueError("lam and X must be complex128")
+        if lam.dim() != 1 or X.dim() != 2 or X.shape[0] != lam.shape[0] or X.shape[1] != self.N:
+            raise ValueError(f"need lam (neig,) and X (neig, {self.N})")
+        if lam.device != X.device or lam.device.type != "cuda":
+            raise ValueError("lam and X must be on one CUDA device")
         neig = lam.shape[0]
         lam_r = torch.view_as_real(lam.contiguous()).contiguous()
         X_r = torch.view_as_real(X.contiguous()).contiguous()
@@ -305,6 +323,8 @@ class Problem:
     def solve_complex(self, b):
         """x = Q(s)^{-1} b with the complex factor; b: complex128 CUDA tensor (N,)."""
         torch = self._torch
+        if b.dim() != 1 or b.shape[0] != self.N or b.device.type != "cuda":
+            raise ValueError(f"b must be a CUDA tensor of shape ({self.N},)")
         br = torch.view_as_real(b.contiguous().to(torch.complex128)).contiguous()
         x = torch.empty_like(br)
         _check(self.lib.rigaqep_solve_complex(self._h, _ptr(br), _ptr(x), 1))
@@ -328,6 +348,10 @@ class Problem:
         res = torch.empty(max(nmax, 1), dtype=torch.float64, device=dev)
         opts = eigs_opts(1, m or 0, tol, max_restarts, seed)
         opts.krylov_dim = m or 0
+        if v1 is not None:
+            v1 = v1.contiguous().to(device=dev, dtype=torch.float64)
+            if v1.numel() != self.N:
+                raise ValueError(f"v1 must have N = {self.N} entries")
         nf, cnt, cert = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
         _check(self.lib.rigaqep_eigs_undamped(self._h, float(mu_lo), float(mu_hi), int(nmax),
                                               ctypes.byref(opts), _ptr(v1), _ptr(mu), _ptr(X),
