@@ -110,24 +110,30 @@ __global__ void __launch_bounds__(kSellBlock) k_spmv_op(
   pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = warp % kSplit;
   const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
-  // the pattern is fixed before the chain starts; the vectors are not
+  // the pattern and the values are fixed before the chain starts (the first
+  // step's share is loaded before the wait for the previous kernels); the
+  // vectors are not
   const Sell q = sell_slice(off, ns, r);
   const int64_t e0 = q.o0 + lane;
+  int32_t c[kSellUnroll];
+  double mv[kSellUnroll], cv[kSellUnroll];
+  auto load_step = [&](int k) {
+#pragma unroll
+    for (int t = 0; t < kSellUnroll; ++t) {
+      const int64_t e = e0 + 32 * (int64_t)max(0, min(k + t * kSplit, q.wd - 1));
+      c[t] = col[e];
+      mv[t] = Ms[e];
+      cv[t] = Cs[e];
+    }
+  };
+  if (sub < q.wd) load_step(sub);
   pdl_wait();
   // kSellUnroll slots per step, every load of a step issued before its
   // products, so that the column-index loads and then the gathers overlap
   double acc = 0.0;
   for (int k = sub; k < q.wd; k += kSellUnroll * kSplit) {
-    int32_t c[kSellUnroll];
-    double mv[kSellUnroll], cv[kSellUnroll], wv[kSellUnroll], uv[kSellUnroll];
-#pragma unroll
-    for (int t = 0; t < kSellUnroll; ++t) {
-      const int kk = k + t * kSplit;
-      const int64_t e = e0 + 32 * (int64_t)min(kk, q.wd - 1);
-      c[t] = col[e];
-      mv[t] = Ms[e];
-      cv[t] = Cs[e];
-    }
+    double wv[kSellUnroll], uv[kSellUnroll];
+    if (k != sub) load_step(k);
 #pragma unroll
     for (int t = 0; t < kSellUnroll; ++t) {
       wv[t] = w[c[t]];
@@ -207,11 +213,14 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
     mbar_fence_init();
   }
   __syncthreads();
-  pdl_wait();
   // tile t covers rows t*128.. of [V_u; W]: V rows 0..Np-1, then 2Np..3Np-1
   auto vrow = [Np](int t) { const int64_t r = (int64_t)t * kTileRows; return (int)(r < Np ? r : r + Np); };
   // producer (thread 0): the block's first two tiles now, then each stage
-  // again once every warp has released it
+  // again once every warp has released it.  The boxes of basis columns
+  // 0..j-1 (normalised in earlier steps) are issued before the wait for the
+  // previous kernels; the box holding column j (normalised at the end of
+  // the previous step) and the columns past it after the wait.
+  const int nb_early = min(nbox, j / kBoxCols);
   int issued[2] = {-1, -1};   // last iteration whose copy went to each stage
   if (threadIdx.x == 0)
     for (int st2 = 0; st2 < 2; ++st2) {
@@ -219,9 +228,19 @@ __global__ void __launch_bounds__(kDotsThreads, 1)
       if (t < ntile) {
         double* dst = st2 ? stage1 : stage0;
         mbar_expect_tx(&full[st2], bytes);
-        for (int b = 0; b < nbox; ++b)
+        for (int b = 0; b < nb_early; ++b)
           tma_load_2d(dst + b * kBoxCols * kTileRows, &tV, vrow(t), kBoxCols * b, &full[st2]);
         issued[st2] = st2;
+      }
+    }
+  pdl_wait();
+  if (threadIdx.x == 0)
+    for (int st2 = 0; st2 < 2; ++st2) {
+      const int t = (int)blockIdx.x + st2 * (int)gridDim.x;
+      if (t < ntile) {
+        double* dst = st2 ? stage1 : stage0;
+        for (int b = nb_early; b < nbox; ++b)
+          tma_load_2d(dst + b * kBoxCols * kTileRows, &tV, vrow(t), kBoxCols * b, &full[st2]);
       }
     }
   double acc[32];
@@ -363,17 +382,22 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
   const int64_t r = ((int64_t)blockIdx.x * kSlicesPerBlock + warp / kSplit) * 32 + lane;
   const Sell q = sell_slice(off, ns, r);
   const int64_t e0 = q.o0 + lane;
-  pdl_wait();
-  double acc = 0.0;
-  for (int k = sub; k < q.wd; k += kSellUnroll * kSplit) {   // as in k_spmv_op
-    int32_t c[kSellUnroll];
-    double mv[kSellUnroll], zv[kSellUnroll];
+  int32_t c[kSellUnroll];
+  double mv[kSellUnroll];
+  auto load_step = [&](int k) {
 #pragma unroll
     for (int t = 0; t < kSellUnroll; ++t) {
-      const int64_t e = e0 + 32 * (int64_t)min(k + t * kSplit, q.wd - 1);
+      const int64_t e = e0 + 32 * (int64_t)max(0, min(k + t * kSplit, q.wd - 1));
       c[t] = col[e];
       mv[t] = Ms[e];
     }
+  };
+  if (sub < q.wd) load_step(sub);   // the pattern and M: fixed before the chain
+  pdl_wait();
+  double acc = 0.0;
+  for (int k = sub; k < q.wd; k += kSellUnroll * kSplit) {   // as in k_spmv_op
+    double zv[kSellUnroll];
+    if (k != sub) load_step(k);
 #pragma unroll
     for (int t = 0; t < kSellUnroll; ++t) zv[t] = zl[c[t]];
 #pragma unroll
@@ -435,17 +459,31 @@ __global__ void __launch_bounds__(kSellBlock) k_bnorm(
 __global__ void __launch_bounds__(1024) k_update(const double* V, int64_t ld, int ncol,
                                                  const double* h, double* z, int64_t rows) {
   pdl_trigger();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double* vr = V + (i < rows ? i : 0);
+  // the first eight basis columns, when all of them precede the newest one
+  // (column ncol - 1, normalised at the end of the previous step), are
+  // loaded before the wait for the previous kernels
+  const bool early = ncol > 8 && i < rows;
+  double v0[8];
+  if (early) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v0[t] = vr[ld * t];
+  }
   pdl_wait();
   __shared__ double hs[kMaxKrylov + 1];
   for (int t = threadIdx.x; t <= kMaxKrylov; t += blockDim.x) hs[t] = t < ncol ? h[t] : 0.0;
   __syncthreads();
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= rows) return;
-  const double* vr = V + i;
   double a[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) a[t] = 0.0;
   int c = 0;
+  if (early) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) a[t] = fma(v0[t], hs[t], a[t]);
+    c = 8;
+  }
   for (; c + 16 <= ncol; c += 16) {
     double v[16];
 #pragma unroll
