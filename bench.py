@@ -15,7 +15,8 @@ refinement (`mixed`); the p = 4, 512 x 512 lognormal-damping workload in
 FP64 and with tensor-core fronts (`workload_mixed`); the p = 3, 512 x 512
 differentiation workload with all 262,144 damping gradients (`workload_grad`);
 the same 256 x 256 mesh with maximum-continuity IGA against rIGA (`iga`);
-and the 64-problem batch (`batch`).
+the complex shift i sqrt(500) and the undamped slice [500, 1000) of the
+headline mesh (`variants`); and the 64-problem batch (`batch`).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
